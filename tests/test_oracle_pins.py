@@ -1,0 +1,286 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each check uses a closed form,
+a value printed in the paper, an invariant of the flow, an independent
+implementation of a different equation (Hartree-Fock), or exact
+diagonalisation.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from oracle import closed_forms as cf
+from oracle.ed import HubbardED
+from tests.conftest import read_golden
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+# ---------------------------------------------------------------- sampler
+def test_philox_known_answers():
+    for row in read_golden("philox4x32_10_kat.txt"):
+        words = [int(x, 16) for x in row]
+        out = oracle.philox4x32_10(words[0:4], words[4:6])
+        assert out.tolist() == words[6:10]
+
+
+def test_philox_counter_layout():
+    """Block output equals single calls at counter (m_lo, m_hi, spin, p)."""
+    seed, m = 0x1234_5678_9ABC_DEF0, (3 << 32) + 17
+    blk = oracle.philox_block(seed, m, 1, 5, 3)
+    for q in range(3):
+        ref = oracle.philox4x32_10([m & 0xFFFFFFFF, m >> 32, 1, 5 + q], [seed & 0xFFFFFFFF, seed >> 32])
+        assert blk[q].tolist() == ref.tolist()
+
+
+def test_complex_normal_moments():
+    """xi is standard complex normal: E xi = 0, E|xi|^2 = 1, E xi^2 = 0
+    (Re, Im i.i.d. N(0, 1/2)), as fixed by the covariance of App. A.3."""
+    N = 12
+    iu = (slice(None),) + np.triu_indices(N, 1)
+    xs = np.concatenate([oracle.normals(N, 7, m)[iu].ravel() for m in range(3000)])
+    n = xs.size
+    assert abs(xs.mean()) < 5 / math.sqrt(n)
+    assert abs(np.mean(np.abs(xs) ** 2) - 1.0) < 5 * math.sqrt(1.0 / n)
+    assert abs(np.mean(xs ** 2)) < 5 * math.sqrt(1.0 / n)
+    # Box-Muller output is Gaussian: 4th moment E|xi|^4 = 2 for a standard complex normal
+    assert abs(np.mean(np.abs(xs) ** 4) - 2.0) < 6 * math.sqrt(20.0 / n)
+    from scipy import stats
+    assert stats.kstest(np.sqrt(2) * xs.real, "norm").pvalue > 1e-4
+
+
+def test_sample_structure_eq12():
+    """Eq. 12: rho_ii = n_i - 1/2; rho Hermitian; rho_ij = xi_ij s_ij with
+    s_ij = sqrt((n_i + n_j - 2 n_i n_j)/2)."""
+    lat = W.hexagon_chain(2)
+    rng = np.random.default_rng(0)
+    nu, nd = rng.uniform(size=10), rng.uniform(size=10)
+    rho = oracle.sample(10, nu, nd, 99, 5)
+    xi = oracle.normals(10, 99, 5)
+    for s, n in enumerate([nu, nd]):
+        assert np.allclose(np.diag(rho[s]).real, n - 0.5, atol=0, rtol=0)
+        assert np.array_equal(rho[s], rho[s].conj().T)
+        iu = np.triu_indices(10, 1)
+        sd = np.sqrt((n[:, None] + n[None, :] - 2 * n[:, None] * n[None, :]) / 2)
+        assert np.allclose(rho[s][iu], xi[s][iu] * sd[iu], rtol=1e-15, atol=0)
+
+
+def test_sample_covariance_fock():
+    """E|rho_ij|^2 = (n_i + n_j - 2 n_i n_j)/2: 1/2 for a filled/empty pair, 0 otherwise."""
+    lat = W.periodic_honeycomb()
+    nu, nd = W.neel_state(lat)
+    acc = np.zeros((2, 8, 8))
+    M = 4000
+    for m in range(M):
+        acc += np.abs(oracle.sample(8, nu, nd, 3, m)) ** 2
+    acc /= M
+    for s, n in enumerate([nu, nd]):
+        expect = (n[:, None] + n[None, :] - 2 * n[:, None] * n[None, :]) / 2
+        np.fill_diagonal(expect, (n - 0.5) ** 2)
+        assert np.max(np.abs(acc[s] - expect)) < 5 * math.sqrt(1.0 / M)
+        zero = expect == 0
+        assert np.all(acc[s][zero] == 0)
+
+
+# ---------------------------------------------------------------- equations of motion
+def test_rk4_closed_form_U0():
+    """U = 0: the oracle's RK4 equals the eigenbasis closed form to 1e-12 per trajectory."""
+    for lat in [W.periodic_honeycomb(), W.hexagonal_flake(2), W.brick_wall_flake(3, 6)]:
+        nu, nd = W.neel_state(lat)
+        rho0 = oracle.sample(lat.n_sites, nu, nd, 11, 2)
+        rho, _ = oracle.evolve(lat, 0.0, rho0, 0.01, 1000)
+        assert _rel(rho, cf.rk4_free(lat, rho0, 0.01, 1000)) < 1e-12
+
+
+def test_exact_propagator_U0():
+    """U = 0: fTWA is exact; with a step small enough that RK4's error is below
+    1e-13 the oracle matches rho(t) = W rho0 W^dagger, W = exp(-iJt), to 1e-12."""
+    lat = W.periodic_honeycomb()
+    nu, nd = W.neel_state(lat)
+    rho0 = oracle.sample(8, nu, nd, 5, 0)
+    rho, _ = oracle.evolve(lat, 0.0, rho0, 2.5e-4, 4000)
+    assert _rel(rho, cf.exact_free(lat, rho0, 1.0)) < 1e-12
+
+
+def test_initial_derivative_paper_value():
+    """App. C: for a filled site 1 and an empty neighbour 2 (Neel start),
+    d rho_12,up/dt (0) = -i U xi_12 / sqrt(2) + i j_12, exactly."""
+    lat = W.hexagon_chain(2)
+    nu, nd = W.neel_state(lat)
+    U = 1.3
+    rho0 = oracle.sample(10, nu, nd, 21, 4)
+    xi = oracle.normals(10, 21, 4)
+    f = oracle.rhs(lat, U, rho0)
+    checked = 0
+    for (i, j), t in zip(lat.bonds, lat.t_bond):
+        a, b = (i, j) if nu[i] > 0.5 else (j, i)      # a filled (up), b empty (up)
+        x = xi[0][a, b] if a < b else np.conj(xi[0][b, a])
+        expect = -1j * U * x / math.sqrt(2) + 1j * t
+        assert abs(f[0][a, b] - expect) < 1e-14
+        checked += 1
+    assert checked == lat.n_bonds
+
+
+def test_short_time_taylor_paper():
+    """Eq. C.7 (ro11u): rho_11(eps) to second order; the residual is O(eps^3)."""
+    lat = W.brick_wall_flake(4, 6)
+    nu, nd = W.neel_state(lat)
+    U = 1.6
+    rho0 = oracle.sample(lat.n_sites, nu, nd, 8, 1)
+    xi = oracle.normals(lat.n_sites, 8, 1)
+    site = 7                          # interior site, filled with spin up
+    assert nu[site] == 1
+    nb = [(j if i == site else i, t) for (i, j), t in zip(lat.bonds, lat.t_bond) if site in (i, j)]
+    j1 = [t for _, t in nb]
+    x1 = [xi[0][site, k] if site < k else np.conj(xi[0][k, site]) for k, _ in nb]
+    res = []
+    for eps in [0.02, 0.01]:
+        rho, _ = oracle.evolve(lat, U, rho0, eps / 200, 200)
+        res.append(abs(rho[0][site, site].real - cf.rho11_taylor(eps, j1, x1, U)))
+    assert res[0] < 1e-4
+    assert 5.5 < res[0] / res[1] < 11.0      # third-order residual: ratio ~ 8
+
+
+def test_hartree_fock_identity():
+    """Sec. III.A: with zero noise the fTWA flow is Hartree-Fock.  Eq. A.6
+    (Heis_HF2) is integrated here independently on n = rho + 1/2 and compared."""
+    lat = W.hexagon_chain(2)
+    nu, nd = W.neel_state(lat)
+    U, dt, steps = 1.6, 0.01, 300
+    J = cf.hopping_matrix(lat)
+    rho0 = np.stack([np.diag(nu - 0.5), np.diag(nd - 0.5)]).astype(np.complex128)
+    rho0[0][2, 5] = rho0[0][5, 2] = 0.1          # a non-trivial (not stationary) HF state
+    rho, _ = oracle.evolve(lat, U, rho0, dt, steps)
+
+    def hf_rhs(n):
+        # d/dt n_ij,s = i sum_l (j_jl n_il,s - j_li n_lj,s + (u_il - u_lj) n_ll,sbar n_ij,s)
+        out = np.empty_like(n)
+        for s in range(2):
+            d = np.real(np.diag(n[1 - s]))
+            out[s] = 1j * (n[s] @ J - J @ n[s] + U * (d[:, None] - d[None, :]) * n[s])
+        return out
+
+    n = rho0 + 0.5 * np.eye(10)[None]
+    for _ in range(steps):
+        k1 = hf_rhs(n)
+        k2 = hf_rhs(n + dt / 2 * k1)
+        k3 = hf_rhs(n + dt / 2 * k2)
+        k4 = hf_rhs(n + dt * k3)
+        n = n + dt / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    assert _rel(rho + 0.5 * np.eye(10)[None], n) < 1e-13
+
+
+def test_invariants_per_trajectory():
+    """Per trajectory: trace per spin is conserved, rho stays Hermitian, and the
+    classical energy H_W (Eq. A.8) and the spectrum of each rho_s drift only by
+    the RK4 error (halving dt cuts the drift by ~16)."""
+    lat = W.hexagonal_flake(2)
+    nu, nd = W.neel_state(lat)
+    U = 1.6
+    rho0 = oracle.sample(lat.n_sites, nu, nd, 4, 9)
+    e0 = oracle.energy(lat, U, rho0)
+    ev0 = [np.linalg.eigvalsh(rho0[s]) for s in range(2)]
+    drift_e, drift_ev = [], []
+    for dt, steps in [(0.04, 250), (0.02, 500)]:
+        rho, _ = oracle.evolve(lat, U, rho0, dt, steps)
+        for s, n in enumerate([nu, nd]):
+            assert abs(np.trace(rho[s]) - (n.sum() - lat.n_sites / 2)) < 1e-11
+            # the two neighbour sums of Eq. 9 associate differently for
+            # (i, j) and (j, i), so Hermiticity holds to rounding
+            assert np.max(np.abs(rho[s] - rho[s].conj().T)) < 1e-13
+        e = oracle.energy(lat, U, rho)
+        assert abs(e.imag) < 1e-12
+        drift_e.append(abs(e.real - e0.real))
+        drift_ev.append(max(np.max(np.abs(np.linalg.eigvalsh(rho[s]) - ev0[s])) for s in range(2)))
+    assert drift_e[0] < 1e-3 and drift_ev[0] < 1e-3
+    assert 10 < drift_e[0] / drift_e[1] < 24
+    assert 10 < drift_ev[0] / drift_ev[1] < 24
+
+
+# ---------------------------------------------------------------- exact diagonalisation
+def test_ed_dimer_closed_form():
+    for U in [0.0, 1.6, 4.0]:
+        lat = W.dimer()
+        ed = HubbardED(lat, U, 1, 1)
+        assert np.allclose(ed.eigenvalues(), cf.dimer_eigenvalues(U), atol=1e-12)
+
+
+def test_ed_free_fermions():
+    """ED at U = 0 against the one-body propagator and Wick's theorem (Eq. A.4)."""
+    lat = W.periodic_honeycomb()
+    nu, nd = W.neel_state(lat)
+    ed = HubbardED(lat, 0.0, 4, 4)
+    psi0 = np.zeros(ed.dim, dtype=np.complex128)
+    psi0[ed.fock_index(nu, nd)] = 1
+    times = np.linspace(0, 2, 5)
+    occ, nn = ed.observables(ed.evolve(psi0, times))
+    for k, t in enumerate(times):
+        n1 = cf.free_fermion_one_body(lat, nu, t)
+        assert np.allclose(occ[k][:8], np.real(np.diag(n1)), atol=1e-9)
+        w = cf.wick_same_spin(n1)
+        off = ~np.eye(8, dtype=bool)
+        assert np.allclose(nn[k][:8, :8][off], w[off], atol=1e-9)
+
+
+def test_ftwa_statistics_equal_exact_at_U0():
+    """U = 0: fTWA sample means equal the exact free-fermion <n_i>(t) and the
+    same-spin <n_i n_j>(t) of Wick's theorem (Eq. 5 estimators), within the
+    sampling error (|z| < 5)."""
+    lat = W.periodic_honeycomb()
+    nu, nd = W.neel_state(lat)
+    M = 4000
+    snap, _ = oracle.run(lat, 0.0, nu, nd, 17, 0, M, 0.01, 200, 50)
+    occ, conn, _ = oracle.moments(snap, want_g2=False)
+    for k in range(snap.shape[0]):
+        t = k * 0.5
+        n1 = cf.free_fermion_one_body(lat, nu, t)
+        se = np.sqrt(conn[k].diagonal()[:8] / M) + 1e-12
+        z = (occ[k][:8] - np.real(np.diag(n1))) / se
+        assert np.max(np.abs(z)) < 5
+        if t > 0:
+            x = snap[k][:, :8] + 0.5
+            nn = (x[:, :, None] * x[:, None, :]).mean(axis=0)
+            nn_se = (x[:, :, None] * x[:, None, :]).std(axis=0) / math.sqrt(M)
+            w = cf.wick_same_spin(n1)
+            off = ~np.eye(8, dtype=bool)
+            z = (nn[off] - w[off]) / (nn_se[off] + 1e-12)
+            assert np.max(np.abs(z)) < 5
+
+
+# ---------------------------------------------------------------- estimators
+def test_moments_definitions():
+    rng = np.random.default_rng(1)
+    X = rng.normal(size=(3, 500, 6)) * 0.3
+    occ, conn, g2 = oracle.moments(X)
+    for t in range(3):
+        assert np.allclose(occ[t], X[t].mean(axis=0) + 0.5, rtol=1e-14)
+        assert np.allclose(conn[t], np.cov(X[t].T, bias=True), rtol=1e-12, atol=1e-15)
+        x = X[t] + 0.5
+        g = (x.T @ x / 500) / np.outer(x.mean(0), x.mean(0))
+        assert np.allclose(g2[t], g, rtol=1e-12)
+
+
+def test_paper_asymptotes():
+    vals = {r[0]: float(r[1]) for r in read_golden("paper_values.txt")}
+    for n in [4, 6, 10]:
+        assert abs(cf.g2_long_time(n) - vals[f"g2_long_time_n{n}"]) < 1e-12
+    assert round(cf.g2_long_time(198), 3) == vals["g2_long_time_n198"]
+    assert abs(cf.g2_short_time(1.0, [1.0, 1.0]) - vals["g2_short_time_two_neighbours"]) < 1e-15
+    assert abs(cf.g2_short_time(1.0, [1.0, 1.0, 1.0]) - vals["g2_short_time_three_neighbours"]) < 1e-15
+
+
+def test_fd_gradient_converges():
+    """Central differences with common random numbers: halving h changes the
+    U-derivative only at O(h^2)."""
+    lat = W.periodic_honeycomb()
+    nu, nd = W.neel_state(lat)
+    tgt = np.full((2, 16), 0.5)
+    g1 = oracle.fd_gradient(lat, 1.6, nu, nd, 3, 8, 0.01, 40, 20, tgt, [("U",), ("t", 0)], h=1e-3)
+    g2 = oracle.fd_gradient(lat, 1.6, nu, nd, 3, 8, 0.01, 40, 20, tgt, [("U",), ("t", 0)], h=5e-4)
+    assert np.all(np.abs(g1 - g2) <= 1e-5 * np.maximum(1, np.abs(g2)))

@@ -1,0 +1,380 @@
+"""Throughput of the fTWA hot path on one or more GB300s.
+
+Workload (one "step" = one pass of the whole path over one batch): the
+198-site open honeycomb flake (11 x 18 brick wall, 277 bonds), U/t = 1.6,
+half filling with the charge-imbalanced Fock start (doubly occupied central
+hexagon, six emptied edge sites), M = 16384 samples, FP32 state, RK4 with
+dt = 0.01 to T = 10 (1000 steps), snapshots every 10 steps (101 rows), FP64
+moments (occupations, connected Gram, g2).  Per step: ftwa_sample ->
+ftwa_evolve -> ftwa_moments.
+
+metric: sample-RK4-steps/s = M * 1000 / (seconds per step), whole job.
+
+Multi-GPU: samples are independent, so ranks take disjoint sample ranges
+(Philox counters are keyed by the global sample index) with no collective
+on the data path (weak scaling).
+
+--impl reference: the CPU oracle (plain FP64 C, OpenMP) on the host cores,
+timed on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fTWA sample-RK4-steps/s at 198 sites, FP32 vs FP64 GPU at stated error; adjoint time"
+UNIT = "sample-RK4-steps/s"
+FLOP_PER_ELEMENT_STEP = 152          # 4 stages x (2x(3+3) hopping FMAs + U term + i) + RK4 combine
+
+
+def workload(M=16384, steps=1000, every=10, U=1.6):
+    import workloads as W
+    lat = W.brick_wall_flake(11, 18)
+    nu, nd = W.charge_imbalanced_state(lat)
+    return dict(lat=lat, n_up=nu, n_dn=nd, U=U, M=M, steps=steps, every=every)
+
+
+def config_dict(wl, extra=None):
+    c = {"workload": "fTWA 198-site honeycomb flake (brick wall 11x18), charge-imbalanced Fock start",
+         "n_sites": 198, "U_over_t": wl["U"], "samples_per_gpu": wl["M"], "rk4_steps": wl["steps"],
+         "dt": 0.01, "T": 10.0, "out_every": wl["every"], "state": "fp32 complex", "moments": "fp64",
+         "l2": "inputs larger than L2 (state 10.3 GB per GPU)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.seek(0)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    import torch
+    import torch.distributed as dist
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return rank, local, ws
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def traffic_record(kernel_src):
+    """ncu DRAM bytes per launch recorded for this kernel source (or None)."""
+    path = os.path.join(ROOT, "profiles", "rk4_stepper_fp32_198_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    if kv.get("source_sha256_16") != sha:
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_full_workload"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(seconds_target=15.0):
+    """The oracle on the host cores, bounded sample: S samples x n steps of the
+    198-site workload (FP64, all cores)."""
+    import oracle
+    wl = workload()
+    threads = os.cpu_count() or 1
+    S, n = max(threads, 16), 20
+    t0 = time.perf_counter()
+    oracle.run(wl["lat"], wl["U"], wl["n_up"], wl["n_dn"], 2, 0, S, 0.01, n, 10, threads=threads)
+    dt = time.perf_counter() - t0
+    # scale the sample to ~seconds_target
+    n2 = max(n, int(n * seconds_target / max(dt, 1e-3)))
+    n2 = min(n2, 1000)
+    n2 -= n2 % 10
+    t0 = time.perf_counter()
+    oracle.run(wl["lat"], wl["U"], wl["n_up"], wl["n_dn"], 2, 0, S, 0.01, n2, 10, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": S * n2 / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{S} samples x {n2} RK4 steps of the 198-site workload (FP64 C oracle, OpenMP)"}
+
+
+def run_reference(args):
+    rank, local, ws = int(os.environ.get("RANK", "0")), 0, int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    wl = workload()
+    threads = os.cpu_count() or 1
+    S = max(threads, 16)
+    # size one step to a few seconds of CPU work
+    t0 = time.perf_counter()
+    oracle.run(wl["lat"], wl["U"], wl["n_up"], wl["n_dn"], 2, 0, S, 0.01, 10, 10, threads=threads)
+    per = (time.perf_counter() - t0) / 10
+    n = max(10, min(1000, int(8.0 / max(per, 1e-4))))
+    n -= n % 10
+    for _ in range(args.warmup):
+        oracle.run(wl["lat"], wl["U"], wl["n_up"], wl["n_dn"], 2, 0, S, 0.01, 10, 10, threads=threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run(wl["lat"], wl["U"], wl["n_up"], wl["n_dn"], 2, 0, S, 0.01, n, 10, threads=threads)
+        times.append(time.perf_counter() - t0)
+    ms = 1000 * sum(times) / len(times)
+    v = S * n / (ms / 1000)
+    sample = f"{S} samples x {n} RK4 steps of the 198-site workload per step (FP64 C oracle, OpenMP)"
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": config_dict(wl, {"reference_sample": sample}),
+                      "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+                      "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    rank, local, ws = dist_init()
+    torch.cuda.set_device(local)
+    import paper_2212_04352_gb300 as F
+    F.load()
+    wl = workload(M=args.samples)
+    lat, M, steps, every = wl["lat"], wl["M"], wl["steps"], wl["every"]
+    N = lat.n_sites
+    first = rank * M
+    P = F.Plan(lat, wl["U"], n_up=wl["n_up"], n_dn=wl["n_dn"], precision=F.FTWA_FP32, out_every=every)
+    stream = torch.cuda.current_stream()
+    rho = P.new_state(M)
+    X = torch.empty((P.n_out(steps), M, 2 * N), dtype=torch.float32, device="cuda")
+    K = 2 * N
+    T = P.n_out(steps)
+    occ = torch.empty((T, K), dtype=torch.float64, device="cuda")
+    conn = torch.empty((T, K, K), dtype=torch.float64, device="cuda")
+    g2 = torch.empty((T, K, K), dtype=torch.float64, device="cuda")
+    from paper_2212_04352_gb300 import _lib, check, load
+    import ctypes
+    lib = load()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+
+    def one_step(k, timed):
+        check(lib.ftwa_sample(P._h, 7, first, M, ctypes.c_void_p(rho.data_ptr()), sp), "sample")
+        if timed:
+            ev[k][0].record(stream)
+        check(lib.ftwa_evolve(P._h, ctypes.c_void_p(rho.data_ptr()), M, steps, ctypes.c_void_p(X.data_ptr()), sp),
+              "evolve")
+        if timed:
+            ev[k][1].record(stream)
+        check(lib.ftwa_moments(P._h, ctypes.c_void_p(X.data_ptr()), M, T, ctypes.c_void_p(occ.data_ptr()),
+                               ctypes.c_void_p(conn.data_ptr()), ctypes.c_void_p(g2.data_ptr()), 0, sp), "moments")
+
+    for _ in range(args.warmup):
+        one_step(0, False)
+    torch.cuda.synchronize()
+    if P.status() != 0:
+        raise RuntimeError("device status after warm-up")
+    info = P.info()
+    clocks = Clocks(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for k in range(args.steps):
+        one_step(k, True)
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    total_ms = start.elapsed_time(end)
+    total_ms = max_over_ranks(total_ms, ws)
+    evolve_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    if P.status() != 0:
+        raise RuntimeError("device status after timed region")
+    ms_per_step = total_ms / args.steps
+    value = ws * M * steps / (ms_per_step / 1000.0)
+
+    # ---- end to end through the public API with host buffers ---------------------
+    e2e = None
+    if not args.no_e2e:
+        occ_h = torch.empty((T, K), dtype=torch.float64, pin_memory=True)
+        conn_h = torch.empty((T, K, K), dtype=torch.float64, pin_memory=True)
+        g2_h = torch.empty((T, K, K), dtype=torch.float64, pin_memory=True)
+        nu_h = torch.from_numpy(np.asarray(wl["n_up"], dtype=np.float64)).pin_memory()
+        nd_h = torch.from_numpy(np.asarray(wl["n_dn"], dtype=np.float64)).pin_memory()
+        n_dev = torch.empty((2, N), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for k in range(args.e2e_steps):
+            # inputs of the step: the initial occupations (host -> device)
+            n_dev[0].copy_(nu_h, non_blocking=True)
+            n_dev[1].copy_(nd_h, non_blocking=True)
+            torch.cuda.synchronize()
+            Pk = F.Plan(lat, wl["U"], n_up=n_dev[0].cpu().numpy(), n_dn=n_dev[1].cpu().numpy(),
+                        precision=F.FTWA_FP32, out_every=every)
+            Pk.sample(7, M, first_sample=first, out=rho)
+            Xk = Pk.evolve(rho, steps, snap=X)
+            o, c, g = Pk.moments(X)
+            occ_h.copy_(o, non_blocking=True)
+            conn_h.copy_(c, non_blocking=True)
+            g2_h.copy_(g, non_blocking=True)
+            torch.cuda.synchronize()
+            Pk.close()
+        dt = time.perf_counter() - t0
+        dt = max_over_ranks(dt, ws)
+        e2e = {"value": ws * M * steps * args.e2e_steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * N * 8 + lat.n_bonds * 8 * 3,
+               "d2h_bytes_per_step": (T * K + 2 * T * K * K) * 8}
+
+    # ---- FP64 GPU path on a subset, and the FP32 error against it ----------------
+    fp64 = None
+    if not args.no_fp64:
+        Ms = args.fp64_samples
+        P64 = F.Plan(lat, wl["U"], n_up=wl["n_up"], n_dn=wl["n_dn"], precision=F.FTWA_FP64, out_every=every)
+        r64 = P64.sample(11, Ms)
+        r32 = P.sample(11, Ms)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        X64 = P64.evolve(r64, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        X32 = P.evolve(r32, steps)
+        o64, c64, _ = P64.moments(X64, g2=False)
+        o32, _, _ = P.moments(X32, g2=False)
+        var = torch.diagonal(c64, dim1=1, dim2=2)
+        se = torch.sqrt(var / Ms)
+        mask = se > 1e-6
+        ratio = ((o32 - o64).abs()[mask] / se[mask]).max().item() if mask.any() else 0.0
+        fp64 = {"value": Ms * steps / (ms64 / 1000.0), "unit": UNIT, "samples": Ms,
+                "fp32_speedup_vs_fp64": (M * steps / (evolve_ms / 1000.0)) / (Ms * steps / (ms64 / 1000.0)),
+                "fp32_occ_err_over_stderr_max": ratio}
+        P64.close()
+
+    # ---- roofline of the dominant kernel (the RK4 stepper) -----------------------
+    pk = peaks()
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12     # TFLOP/s
+    flops = FLOP_PER_ELEMENT_STEP * N * (N + 1) * M * steps
+    achieved = flops / (evolve_ms / 1000.0) / 1e12
+    traffic = traffic_record(os.path.join(ROOT, "paper_2212_04352_gb300", "csrc", "ftwa_evolve.cu"))
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+            "traffic": traffic, "kernel": "rk4_stepper<float>",
+            "peak_source": f"FP32 FMA: {sm_count} SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (max SM clock, MEASURED_PEAKS.json)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": config_dict(wl, {"parallelism": f"samples split over {ws} GPU(s), no collective",
+                                       "launch": info}),
+            "e2e": e2e, "roofline": roof, "clocks": clk, "gpu_launches": 4 * args.steps,
+            "evolve_ms": evolve_ms, "fp64": fp64}
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line))
+    P.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--samples", type=int, default=16384)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--fp64-samples", type=int, default=512)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "native":
+        print("note: fewer than 3 warm-up steps; the timing contract asks for >= 3", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

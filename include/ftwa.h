@@ -1,0 +1,224 @@
+/*
+ * ftwa.h -- C ABI of the GB300 (sm_103a) fTWA library.
+ *
+ * The library integrates many independent phase-space samples of the
+ * fermionic truncated Wigner approximation (fTWA) for the Fermi-Hubbard
+ * model of Rousse, Eriksson and Ogren (arXiv:2212.04352):
+ *
+ *   H = - sum_{ij s} j_ij c+_is c_js + U sum_i n_i,up n_i,dn         (Eq. 1)
+ *
+ * with nearest-neighbour hoppings j_ij = t_b on the bonds of a lattice of
+ * degree <= 3 and on-site U.  A sample is one complex one-body matrix
+ * rho_ij,s per spin s, drawn from the Gaussian Wigner distribution of a
+ * diagonal initial state (Eq. 12) and advanced by the fTWA equation of
+ * motion (Eq. 9)
+ *
+ *   d/dt rho_s = i (rho_s J - J rho_s) + i U (D_sbar rho_s - rho_s D_sbar),
+ *   D_sbar = diag(Re rho_kk,sbar + 1/2),
+ *
+ * with classical RK4 (the paper names no integrator).  Occupations and
+ * density-density correlators are sample means (Eqs. 5 and 11).
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an int status: FTWA_OK (0) or a negative FTWA_ERR_*
+ *    code.  No call aborts or throws.
+ *  - Pointers named *_dev are device pointers; every other pointer is host
+ *    memory.  The caller owns every state, snapshot and output buffer; the
+ *    plan owns only its constant tables and its internal workspace.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is enqueued asynchronously on it; host-side
+ *    argument errors are reported synchronously before anything is enqueued.
+ *  - Errors raised inside a kernel (a bounded wait that timed out, a
+ *    non-finite value) are recorded in the plan's device status word and
+ *    returned by ftwa_status().
+ *  - State layout at the ABI ("rho_dev"): [M][2][N][N] complex, row-major,
+ *    interleaved (re, im), in the plan's precision (double for FTWA_FP64,
+ *    float for FTWA_FP32).  Index s = 0 is spin up, s = 1 spin down.  Only the
+ *    upper triangle i <= j is read on input (the state is Hermitian); the
+ *    full Hermitian matrix is written on output.
+ *  - Snapshot layout ("snap_dev"): [n_out][M][2N] real, plan precision,
+ *    X[t][m][s*N + i] = Re rho_ii,s of sample m after t*out_every steps,
+ *    n_out = n_steps / out_every + 1 (row 0 is the initial state).
+ */
+#ifndef FTWA_H
+#define FTWA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define FTWA_OK                     0
+#define FTWA_ERR_INVALID_ARGUMENT  -1  /* null pointer, bad size, bad value   */
+#define FTWA_ERR_UNSUPPORTED       -2  /* degree > 3, N above the limit, ...  */
+#define FTWA_ERR_OUT_OF_MEMORY     -3  /* device allocation failed            */
+#define FTWA_ERR_CUDA              -4  /* a CUDA runtime call failed          */
+#define FTWA_ERR_DEVICE_TIMEOUT    -5  /* a bounded in-kernel wait gave up    */
+#define FTWA_ERR_NONFINITE         -6  /* a kernel produced NaN/Inf           */
+
+/* ---- precision and Gram modes ------------------------------------------ */
+#define FTWA_FP64          0   /* state and arithmetic in double             */
+#define FTWA_FP32          1   /* state and arithmetic in float              */
+#define FTWA_GRAM_FP64     0   /* connected Gram in double (CUDA cores)      */
+#define FTWA_GRAM_BF16X3   1   /* hi/lo bf16 split products on tcgen05 MMA   */
+
+/* Largest lattice a plan accepts (sites). */
+#define FTWA_MAX_SITES   256
+
+typedef struct ftwa_plan ftwa_plan_t;
+
+/* Lattice of Eq. 1: n_sites sites and n_bonds bonds (i, j), 0 <= i < j <
+ * n_sites, unique; every site has at most 3 bonds.  t_bond (nullable) gives
+ * j_ij per bond; when NULL every bond has hopping `t` (argument of
+ * ftwa_plan).  Arrays are read during ftwa_plan only. */
+typedef struct {
+    int32_t n_sites;
+    int32_t n_bonds;
+    const int32_t *bonds;    /* host, [n_bonds][2] */
+    const double *t_bond;    /* host, [n_bonds] or NULL */
+} ftwa_lattice;
+
+/* Diagonal initial state of Eq. 12: occupations n_i,s in [0, 1] (Fock
+ * states use 0/1; fractional values describe a thermal diagonal state). */
+typedef struct {
+    const double *n_up;      /* host, [n_sites] */
+    const double *n_dn;      /* host, [n_sites] */
+} ftwa_init_state;
+
+/* Options (zero-initialised = defaults: FP64, dt 0.01, out_every 10,
+ * automatic launch shape). */
+typedef struct {
+    int32_t precision;        /* FTWA_FP64 or FTWA_FP32                       */
+    double dt;                /* RK4 step in units of hbar/t (> 0)            */
+    int32_t out_every;        /* snapshot cadence in steps (>= 1)             */
+    int32_t cluster_override; /* CTAs per sample (1..8), 0 = automatic         */
+    int32_t threads_override; /* threads per CTA (128..1024, multiple of 128)  */
+    int32_t autotune;         /* 1 = time candidate shapes on first evolve     */
+    uint64_t timeout_us;      /* limit of every bounded in-kernel wait in
+                                 microseconds, 0 = default (5 s)             */
+} ftwa_options;
+
+/* Launch shape chosen by the plan (for reporting and tests). */
+typedef struct {
+    int32_t n_sites, n_bonds, precision;
+    int32_t cluster;          /* CTAs per sample                              */
+    int32_t threads;          /* threads per CTA                              */
+    int32_t samples_per_cta;  /* samples resident in one CTA (cluster == 1)   */
+    int32_t smem_bytes;       /* dynamic shared memory per CTA                */
+    int32_t tmem_cols;        /* tensor-memory columns per CTA                */
+    int32_t grid_clusters;    /* persistent clusters launched                 */
+    int32_t units_per_warp;   /* 32-lane work units per warp and sample slot  */
+} ftwa_plan_info;
+
+/* Create a plan: validates the lattice and initial state, builds the
+ * neighbour tables (degree <= 3, per-bond hopping) and uploads them to the
+ * current device.  U is the on-site interaction of Eq. 1.  `filling`, when
+ * > 0, must equal sum_i (n_up + n_dn) / (2 N) within 1e-9 (a consistency
+ * check); when init is NULL a Neel state is built from the lattice's
+ * two-colouring (sublattice of site 0 spin up) and `filling` must be 0.5.
+ * On success *out receives a plan to be released with ftwa_destroy.
+ * Errors: FTWA_ERR_INVALID_ARGUMENT (null out/lattice, bad bonds, n outside
+ * [0,1], dt <= 0, filling mismatch, non-bipartite lattice without init),
+ * FTWA_ERR_UNSUPPORTED (degree > 3, n_sites > FTWA_MAX_SITES or < 2),
+ * FTWA_ERR_OUT_OF_MEMORY, FTWA_ERR_CUDA. */
+int ftwa_plan(const ftwa_lattice *lattice, double U, double t, double filling,
+              const ftwa_init_state *init, const ftwa_options *opts, ftwa_plan_t **out);
+
+/* Release a plan and its device tables (NULL is accepted). */
+void ftwa_destroy(ftwa_plan_t *plan);
+
+/* Report the plan's launch shape. */
+int ftwa_get_info(const ftwa_plan_t *plan, ftwa_plan_info *info);
+
+/* Eq. 12 (ic_fTWA): write M initial samples m = first_sample ..
+ * first_sample + M - 1 into rho_dev ([M][2][N][N] complex, plan precision):
+ * rho_ii,s = n_i,s - 1/2 and, for i < j, rho_ij,s = xi_ij,s sqrt((n_i,s +
+ * n_j,s - 2 n_i,s n_j,s)/2), rho_ji,s = conj(rho_ij,s), xi standard complex
+ * normal (E|xi|^2 = 1, the covariance of App. A.3).  xi comes from
+ * Philox4x32-10 (Salmon et al., SC'11) with key (seed_lo, seed_hi) and
+ * counter (m_lo, m_hi, s, p), p = i N - i(i+1)/2 + j - i - 1, followed by
+ * Box-Muller on two 53-bit uniforms; sample m is a pure function of
+ * (seed, m).  Errors: FTWA_ERR_INVALID_ARGUMENT (null plan/rho_dev with
+ * M > 0, M < 0, first_sample < 0), FTWA_ERR_CUDA. */
+int ftwa_sample(ftwa_plan_t *plan, uint64_t seed, int64_t first_sample, int64_t M,
+                void *rho_dev, void *stream);
+
+/* Raw Philox4x32-10 words for counters (m_lo, m_hi, spin, p0 + q),
+ * q = 0 .. count-1, key (seed_lo, seed_hi): out_dev[q][4] uint32.  Exposes
+ * the integer stage of ftwa_sample for bit-exact checks. */
+int ftwa_philox(uint64_t seed, int64_t m, int32_t spin, int64_t p0, int64_t count,
+                uint32_t *out_dev, void *stream);
+
+/* Eq. 9 (drho) with classical RK4: advance the M samples in rho_dev
+ * (in place, [M][2][N][N] complex, plan precision) by n_steps steps of
+ * size dt.  When snap_dev is not NULL, X[t][m][s*N+i] = Re rho_ii,s after
+ * t*out_every steps is written for t = 0 .. n_steps/out_every ([n_out][M][2N],
+ * plan precision).  Samples are processed by a persistent kernel; one
+ * sample's state stays on chip (shared memory, split across a thread-block
+ * cluster for large N; RK4 registers in tensor memory) for all n_steps.
+ * Errors: FTWA_ERR_INVALID_ARGUMENT (null plan/rho_dev with M > 0, M < 0,
+ * n_steps < 0), FTWA_ERR_UNSUPPORTED (no launch shape fits on chip),
+ * FTWA_ERR_CUDA; in-kernel timeouts via ftwa_status. */
+int ftwa_evolve(ftwa_plan_t *plan, void *rho_dev, int64_t M, int64_t n_steps,
+                void *snap_dev, void *stream);
+
+/* Eqs. 5 and 11 (fTWA_moments, g2_fTWA) from snapshots snap_dev
+ * ([n_times][M][2N], plan precision), accumulated in double:
+ *   occ_dev[t][k]     = <n_k>(t) = mean_m X[t][m][k] + 1/2,   k = s*N + i
+ *   conn_dev[t][k][l] = (1/M) sum_m (X_k - mu_k)(X_l - mu_l)  (connected
+ *                       <n_k n_l> - <n_k><n_l> for k != l; the diagonal is
+ *                       the sample variance of X_k)
+ *   g2_dev[t][k][l]   = mean((X_k + 1/2)(X_l + 1/2)) / (<n_k><n_l>)  (Eq. 11;
+ *                       nullable; the k == l entries are not a g2)
+ * gram_mode FTWA_GRAM_FP64 forms the Gram in double; FTWA_GRAM_BF16X3 forms
+ * it on the tensor cores from centred data split as x = hi + lo (bf16) with
+ * products hi*hi + hi*lo + lo*hi in fp32, reduced across sample blocks in
+ * double.  All outputs are device double arrays.  Errors:
+ * FTWA_ERR_INVALID_ARGUMENT (null pointers, M < 1, n_times < 1, bad mode),
+ * FTWA_ERR_CUDA. */
+int ftwa_moments(ftwa_plan_t *plan, const void *snap_dev, int64_t M, int32_t n_times,
+                 double *occ_dev, double *conn_dev, double *g2_dev, int32_t gram_mode,
+                 void *stream);
+
+/* Discrete adjoint of the RK4 integration of Eq. 9 for the loss
+ * L = sum_{t=1..T} sum_k g_t,k <n_k>(t) (linearised: the caller supplies
+ * dL_docc_dev[t][k] = dL/d<n_k>(t) for the output rows t = 0 .. T,
+ * T = n_steps/out_every, [T+1][2N] device double).  Samples m = 0 .. M-1 of
+ * `seed` are regenerated (Eq. 12), integrated forward with a checkpoint
+ * every ckpt_every steps, and swept backward stage by stage.  Outputs
+ * (device double, overwritten): grad_U_dev[1] = dL/dU, grad_t_dev[n_bonds] =
+ * dL/dt_b (bond order of the lattice), grad_n0_dev[2][N] = dL/dn_i,s through
+ * both rho_ii(0) = n - 1/2 and the noise scale s_ij(n) of Eq. 12 (finite only
+ * where every s_ij > 0, e.g. fractional occupations).  Any output pointer
+ * may be NULL.  ckpt_every must divide n_steps and be a multiple of
+ * out_every.  Errors: FTWA_ERR_INVALID_ARGUMENT, FTWA_ERR_OUT_OF_MEMORY,
+ * FTWA_ERR_CUDA. */
+int ftwa_adjoint(ftwa_plan_t *plan, uint64_t seed, int64_t M, int64_t n_steps, int32_t ckpt_every,
+                 const double *dL_docc_dev, double *grad_U_dev, double *grad_t_dev,
+                 double *grad_n0_dev, void *stream);
+
+/* Synchronise `stream`, then return and clear the plan's device status word
+ * (FTWA_OK, FTWA_ERR_DEVICE_TIMEOUT or FTWA_ERR_NONFINITE), or FTWA_ERR_CUDA
+ * if the synchronisation itself failed. */
+int ftwa_status(ftwa_plan_t *plan, void *stream);
+
+/* Test hook for the timeout path.  While armed (1), every CTA of the next
+ * ftwa_evolve first waits, with the plan's bounded-wait limit, on an
+ * mbarrier that nothing arrives at; the wait runs out, the kernel records
+ * FTWA_ERR_DEVICE_TIMEOUT, skips its work and exits cleanly (the state
+ * buffer is left unchanged).  Disarm with 0. */
+int ftwa_debug_force_timeout(ftwa_plan_t *plan, int32_t armed);
+
+/* Human-readable text of a status code (static storage). */
+const char *ftwa_error_string(int status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int ftwa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FTWA_H */

@@ -1,0 +1,168 @@
+"""GB300 (sm_103a) fTWA hot path: Python binding of the libftwa C ABI.
+
+fermionic truncated Wigner approximation for the Fermi-Hubbard model of
+arXiv:2212.04352: Gaussian Wigner samples of a diagonal state (Eq. 12),
+RK4 integration of the fTWA equation of motion (Eq. 9) and sample-mean
+estimators (Eqs. 5 and 11), each a hand-written CUDA kernel behind
+include/ftwa.h.  This module only marshals arguments: device buffers are
+torch CUDA tensors, passed to the library as raw pointers on torch's current
+stream.  There is no CPU fallback; a missing libftwa.so raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (  # noqa: F401
+    FTWA_FP32, FTWA_FP64, FTWA_GRAM_BF16X3, FTWA_GRAM_FP64, FtwaError, check, load,
+)
+
+__all__ = ["Plan", "plan", "philox", "FTWA_FP32", "FTWA_FP64", "FTWA_GRAM_FP64", "FTWA_GRAM_BF16X3",
+           "FtwaError", "load"]
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """Owner of one ftwa_plan_t (lattice tables, launch shape, status word)."""
+
+    def __init__(self, lattice, U, t=1.0, filling=0.0, n_up=None, n_dn=None, precision=FTWA_FP64,
+                 dt=0.01, out_every=10, cluster=0, timeout_us=0):
+        lib = load()
+        self.N = int(lattice.n_sites)
+        self.n_bonds = int(lattice.n_bonds)
+        self._bonds = np.ascontiguousarray(lattice.bonds, dtype=np.int32)
+        tb = getattr(lattice, "t_bond", None)
+        self._t = None if tb is None else np.ascontiguousarray(tb, dtype=np.float64)
+        lat = _lib.Lattice(self.N, self.n_bonds, self._bonds.ctypes.data,
+                           None if self._t is None else self._t.ctypes.data)
+        init = None
+        if n_up is not None:
+            self._nu = np.ascontiguousarray(n_up, dtype=np.float64)
+            self._nd = np.ascontiguousarray(n_dn, dtype=np.float64)
+            init = _lib.InitState(self._nu.ctypes.data, self._nd.ctypes.data)
+        opts = _lib.Options(int(precision), float(dt), int(out_every), int(cluster), 0, 0, int(timeout_us))
+        h = ctypes.c_void_p()
+        check(lib.ftwa_plan(ctypes.byref(lat), float(U), float(t), float(filling),
+                            None if init is None else ctypes.byref(init), ctypes.byref(opts), ctypes.byref(h)),
+              "ftwa_plan")
+        self._h = h
+        self.U = float(U)
+        self.precision = int(precision)
+        self.dt = float(dt)
+        self.out_every = int(out_every)
+
+    # -- lifetime --------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ftwa_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- helpers ---------------------------------------------------------------
+    @property
+    def real_dtype(self):
+        import torch
+        return torch.float64 if self.precision == FTWA_FP64 else torch.float32
+
+    @property
+    def complex_dtype(self):
+        import torch
+        return torch.complex128 if self.precision == FTWA_FP64 else torch.complex64
+
+    def info(self):
+        inf = _lib.PlanInfo()
+        check(load().ftwa_get_info(self._h, ctypes.byref(inf)), "ftwa_get_info")
+        return {n: getattr(inf, n) for n, _ in _lib.PlanInfo._fields_}
+
+    def new_state(self, M, device="cuda"):
+        import torch
+        return torch.empty((M, 2, self.N, self.N), dtype=self.complex_dtype, device=device)
+
+    def n_out(self, n_steps):
+        return n_steps // self.out_every + 1
+
+    # -- entry points ----------------------------------------------------------
+    def sample(self, seed, M, first_sample=0, out=None, stream=None):
+        rho = self.new_state(M) if out is None else out
+        check(load().ftwa_sample(self._h, int(seed), int(first_sample), int(M), _ptr(rho), _stream(stream)),
+              "ftwa_sample")
+        return rho
+
+    def evolve(self, rho, n_steps, snap=True, stream=None):
+        """Advance rho in place; returns snapshots [n_out, M, 2N] (or None)."""
+        import torch
+        M = rho.shape[0]
+        X = None
+        if snap is True:
+            X = torch.empty((self.n_out(n_steps), M, 2 * self.N), dtype=self.real_dtype, device=rho.device)
+        elif snap is not None and snap is not False:
+            X = snap
+        check(load().ftwa_evolve(self._h, _ptr(rho), int(M), int(n_steps), _ptr(X), _stream(stream)),
+              "ftwa_evolve")
+        return X
+
+    def moments(self, X, gram_mode=FTWA_GRAM_FP64, g2=True, stream=None):
+        """(occ [T, 2N], conn [T, 2N, 2N], g2 [T, 2N, 2N] or None), float64."""
+        import torch
+        T, M, K = X.shape
+        occ = torch.empty((T, K), dtype=torch.float64, device=X.device)
+        conn = torch.empty((T, K, K), dtype=torch.float64, device=X.device)
+        g = torch.empty((T, K, K), dtype=torch.float64, device=X.device) if g2 else None
+        check(load().ftwa_moments(self._h, _ptr(X), int(M), int(T), _ptr(occ), _ptr(conn), _ptr(g),
+                                  int(gram_mode), _stream(stream)), "ftwa_moments")
+        return occ, conn, g
+
+    def adjoint(self, seed, M, n_steps, ckpt_every, dL_docc, stream=None):
+        """(dL/dU [1], dL/dt_b [n_bonds], dL/dn0 [2, N]), float64 device tensors."""
+        import torch
+        dev = dL_docc.device
+        gU = torch.zeros(1, dtype=torch.float64, device=dev)
+        gt = torch.zeros(self.n_bonds, dtype=torch.float64, device=dev)
+        gn = torch.zeros((2, self.N), dtype=torch.float64, device=dev)
+        dl = dL_docc.contiguous().to(torch.float64)
+        check(load().ftwa_adjoint(self._h, int(seed), int(M), int(n_steps), int(ckpt_every), _ptr(dl), _ptr(gU),
+                                  _ptr(gt), _ptr(gn), _stream(stream)), "ftwa_adjoint")
+        return gU, gt, gn
+
+    def status(self, stream=None):
+        """Synchronise the stream and return (and clear) the device status word."""
+        return int(load().ftwa_status(self._h, _stream(stream)))
+
+    def debug_force_timeout(self, armed=True):
+        check(load().ftwa_debug_force_timeout(self._h, 1 if armed else 0), "ftwa_debug_force_timeout")
+
+
+def plan(lattice, U, **kw) -> Plan:
+    return Plan(lattice, U, **kw)
+
+
+def philox(seed, m, spin, p0, count, stream=None):
+    """Raw Philox4x32-10 words [count, 4] (uint32 as int64 tensor on the device)."""
+    import torch
+    out = torch.empty((count, 4), dtype=torch.int32, device="cuda")
+    check(load().ftwa_philox(int(seed), int(m), int(spin), int(p0), int(count), _ptr(out), _stream(stream)),
+          "ftwa_philox")
+    return out.to(torch.int64) & 0xFFFFFFFF

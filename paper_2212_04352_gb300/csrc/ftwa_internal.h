@@ -1,0 +1,72 @@
+// Internal declarations shared by the translation units of libftwa.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/ftwa.h"
+
+namespace ftwa {
+
+constexpr int kMaxCluster = 8;
+constexpr int kThreads = 512;          // threads per CTA of the stepper
+constexpr int kWarps = kThreads / 32;
+constexpr int kTmemCols = 512;         // one CTA per SM holds all of tensor memory
+constexpr int kMinSmem = 120 * 1024;   // forces one stepper CTA per SM
+
+// Launch shape of the RK4 stepper for one slot count.
+struct StepperShape {
+    int cluster = 1;        // CTAs per sample group
+    int slots = 1;          // samples per cluster (cluster == 1 only)
+    int units_per_warp = 0; // E: 32-element work units per warp
+    int meta_cols = 0;      // tensor-memory columns of the metadata block
+    int smem_bytes = 0;
+    int buf_bytes = 0;      // bytes of one stage buffer (max over ranks)
+    int row_begin[kMaxCluster + 1] = {0};  // spin-row partition over ranks
+    int grid = 0;           // CTAs launched
+};
+
+struct Plan {
+    int device = 0;
+    int N = 0, B = 0;
+    int precision = FTWA_FP64;
+    double U = 0, dt = 0.01;
+    int out_every = 10;
+    int cluster_override = 0, threads_override = 0, autotune = 0;
+    uint64_t timeout_ns = 5000000000ull;
+    int force_timeout = 0;
+    int sm_count = 0;
+    bool uniform_t = true;
+    std::vector<int32_t> bonds;       // [B][2]
+    std::vector<double> t_bond;       // [B]
+    std::vector<double> n_up, n_dn;   // [N]
+    std::vector<int32_t> nbr_host;    // [N]: k0 | k1 << 8 | k2 << 16 | deg << 24
+    std::vector<int32_t> nbr_bond;    // [N][3]: bond index of each slot (-1 if none)
+    // device tables
+    int32_t *d_nbr = nullptr;         // [N]
+    int32_t *d_nbr_bond = nullptr;    // [N][3]
+    double *d_t64 = nullptr;          // [N][4] hopping per neighbour slot
+    float *d_t32 = nullptr;           // [N][4]
+    double *d_n = nullptr;            // [2][N] occupations
+    int32_t *d_bonds = nullptr;       // [B][2]
+    int *d_status = nullptr;          // device status word
+    void *d_ws = nullptr;             // plan-owned workspace (moments, adjoint)
+    size_t ws_bytes = 0;
+    StepperShape shape;               // chosen for the full machine
+};
+
+int set_cuda_error(cudaError_t e);
+
+// per-translation-unit launchers
+int launch_sample(Plan *p, uint64_t seed, int64_t first, int64_t M, void *rho, cudaStream_t s);
+int launch_philox(uint64_t seed, int64_t m, int32_t spin, int64_t p0, int64_t count, uint32_t *out,
+                  cudaStream_t s);
+int launch_evolve(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s);
+int choose_stepper_shape(Plan *p, int64_t M, StepperShape *out);
+int launch_moments(Plan *p, const void *snap, int64_t M, int32_t T, double *occ, double *conn, double *g2,
+                   int32_t mode, cudaStream_t s);
+int launch_adjoint(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, int32_t ckpt_every, const double *dL,
+                   double *gU, double *gt, double *gn, cudaStream_t s);
+
+}  // namespace ftwa

@@ -1,0 +1,138 @@
+// Sample-mean estimators of Eqs. 5 and 11 from diagonal snapshots.
+//
+//   mu[t][k]   = (1/M) sum_m X[t][m][k]                 (double, fixed order)
+//   occ[t][k]  = mu + 1/2                               (Eq. 5, first line)
+//   conn[t]    = (1/M) (X - mu)^T (X - mu)              (connected Gram)
+//   g2[t][k][l] = (conn_kl + occ_k occ_l) / (occ_k occ_l)   (Eq. 11: the sample
+//                mean of (X_k + 1/2)(X_l + 1/2) equals conn_kl + occ_k occ_l)
+//
+// Two Gram paths: FP64 on the CUDA cores (reference), and BF16x3 split
+// products on the tcgen05 tensor cores (ftwa_gram_tc.cu).
+#include <cuda_runtime.h>
+
+#include "ftwa_internal.h"
+
+namespace ftwa {
+
+// mean over samples, one block per (t, 32-column group); deterministic order
+template <typename T>
+__global__ void mean_kernel(const T *__restrict__ X, long long M, int K, double *__restrict__ mu,
+                            double *__restrict__ occ)
+{
+    const int t = blockIdx.y;
+    const int k = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int row = threadIdx.x >> 5;      // 8 row groups
+    __shared__ double part[8][32];
+    double s = 0.0;
+    if (k < K) {
+        const T *x = X + (long long)t * M * K + k;
+        for (long long m = row; m < M; m += 8) s += (double)x[m * K];
+    }
+    part[row][threadIdx.x & 31] = s;
+    __syncthreads();
+    if (row == 0 && k < K) {
+        double a = 0.0;
+        for (int r = 0; r < 8; ++r) a += part[r][threadIdx.x];
+        a /= (double)M;
+        mu[t * K + k] = a;
+        occ[t * K + k] = a + 0.5;
+    }
+}
+
+// FP64 connected Gram: one block per (t, 64x64 tile of the upper triangle);
+// 256 threads, 4x4 outputs each; centred samples staged through shared memory.
+template <typename T>
+__global__ void gram_fp64_kernel(const T *__restrict__ X, long long M, int K, const double *__restrict__ mu,
+                                 double *__restrict__ conn, double *__restrict__ g2)
+{
+    const int t = blockIdx.z;
+    const int tk = blockIdx.y, tl = blockIdx.x;
+    if (tl < tk) return;
+    __shared__ double xa[32][64 + 1];
+    __shared__ double xb[32][64 + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4] = {};
+    const T *x = X + (long long)t * M * K;
+    const double *mut = mu + (long long)t * K;
+    for (long long m0 = 0; m0 < M; m0 += 32) {
+        for (int i = threadIdx.x; i < 32 * 64; i += 256) {
+            const int r = i / 64, c = i % 64;
+            const long long m = m0 + r;
+            const int ka = tk * 64 + c, kb = tl * 64 + c;
+            xa[r][c] = (m < M && ka < K) ? (double)x[m * K + ka] - mut[ka] : 0.0;
+            xb[r][c] = (m < M && kb < K) ? (double)x[m * K + kb] - mut[kb] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int r = 0; r < 32; ++r) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                a[i] = xa[r][ty * 4 + i];
+                b[i] = xb[r][tx * 4 + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    const double inv = 1.0 / (double)M;
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            const int k = tk * 64 + ty * 4 + i, l = tl * 64 + tx * 4 + j;
+            if (k >= K || l >= K) continue;
+            const double c = acc[i][j] * inv;
+            const double ok = mut[k] + 0.5, ol = mut[l] + 0.5;
+            const long long base = (long long)t * K * K;
+            conn[base + (long long)k * K + l] = c;
+            conn[base + (long long)l * K + k] = c;
+            if (g2) {
+                const double g = (c + ok * ol) / (ok * ol);
+                g2[base + (long long)k * K + l] = g;
+                g2[base + (long long)l * K + k] = g;
+            }
+        }
+}
+
+int launch_gram_bf16x3(Plan *p, const void *snap, int64_t M, int32_t T, const double *mu, double *conn,
+                       double *g2, cudaStream_t s);
+
+static int ensure_workspace(Plan *p, size_t bytes)
+{
+    if (p->ws_bytes >= bytes) return FTWA_OK;
+    if (p->d_ws) cudaFree(p->d_ws);
+    p->d_ws = nullptr;
+    p->ws_bytes = 0;
+    cudaError_t e = cudaMalloc(&p->d_ws, bytes);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    p->ws_bytes = bytes;
+    return FTWA_OK;
+}
+
+int launch_moments(Plan *p, const void *snap, int64_t M, int32_t T, double *occ, double *conn, double *g2,
+                   int32_t mode, cudaStream_t s)
+{
+    const int K = 2 * p->N;
+    int rc = ensure_workspace(p, sizeof(double) * (size_t)T * K);
+    if (rc != FTWA_OK) return rc;
+    double *mu = reinterpret_cast<double *>(p->d_ws);
+    dim3 gm((K + 31) / 32, T);
+    if (p->precision == FTWA_FP64)
+        mean_kernel<double><<<gm, 256, 0, s>>>(reinterpret_cast<const double *>(snap), M, K, mu, occ);
+    else
+        mean_kernel<float><<<gm, 256, 0, s>>>(reinterpret_cast<const float *>(snap), M, K, mu, occ);
+    rc = set_cuda_error(cudaGetLastError());
+    if (rc != FTWA_OK) return rc;
+    if (mode == FTWA_GRAM_BF16X3) return launch_gram_bf16x3(p, snap, M, T, mu, conn, g2, s);
+    const int nt = (K + 63) / 64;
+    dim3 gg(nt, nt, T);
+    if (p->precision == FTWA_FP64)
+        gram_fp64_kernel<double><<<gg, 256, 0, s>>>(reinterpret_cast<const double *>(snap), M, K, mu, conn, g2);
+    else
+        gram_fp64_kernel<float><<<gg, 256, 0, s>>>(reinterpret_cast<const float *>(snap), M, K, mu, conn, g2);
+    return set_cuda_error(cudaGetLastError());
+}
+
+}  // namespace ftwa

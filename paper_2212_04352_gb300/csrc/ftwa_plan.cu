@@ -1,0 +1,343 @@
+// C ABI entry points: plan creation and validation, dispatch, status.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <set>
+#include <utility>
+
+#include "ftwa_internal.h"
+
+struct ftwa_plan : public ftwa::Plan {};
+
+namespace ftwa {
+
+int set_cuda_error(cudaError_t e)
+{
+    if (e == cudaSuccess) return FTWA_OK;
+    if (e == cudaErrorMemoryAllocation) return FTWA_ERR_OUT_OF_MEMORY;
+    return FTWA_ERR_CUDA;
+}
+
+static void free_tables(Plan *p)
+{
+    cudaFree(p->d_nbr);
+    cudaFree(p->d_nbr_bond);
+    cudaFree(p->d_t64);
+    cudaFree(p->d_t32);
+    cudaFree(p->d_n);
+    cudaFree(p->d_bonds);
+    cudaFree(p->d_status);
+    cudaFree(p->d_ws);
+    p->d_ws = nullptr;
+    p->ws_bytes = 0;
+    p->d_nbr = nullptr;
+    p->d_nbr_bond = nullptr;
+    p->d_t64 = nullptr;
+    p->d_t32 = nullptr;
+    p->d_n = nullptr;
+    p->d_bonds = nullptr;
+    p->d_status = nullptr;
+}
+
+template <typename X>
+static int upload(X **dst, const X *src, size_t n)
+{
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), std::max<size_t>(n, 1) * sizeof(X));
+    if (e != cudaSuccess) return set_cuda_error(e);
+    if (n) e = cudaMemcpy(*dst, src, n * sizeof(X), cudaMemcpyHostToDevice);
+    return set_cuda_error(e);
+}
+
+// Two-colouring of the bond graph; false if it is not bipartite.
+static bool two_colour(int N, const std::vector<int32_t> &bonds, std::vector<int> &col)
+{
+    std::vector<std::vector<int>> adj(N);
+    for (size_t b = 0; b < bonds.size() / 2; ++b) {
+        adj[bonds[2 * b]].push_back(bonds[2 * b + 1]);
+        adj[bonds[2 * b + 1]].push_back(bonds[2 * b]);
+    }
+    col.assign(N, -1);
+    for (int s0 = 0; s0 < N; ++s0) {
+        if (col[s0] >= 0) continue;
+        col[s0] = 0;
+        std::vector<int> q{s0};
+        for (size_t h = 0; h < q.size(); ++h) {
+            for (int v : adj[q[h]]) {
+                if (col[v] < 0) {
+                    col[v] = 1 - col[q[h]];
+                    q.push_back(v);
+                } else if (col[v] == col[q[h]]) {
+                    return false;
+                }
+            }
+        }
+    }
+    return true;
+}
+
+}  // namespace ftwa
+
+using namespace ftwa;
+
+extern "C" {
+
+int ftwa_version(void) { return 10000; }
+
+const char *ftwa_error_string(int status)
+{
+    switch (status) {
+    case FTWA_OK: return "ok";
+    case FTWA_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case FTWA_ERR_UNSUPPORTED: return "unsupported lattice or size";
+    case FTWA_ERR_OUT_OF_MEMORY: return "device out of memory";
+    case FTWA_ERR_CUDA: return "CUDA runtime error";
+    case FTWA_ERR_DEVICE_TIMEOUT: return "bounded device wait timed out";
+    case FTWA_ERR_NONFINITE: return "non-finite value produced";
+    default: return "unknown status";
+    }
+}
+
+int ftwa_plan(const ftwa_lattice *lat, double U, double t, double filling, const ftwa_init_state *init,
+              const ftwa_options *opts, ftwa_plan_t **out)
+{
+    if (!out || !lat) return FTWA_ERR_INVALID_ARGUMENT;
+    *out = nullptr;
+    const int N = lat->n_sites, B = lat->n_bonds;
+    if (N < 2 || N > FTWA_MAX_SITES) return FTWA_ERR_UNSUPPORTED;
+    if (B < 0 || (B > 0 && !lat->bonds)) return FTWA_ERR_INVALID_ARGUMENT;
+    if (!std::isfinite(U) || !std::isfinite(t)) return FTWA_ERR_INVALID_ARGUMENT;
+    if (B > 3 * N) return FTWA_ERR_UNSUPPORTED;
+
+    ftwa_options o{};
+    if (opts) o = *opts;
+    if (o.precision != FTWA_FP64 && o.precision != FTWA_FP32) return FTWA_ERR_INVALID_ARGUMENT;
+    if (o.dt == 0.0) o.dt = 0.01;
+    if (!(o.dt > 0.0) || !std::isfinite(o.dt)) return FTWA_ERR_INVALID_ARGUMENT;
+    if (o.out_every == 0) o.out_every = 10;
+    if (o.out_every < 1) return FTWA_ERR_INVALID_ARGUMENT;
+    if (o.cluster_override < 0 || o.cluster_override > kMaxCluster ||
+        (o.cluster_override & (o.cluster_override - 1)) != 0)
+        return FTWA_ERR_INVALID_ARGUMENT;
+    if (o.threads_override != 0 && o.threads_override != kThreads) return FTWA_ERR_UNSUPPORTED;
+
+    ftwa_plan_t *p = new (std::nothrow) ftwa_plan_t();
+    if (!p) return FTWA_ERR_OUT_OF_MEMORY;
+    p->N = N;
+    p->B = B;
+    p->precision = o.precision;
+    p->U = U;
+    p->dt = o.dt;
+    p->out_every = o.out_every;
+    p->cluster_override = o.cluster_override;
+    p->threads_override = o.threads_override;
+    p->autotune = o.autotune;
+    if (o.timeout_us) p->timeout_ns = o.timeout_us * 1000ull;
+
+    // bonds: 0 <= i < j < N, unique, degree <= 3
+    p->bonds.assign(lat->bonds, lat->bonds + 2 * (size_t)B);
+    p->t_bond.resize(B);
+    std::set<std::pair<int, int>> seen;
+    std::vector<int> deg(N, 0);
+    for (int b = 0; b < B; ++b) {
+        const int i = p->bonds[2 * b], j = p->bonds[2 * b + 1];
+        if (i < 0 || j >= N || i >= j || !seen.insert({i, j}).second) {
+            delete p;
+            return FTWA_ERR_INVALID_ARGUMENT;
+        }
+        const double tb = lat->t_bond ? lat->t_bond[b] : t;
+        if (!std::isfinite(tb)) {
+            delete p;
+            return FTWA_ERR_INVALID_ARGUMENT;
+        }
+        p->t_bond[b] = tb;
+        if (++deg[i] > 3 || ++deg[j] > 3) {
+            delete p;
+            return FTWA_ERR_UNSUPPORTED;
+        }
+    }
+    p->uniform_t = true;
+    for (int b = 1; b < B; ++b) p->uniform_t = p->uniform_t && p->t_bond[b] == p->t_bond[0];
+
+    // occupations
+    p->n_up.resize(N);
+    p->n_dn.resize(N);
+    if (init) {
+        if (!init->n_up || !init->n_dn) {
+            delete p;
+            return FTWA_ERR_INVALID_ARGUMENT;
+        }
+        double tot = 0;
+        for (int i = 0; i < N; ++i) {
+            const double a = init->n_up[i], b = init->n_dn[i];
+            if (!(a >= 0.0 && a <= 1.0 && b >= 0.0 && b <= 1.0)) {
+                delete p;
+                return FTWA_ERR_INVALID_ARGUMENT;
+            }
+            p->n_up[i] = a;
+            p->n_dn[i] = b;
+            tot += a + b;
+        }
+        if (filling > 0 && std::fabs(tot / (2.0 * N) - filling) > 1e-9) {
+            delete p;
+            return FTWA_ERR_INVALID_ARGUMENT;
+        }
+    } else {
+        std::vector<int> col;
+        if (filling != 0.5 || !two_colour(N, p->bonds, col)) {
+            delete p;
+            return FTWA_ERR_INVALID_ARGUMENT;
+        }
+        for (int i = 0; i < N; ++i) {
+            p->n_up[i] = col[i] == col[0] ? 1.0 : 0.0;
+            p->n_dn[i] = 1.0 - p->n_up[i];
+        }
+    }
+
+    // neighbour tables: slots in bond order; empty slots point at the site
+    // itself with zero hopping
+    p->nbr_host.assign(N, 0);
+    p->nbr_bond.assign(3 * (size_t)N, -1);
+    std::vector<double> t64(4 * (size_t)N, 0.0);
+    std::vector<int> fill(N, 0);
+    std::vector<int> slot_k(3 * (size_t)N);
+    for (int i = 0; i < N; ++i)
+        for (int n = 0; n < 3; ++n) slot_k[3 * i + n] = i;
+    for (int b = 0; b < B; ++b) {
+        const int i = p->bonds[2 * b], j = p->bonds[2 * b + 1];
+        slot_k[3 * i + fill[i]] = j;
+        t64[4 * i + fill[i]] = p->t_bond[b];
+        p->nbr_bond[3 * i + fill[i]] = b;
+        fill[i]++;
+        slot_k[3 * j + fill[j]] = i;
+        t64[4 * j + fill[j]] = p->t_bond[b];
+        p->nbr_bond[3 * j + fill[j]] = b;
+        fill[j]++;
+    }
+    for (int i = 0; i < N; ++i)
+        p->nbr_host[i] = slot_k[3 * i] | (slot_k[3 * i + 1] << 8) | (slot_k[3 * i + 2] << 16) | (fill[i] << 24);
+    std::vector<float> t32(t64.begin(), t64.end());
+    std::vector<double> nn(2 * (size_t)N);
+    for (int i = 0; i < N; ++i) {
+        nn[i] = p->n_up[i];
+        nn[N + i] = p->n_dn[i];
+    }
+
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return set_cuda_error(e);
+    }
+    int rc = upload(&p->d_nbr, p->nbr_host.data(), N);
+    if (rc == FTWA_OK) rc = upload(&p->d_nbr_bond, p->nbr_bond.data(), 3 * (size_t)N);
+    if (rc == FTWA_OK) rc = upload(&p->d_t64, t64.data(), t64.size());
+    if (rc == FTWA_OK) rc = upload(&p->d_t32, t32.data(), t32.size());
+    if (rc == FTWA_OK) rc = upload(&p->d_n, nn.data(), nn.size());
+    if (rc == FTWA_OK) rc = upload(&p->d_bonds, p->bonds.data(), p->bonds.size());
+    if (rc == FTWA_OK) {
+        e = cudaMalloc(&p->d_status, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+        rc = set_cuda_error(e);
+    }
+    if (rc != FTWA_OK) {
+        free_tables(p);
+        delete p;
+        return rc;
+    }
+    rc = choose_stepper_shape(p, (int64_t)p->sm_count, &p->shape);
+    if (rc != FTWA_OK) {
+        free_tables(p);
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return FTWA_OK;
+}
+
+void ftwa_destroy(ftwa_plan_t *p)
+{
+    if (!p) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != p->device) cudaSetDevice(p->device);
+    free_tables(p);
+    if (cur != p->device) cudaSetDevice(cur);
+    delete p;
+}
+
+int ftwa_get_info(const ftwa_plan_t *p, ftwa_plan_info *info)
+{
+    if (!p || !info) return FTWA_ERR_INVALID_ARGUMENT;
+    info->n_sites = p->N;
+    info->n_bonds = p->B;
+    info->precision = p->precision;
+    info->cluster = p->shape.cluster;
+    info->threads = kThreads;
+    info->samples_per_cta = p->shape.slots;
+    info->smem_bytes = p->shape.smem_bytes;
+    info->tmem_cols = kTmemCols;
+    info->grid_clusters = p->shape.grid / std::max(1, p->shape.cluster);
+    info->units_per_warp = p->shape.units_per_warp;
+    return FTWA_OK;
+}
+
+int ftwa_sample(ftwa_plan_t *p, uint64_t seed, int64_t first_sample, int64_t M, void *rho_dev, void *stream)
+{
+    if (!p || M < 0 || first_sample < 0 || (M > 0 && !rho_dev)) return FTWA_ERR_INVALID_ARGUMENT;
+    return launch_sample(p, seed, first_sample, M, rho_dev, static_cast<cudaStream_t>(stream));
+}
+
+int ftwa_philox(uint64_t seed, int64_t m, int32_t spin, int64_t p0, int64_t count, uint32_t *out_dev, void *stream)
+{
+    if (count < 0 || m < 0 || p0 < 0 || (count > 0 && !out_dev)) return FTWA_ERR_INVALID_ARGUMENT;
+    return launch_philox(seed, m, spin, p0, count, out_dev, static_cast<cudaStream_t>(stream));
+}
+
+int ftwa_evolve(ftwa_plan_t *p, void *rho_dev, int64_t M, int64_t n_steps, void *snap_dev, void *stream)
+{
+    if (!p || M < 0 || n_steps < 0 || (M > 0 && !rho_dev)) return FTWA_ERR_INVALID_ARGUMENT;
+    return launch_evolve(p, rho_dev, M, n_steps, snap_dev, static_cast<cudaStream_t>(stream));
+}
+
+int ftwa_moments(ftwa_plan_t *p, const void *snap_dev, int64_t M, int32_t n_times, double *occ_dev, double *conn_dev,
+                 double *g2_dev, int32_t gram_mode, void *stream)
+{
+    if (!p || !snap_dev || M < 1 || n_times < 1 || !occ_dev || !conn_dev) return FTWA_ERR_INVALID_ARGUMENT;
+    if (gram_mode != FTWA_GRAM_FP64 && gram_mode != FTWA_GRAM_BF16X3) return FTWA_ERR_INVALID_ARGUMENT;
+    return launch_moments(p, snap_dev, M, n_times, occ_dev, conn_dev, g2_dev, gram_mode,
+                          static_cast<cudaStream_t>(stream));
+}
+
+int ftwa_adjoint(ftwa_plan_t *p, uint64_t seed, int64_t M, int64_t n_steps, int32_t ckpt_every,
+                 const double *dL_docc_dev, double *grad_U_dev, double *grad_t_dev, double *grad_n0_dev, void *stream)
+{
+    if (!p || M < 1 || n_steps < 1 || ckpt_every < 1 || !dL_docc_dev) return FTWA_ERR_INVALID_ARGUMENT;
+    if (n_steps % ckpt_every != 0 || ckpt_every % p->out_every != 0) return FTWA_ERR_INVALID_ARGUMENT;
+    return launch_adjoint(p, seed, M, n_steps, ckpt_every, dL_docc_dev, grad_U_dev, grad_t_dev, grad_n0_dev,
+                          static_cast<cudaStream_t>(stream));
+}
+
+int ftwa_status(ftwa_plan_t *p, void *stream)
+{
+    if (!p) return FTWA_ERR_INVALID_ARGUMENT;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return FTWA_ERR_CUDA;
+    int v = 0;
+    e = cudaMemcpy(&v, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) return FTWA_ERR_CUDA;
+    return v;
+}
+
+int ftwa_debug_force_timeout(ftwa_plan_t *p, int32_t armed)
+{
+    if (!p) return FTWA_ERR_INVALID_ARGUMENT;
+    p->force_timeout = armed ? 1 : 0;
+    return FTWA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,241 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the CPU oracle
+on the same seeded inputs.
+
+Tolerances:
+ - integer stage (Philox words): bit-exact;
+ - FP64 sampler: |rho_gpu - rho_oracle| <= 1e-14 (both evaluate log, sqrt,
+   cos/sin in double; a few ulp of the O(1) normals);
+ - FP64 trajectories: ||rho_gpu - rho_oracle||_F / ||rho_oracle||_F <= 1e-10
+   per sample at T = 10 (1000 RK4 steps, dt = 0.01);
+ - FP32 trajectories: <= 1e-4 relative after 100 steps (float rounding,
+   ~1e-7 per step, amplified by the flow);
+ - FP64 moments: 1e-12 relative (same data, different summation order).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ftwa():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2212_04352_gb300 as F
+    F.load()
+    return F
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _oracle_states(lat, nu, nd, seed, M):
+    return np.stack([oracle.sample(lat.n_sites, nu, nd, seed, m) for m in range(M)])
+
+
+# ------------------------------------------------------------------ sampler
+def test_philox_bit_exact(ftwa):
+    for seed, m, spin, p0, count in [(0, 0, 0, 0, 64), (2**64 - 1, 2**40 + 3, 1, 12345, 100),
+                                     (0x243F6A8885A308D3, 7, 0, 2**31 - 5, 10)]:
+        g = ftwa.philox(seed, m, spin, p0, count).cpu().numpy().astype(np.uint32)
+        o = oracle.philox_block(seed, m, spin, p0, count)
+        assert np.array_equal(g, o)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sample_parity(ftwa, precision):
+    lat = W.hexagonal_flake(2)
+    rng = np.random.default_rng(3)
+    nu, nd = rng.uniform(size=24), rng.uniform(size=24)
+    nu[:4] = [0, 1, 0, 1]                       # Fock entries give s_ij = 0 pairs
+    nd[:4] = [1, 1, 0, 0]
+    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=precision) as P:
+        rho = P.sample(seed=77, M=5, first_sample=3).cpu().numpy()
+    ref = np.stack([oracle.sample(24, nu, nd, 77, 3 + m) for m in range(5)])
+    if precision == 0:
+        assert np.max(np.abs(rho - ref)) <= 1e-14
+    else:
+        assert np.max(np.abs(rho - ref)) <= 2e-6
+
+
+# ------------------------------------------------------------------ stepper
+CASES = [
+    ("periodic8", lambda: W.periodic_honeycomb(), 1.6, "neel", 7),
+    ("hexflake24", lambda: W.hexagonal_flake(2), 1.6, "neel", 5),
+    ("hexchain10_thermal", lambda: W.hexagon_chain(2), 2.5, "thermal", 3),
+]
+
+
+def _state(lat, kind):
+    if kind == "neel":
+        return W.neel_state(lat)
+    rng = np.random.default_rng(11)
+    return rng.uniform(size=lat.n_sites), rng.uniform(size=lat.n_sites)
+
+
+@pytest.mark.parametrize("name,make,U,kind,M", CASES)
+def test_evolve_fp64_matches_oracle(ftwa, name, make, U, kind, M):
+    """Per trajectory, FP64, T = 10 (1000 steps), snapshots every 10 steps."""
+    lat = make()
+    nu, nd = _state(lat, kind)
+    seed, steps, every = 1, 1000, 10
+    snap_o, fin_o = oracle.run(lat, U, nu, nd, seed, 0, M, 0.01, steps, every, want_final=True)
+    with ftwa.Plan(lat, U, n_up=nu, n_dn=nd, precision=0, out_every=every) as P:
+        rho = P.sample(seed, M)
+        X = P.evolve(rho, steps)
+        assert P.status() == 0
+        fin = rho.cpu().numpy()
+        X = X.cpu().numpy()
+    for m in range(M):
+        assert _rel(fin[m], fin_o[m]) <= 1e-10, (name, m, _rel(fin[m], fin_o[m]))
+    assert np.max(np.abs(X - snap_o)) <= 1e-10
+
+
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8])
+def test_evolve_cluster_shapes(ftwa, cluster):
+    """Every cluster split of the spin-rows gives the oracle's trajectory
+    (oracle-drawn rho(0) fed to the GPU; ragged M)."""
+    lat = W.hexagonal_flake(3)          # 54 sites
+    nu, nd = W.neel_state(lat)
+    M, steps = 3, 200
+    rho0 = _oracle_states(lat, nu, nd, 9, M)
+    fin_o = np.stack([oracle.evolve(lat, 1.6, rho0[m], 0.01, steps)[0] for m in range(M)])
+    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=0, cluster=cluster) as P:
+        assert P.info()["cluster"] == cluster
+        rho = torch.from_numpy(rho0).cuda()
+        P.evolve(rho, steps, snap=None)
+        assert P.status() == 0
+        fin = rho.cpu().numpy()
+    for m in range(M):
+        assert _rel(fin[m], fin_o[m]) <= 1e-11
+
+
+def test_evolve_198_sites_fp64(ftwa):
+    """The 198-site brick-wall flake, charge-imbalanced start: a few sampled
+    trajectories, full T = 10."""
+    lat = W.brick_wall_flake()
+    nu, nd = W.charge_imbalanced_state(lat)
+    M, steps = 2, 1000
+    snap_o, fin_o = oracle.run(lat, 1.6, nu, nd, 2, 0, M, 0.01, steps, 100, want_final=True)
+    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=0, out_every=100) as P:
+        rho = P.sample(2, M)
+        X = P.evolve(rho, steps)
+        assert P.status() == 0
+        fin = rho.cpu().numpy()
+    for m in range(M):
+        assert _rel(fin[m], fin_o[m]) <= 1e-10
+    assert np.max(np.abs(X.cpu().numpy() - snap_o)) <= 1e-10
+
+
+@pytest.mark.parametrize("lat_name", ["periodic8", "brick198"])
+def test_evolve_fp32_short(ftwa, lat_name):
+    lat = W.periodic_honeycomb() if lat_name == "periodic8" else W.brick_wall_flake()
+    nu, nd = W.neel_state(lat)
+    M, steps = 3, 100
+    rho0 = _oracle_states(lat, nu, nd, 4, M)
+    fin_o = np.stack([oracle.evolve(lat, 1.6, rho0[m], 0.01, steps)[0] for m in range(M)])
+    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=1) as P:
+        rho = torch.from_numpy(rho0.astype(np.complex64)).cuda()
+        P.evolve(rho, steps, snap=None)
+        assert P.status() == 0
+        fin = rho.cpu().numpy().astype(np.complex128)
+    for m in range(M):
+        assert _rel(fin[m], fin_o[m]) <= 1e-4
+
+
+def test_hermitian_output_and_trace(ftwa):
+    lat = W.hexagonal_flake(2)
+    nu, nd = W.neel_state(lat)
+    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=0) as P:
+        rho = P.sample(5, 4)
+        P.evolve(rho, 300, snap=None)
+        r = rho.cpu().numpy()
+    for m in range(4):
+        for s, n in enumerate([nu, nd]):
+            assert np.array_equal(r[m, s], r[m, s].conj().T)
+            assert abs(np.trace(r[m, s]) - (n.sum() - 12)) < 1e-11
+
+
+def test_edge_cases(ftwa):
+    lat = W.dimer()
+    with ftwa.Plan(lat, 1.0, n_up=[1, 0], n_dn=[0, 1], precision=0) as P:
+        rho = P.sample(1, 1)
+        r0 = rho.clone()
+        P.evolve(rho, 0, snap=None)                 # zero steps: state unchanged
+        assert torch.equal(rho, r0)
+        P.evolve(rho[:0], 10, snap=None)             # empty batch
+        with pytest.raises(ftwa.FtwaError):
+            ftwa.load()
+            from paper_2212_04352_gb300 import check, load
+            check(load().ftwa_evolve(P._h, None, 4, 10, None, None), "evolve")
+        assert P.status() == 0
+    # dimer: fTWA at U = 0 is exact -> <n_1,up>(t) = cos^2(t)
+    with ftwa.Plan(lat, 0.0, n_up=[1, 0], n_dn=[0, 1], precision=0, out_every=50) as P:
+        rho = P.sample(3, 20000)
+        X = P.evolve(rho, 100)
+        occ, conn, _ = P.moments(X, g2=False)
+        occ = occ.cpu().numpy()
+        se = np.sqrt(np.diagonal(conn.cpu().numpy(), axis1=1, axis2=2) / 20000) + 1e-12
+        for k, t in enumerate([0.0, 0.5, 1.0]):
+            assert abs(occ[k, 0] - math.cos(t) ** 2) < 5 * se[k, 0] + 1e-12
+
+
+def test_timeout_hook_returns_status(ftwa):
+    """A bounded wait that runs out (a barrier nothing arrives at) reports
+    FTWA_ERR_DEVICE_TIMEOUT; the context stays usable afterwards."""
+    lat = W.hexagonal_flake(3)
+    nu, nd = W.neel_state(lat)
+    for cluster in [1, 2]:
+        with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=0, cluster=cluster, timeout_us=2000) as P:
+            rho = P.sample(1, 2)
+            r0 = rho.clone()
+            P.debug_force_timeout(True)
+            P.evolve(rho, 50, snap=None)
+            assert P.status() == -5
+            assert torch.equal(rho, r0)
+            P.debug_force_timeout(False)
+            P.evolve(rho, 10, snap=None)
+            assert P.status() == 0
+
+
+# ------------------------------------------------------------------ moments
+@pytest.mark.parametrize("precision", [0, 1])
+def test_moments_fp64_parity(ftwa, precision):
+    lat = W.periodic_honeycomb()
+    nu, nd = W.neel_state(lat)
+    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=precision) as P:
+        rho = P.sample(1, 1000)
+        X = P.evolve(rho, 200)
+        occ, conn, g2 = P.moments(X)
+        Xh = X.cpu().numpy().astype(np.float64)
+    occ_o, conn_o, g2_o = oracle.moments(Xh)
+    assert np.max(np.abs(occ.cpu().numpy() - occ_o)) <= 1e-13
+    assert np.max(np.abs(conn.cpu().numpy() - conn_o)) <= 1e-13
+    assert np.max(np.abs(g2.cpu().numpy() - g2_o) / np.abs(g2_o)) <= 1e-11
+
+
+def test_full_path_config1_against_oracle(ftwa):
+    """8-site periodic honeycomb, U/t = 1.6, Neel, M = 1000, T = 10, 100 output
+    times: GPU FP64 path (sample -> evolve -> moments) equals the oracle's."""
+    lat = W.periodic_honeycomb()
+    nu, nd = W.neel_state(lat)
+    M = 1000
+    snap_o, _ = oracle.run(lat, 1.6, nu, nd, 1, 0, M, 0.01, 1000, 10)
+    occ_o, conn_o, _ = oracle.moments(snap_o, want_g2=False)
+    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=0, out_every=10) as P:
+        rho = P.sample(1, M)
+        X = P.evolve(rho, 1000)
+        occ, conn, _ = P.moments(X, g2=False)
+        assert P.status() == 0
+    assert X.shape == (101, M, 16)
+    assert np.max(np.abs(occ.cpu().numpy() - occ_o)) <= 1e-10
+    assert np.max(np.abs(conn.cpu().numpy() - conn_o)) <= 1e-10

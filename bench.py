@@ -355,6 +355,26 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_profile_case(args):
+    """A small invocation for ncu captures: one sample -> evolve -> moments pass
+    on the 198-site workload with few samples and steps."""
+    import torch
+    import paper_2212_04352_gb300 as F
+    wl = workload(M=args.samples, steps=args.prof_steps)
+    prec = F.FTWA_FP64 if args.precision == "fp64" else F.FTWA_FP32
+    P = F.Plan(wl["lat"], wl["U"], n_up=wl["n_up"], n_dn=wl["n_dn"], precision=prec, out_every=wl["every"])
+    for _ in range(args.prof_repeat):
+        rho = P.sample(7, wl["M"])
+        X = P.evolve(rho, wl["steps"])
+        P.moments(X, gram_mode=args.gram)
+    torch.cuda.synchronize()
+    st = P.status()
+    print(json.dumps({"profile_case": True, "samples": wl["M"], "steps": wl["steps"], "status": st,
+                      "launch": P.info()}))
+    if st != 0:
+        raise SystemExit(1)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -367,7 +387,15 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="small case for ncu captures")
+    ap.add_argument("--prof-steps", type=int, default=20)
+    ap.add_argument("--prof-repeat", type=int, default=2)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--gram", type=int, default=0)
     args = ap.parse_args()
+    if args.profile:
+        run_profile_case(args)
+        return
     if args.warmup < 3 and args.impl == "native":
         print("note: fewer than 3 warm-up steps; the timing contract asks for >= 3", file=sys.stderr)
     if args.impl == "reference":

@@ -36,8 +36,8 @@ template <typename T>
 struct StepArgs {
     const int32_t *nbr;   // [N] k0 | k1 << 8 | k2 << 16 | deg << 24
     const T *tnb;         // [N][4]
-    T U, dt;
-    int N, C, S, E, meta_cols, buf_bytes;
+    T U, dt, t_uniform;
+    int N, C, S, E, buf_bytes, n_units_max, fast_chunk;
     int row_begin[kMaxCluster + 1];
     long long M, n_steps;
     int out_every;
@@ -53,7 +53,23 @@ struct SmemHeader {
     unsigned long long dead_bar;  // never completes (timeout test hook)
     uint32_t tmem_base;
     int abort;
-    int pad[2];
+    int n_units;
+    int pad;
+};
+
+// Per spin-row descriptor.  base(r) denotes the address of element (p, 0)
+// of row r = (s, p) in stage buffer A as if the row were stored in full:
+// element (p, q), q >= p, lives at base(r) + q * sizeof(V).
+struct __align__(16) RowDesc {
+    uint32_t base_local;   // base of this row in the owning CTA (shared::cta)
+    uint32_t base_k[3];    // bases of the rows of p's neighbours: shared::cta if
+                           // the row is owned by this CTA, else shared::cluster
+    int32_t nbp;           // p's neighbour slots (packed as in nbr)
+    int32_t p;             // site index
+    int32_t remote;        // bit n: neighbour row n lives in another CTA
+    int32_t deg;           // number of bonds of p
+    uint32_t base_kc[3];   // the same bases as shared::cluster addresses
+    uint32_t pad;
 };
 
 __device__ __forceinline__ void record_status(int *status, int code)
@@ -84,56 +100,295 @@ __device__ __forceinline__ bool stage_barrier(SmemHeader *h, uint32_t &phase, in
 }
 
 template <typename T, bool CLUSTER>
+__device__ __forceinline__ typename C2<T>::type ld_state(uint32_t a)
+{
+    if constexpr (CLUSTER) return ldc2(a, T());
+    else return lds2(a, T());
+}
+
+// tensor-memory state words of one element: y0 then acc (WC words each)
+template <int WC>
+__device__ __forceinline__ void tmem_ld_state(uint32_t ta, uint32_t (&w)[2 * WC])
+{
+    if constexpr (WC == 2) {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "r"(ta) : "memory");
+    } else {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+                     : "r"(ta)
+                     : "memory");
+    }
+}
+// wait for the load; the words are in/out operands so no use of them can be
+// scheduled before the wait
+template <int WC>
+__device__ __forceinline__ void tmem_wait_ld_regs(uint32_t (&w)[2 * WC])
+{
+    if constexpr (WC == 2) {
+        asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(w[0]), "+r"(w[1]), "+r"(w[2]), "+r"(w[3]) :: "memory");
+    } else {
+        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                     : "+r"(w[0]), "+r"(w[1]), "+r"(w[2]), "+r"(w[3]), "+r"(w[4]), "+r"(w[5]), "+r"(w[6]), "+r"(w[7])
+                     :: "memory");
+    }
+}
+template <int WC, typename V>
+__device__ __forceinline__ void unpack_state(const uint32_t (&w)[2 * WC], V &y0, V &acc)
+{
+    if constexpr (WC == 2) {
+        y0.x = __uint_as_float(w[0]);
+        y0.y = __uint_as_float(w[1]);
+        acc.x = __uint_as_float(w[2]);
+        acc.y = __uint_as_float(w[3]);
+    } else {
+        y0.x = __longlong_as_double(((unsigned long long)w[1] << 32) | w[0]);
+        y0.y = __longlong_as_double(((unsigned long long)w[3] << 32) | w[2]);
+        acc.x = __longlong_as_double(((unsigned long long)w[5] << 32) | w[4]);
+        acc.y = __longlong_as_double(((unsigned long long)w[7] << 32) | w[6]);
+    }
+}
+
+template <int STAGE, typename T, bool CLUSTER, bool UNIFORM_T>
+__device__ __forceinline__ void rk4_stage(const StepArgs<T> &a, const RowDesc *s_desc, const uint32_t *s_rowbase,
+                                          const uint32_t *s_units, const int32_t *s_nbr, const T *s_t, T *s_diag,
+                                          uint32_t diag_s, int n_units, int warp, int lane, uint32_t t_state,
+                                          int eps_bytes, int diag_stride, long long b, bool snap_now,
+                                          long long snap_row)
+{
+    using V = typename C2<T>::type;
+    constexpr int SZ = sizeof(V);
+    constexpr int WC = SZ / 4;
+    constexpr int CUR = STAGE & 1;
+    const int N = a.N, twoN = 2 * N;
+    const uint32_t boff_cur = CUR ? (uint32_t)a.buf_bytes : 0u;
+    const uint32_t boff_nxt = CUR ? 0u : (uint32_t)a.buf_bytes;
+    const T *dg = s_diag + CUR * diag_stride;
+    const T half_dt = a.dt * T(0.5), sixth_dt = a.dt / T(6);
+    // y0 and acc of the next unit are loaded from tensor memory while the
+    // current unit computes (one tcgen05.ld in flight per warp)
+    uint32_t nx[2 * WC];
+    tmem_ld_state<WC>(t_state, nx);
+    for (int j = 0; j < a.E; ++j) {
+        const int u = j * kWarps + warp;
+        tmem_wait_ld_regs<WC>(nx);
+        V y0, acc;
+        unpack_state<WC>(nx, y0, acc);
+        __syncwarp();
+        if (j + 1 < a.E) tmem_ld_state<WC>(t_state + (uint32_t)((j + 1) * 2 * WC), nx);
+        if (u < n_units) {
+            const uint32_t unit = s_units[u];
+            const int chunk = unit & 7, sr = (unit >> 3) & 511, slot = unit >> 12;
+            const RowDesc d = s_desc[sr];
+            const int p = d.p, s = sr >= N ? 1 : 0;
+            const int q = p + 32 * chunk + lane;
+            if (q < N) {
+                const uint32_t soff = (uint32_t)(slot * eps_bytes) + boff_cur;
+                const uint32_t qoff = soff + (uint32_t)(q * SZ);
+                const V own = lds2(d.base_local + qoff, T());
+                const int nq = s_nbr[q];
+                T hr = T(0), hi = T(0);
+                if (chunk >= a.fast_chunk) {
+                    // away from the diagonal: every rho_pk (k in nb(q)) and rho_kq
+                    // (k in nb(p)) is in the stored triangle; rho_pk is in this
+                    // CTA's own row p.  Empty neighbour slots carry zero hopping.
+#pragma unroll
+                    for (int n = 0; n < 3; ++n) {
+                        const int k = (nq >> (8 * n)) & 0xFF;
+                        const T t = UNIFORM_T ? (n < (nq >> 24) ? a.t_uniform : T(0)) : s_t[4 * q + n];
+                        const V v = lds2(d.base_local + soff + (uint32_t)(k * SZ), T());
+                        hr = fma(t, v.x, hr);
+                        hi = fma(t, v.y, hi);
+                    }
+#pragma unroll
+                    for (int n = 0; n < 3; ++n) {
+                        const T t = UNIFORM_T ? (n < d.deg ? a.t_uniform : T(0)) : s_t[4 * p + n];
+                        const V v = CLUSTER ? ldc2(d.base_kc[n] + qoff, T()) : lds2(d.base_k[n] + qoff, T());
+                        hr = fma(-t, v.x, hr);
+                        hi = fma(-t, v.y, hi);
+                    }
+                } else {
+                    // near the diagonal: entries below it are read as conj(rho_ba)
+#pragma unroll
+                    for (int n = 0; n < 3; ++n) {
+                        const int k = (nq >> (8 * n)) & 0xFF;
+                        const T t = UNIFORM_T ? (n < (nq >> 24) ? a.t_uniform : T(0)) : s_t[4 * q + n];
+                        V v;
+                        if (k >= p) {
+                            v = lds2(d.base_local + soff + (uint32_t)(k * SZ), T());
+                        } else {
+                            v = ld_state<T, CLUSTER>(s_rowbase[s * N + k] + soff + (uint32_t)(p * SZ));
+                            v.y = -v.y;
+                        }
+                        hr = fma(t, v.x, hr);
+                        hi = fma(t, v.y, hi);
+                    }
+#pragma unroll
+                    for (int n = 0; n < 3; ++n) {
+                        if (n < d.deg) {
+                            const int k = (d.nbp >> (8 * n)) & 0xFF;
+                            const T t = UNIFORM_T ? a.t_uniform : s_t[4 * p + n];
+                            V v;
+                            if (k <= q) {
+                                if (CLUSTER && ((d.remote >> n) & 1)) v = ldc2(d.base_k[n] + qoff, T());
+                                else v = lds2(d.base_k[n] + qoff, T());
+                            } else {
+                                v = ld_state<T, CLUSTER>(s_rowbase[s * N + q] + soff + (uint32_t)(k * SZ));
+                                v.y = -v.y;
+                            }
+                            hr = fma(-t, v.x, hr);
+                            hi = fma(-t, v.y, hi);
+                        }
+                    }
+                }
+                // + U (Re rho_pp,sbar - Re rho_qq,sbar) rho_pq
+                const T *db = dg + slot * twoN + (1 - s) * N;
+                const T g = a.U * (db[p] - db[q]);
+                hr = fma(g, own.x, hr);
+                hi = fma(g, own.y, hi);
+                // k = i (hr + i hi); on the diagonal Eq. 9 is real, so its imaginary
+                // part (pure rounding residue) is dropped
+                const T kx = -hi, ky = (q == p) ? T(0) : hr;
+                V nxt;
+                if constexpr (STAGE == 0) {
+                    acc.x = kx;
+                    acc.y = ky;
+                    nxt.x = fma(half_dt, kx, y0.x);
+                    nxt.y = fma(half_dt, ky, y0.y);
+                } else if constexpr (STAGE < 3) {
+                    acc.x = fma(T(2), kx, acc.x);
+                    acc.y = fma(T(2), ky, acc.y);
+                    const T c = STAGE == 1 ? half_dt : a.dt;
+                    nxt.x = fma(c, kx, y0.x);
+                    nxt.y = fma(c, ky, y0.y);
+                } else {
+                    nxt.x = fma(sixth_dt, acc.x + kx, y0.x);
+                    nxt.y = fma(sixth_dt, acc.y + ky, y0.y);
+                    y0 = nxt;
+                }
+                sts2(d.base_local + qoff - boff_cur + boff_nxt, nxt);
+                if (q == p) {
+                    const int di = (CUR ^ 1) * diag_stride + slot * twoN + s * N + p;
+                    if constexpr (CLUSTER) {
+                        const uint32_t da = diag_s + (uint32_t)(di * (int)sizeof(T));
+                        for (int r = 0; r < a.C; ++r) stc1(map_rank(da, r), nxt.x);
+                    } else {
+                        s_diag[di] = nxt.x;
+                    }
+                    if (STAGE == 3 && snap_now) {
+                        const long long m = b * a.S + slot;
+                        if (m < a.M) a.snap[(snap_row * a.M + m) * twoN + s * N + p] = nxt.x;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if constexpr (STAGE < 3) tmem_put(t_state + (uint32_t)(j * 2 * WC + WC), acc);
+        else tmem_put(t_state + (uint32_t)(j * 2 * WC), y0);
+    }
+}
+
+template <typename T, bool CLUSTER, bool UNIFORM_T>
 __global__ void __launch_bounds__(kThreads, 1) rk4_stepper(const StepArgs<T> a)
 {
     using V = typename C2<T>::type;
+    constexpr int SZ = sizeof(V);
+    constexpr int WC = SZ / 4;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int N = a.N, S = a.S, C = a.C;
+    const int N = a.N, S = a.S, C = a.C, twoN = 2 * N;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = CLUSTER ? cluster_ctarank() : 0u;
     const uint32_t cid = CLUSTER ? cluster_id_x() : blockIdx.x;
     const uint32_t ncl = CLUSTER ? n_clusters_x() : gridDim.x;
 
-    // ---- shared-memory carve-up ------------------------------------------
-    SmemHeader *h = reinterpret_cast<SmemHeader *>(smem);
-    int32_t *s_nbr = reinterpret_cast<int32_t *>(smem + 64);
-    T *s_t = reinterpret_cast<T *>(smem + 64 + 4 * 256);
-    uint32_t *s_row = reinterpret_cast<uint32_t *>(smem + 64 + 4 * 256 + sizeof(T) * 4 * 256);
-    T *s_diag = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(s_row) +
-                                      ((4 * S * 2 * N + 15) / 16) * 16);   // [2 buf][S][2N]
-    unsigned char *bufA = reinterpret_cast<unsigned char *>(s_diag) + ((sizeof(T) * 2 * S * 2 * N + 15) / 16) * 16;
+    // ---- shared-memory carve-up (mirrors smem_needed on the host) -----------
+    unsigned char *ptr = smem;
+    SmemHeader *h = reinterpret_cast<SmemHeader *>(ptr);
+    ptr += 64;
+    int32_t *s_nbr = reinterpret_cast<int32_t *>(ptr);
+    ptr += 4 * 256;
+    T *s_t = reinterpret_cast<T *>(ptr);
+    ptr += sizeof(T) * 4 * 256;
+    RowDesc *s_desc = reinterpret_cast<RowDesc *>(ptr);
+    ptr += sizeof(RowDesc) * 2 * 256;
+    uint32_t *s_rowbase = reinterpret_cast<uint32_t *>(ptr);
+    ptr += 4 * 2 * 256;
+    uint32_t *s_units = reinterpret_cast<uint32_t *>(ptr);
+    ptr += 4 * ((a.n_units_max + 3) / 4) * 4;
+    T *s_diag = reinterpret_cast<T *>(ptr);                        // [2 buf][S][2N]
+    ptr += ((sizeof(T) * 2 * S * twoN + 15) / 16) * 16;
+    unsigned char *bufA = ptr;
     const uint32_t bufA_s = smem_addr(bufA);
     const uint32_t diag_s = smem_addr(s_diag);
-    const int diag_stride = S * 2 * N;   // elements per diag buffer
+    const int diag_stride = S * twoN;
 
     const int rb0 = a.row_begin[rank], rb1 = a.row_begin[rank + 1];
-    // elements per slot of this rank
-    int eps = 0;
+    int eps = 0;                      // packed elements per slot of this rank
     for (int sr = rb0; sr < rb1; ++sr) eps += N - (sr % N);
-    const int n_elem = eps * S;
+    const int eps_bytes = eps * SZ;
 
     if (threadIdx.x == 0) {
         h->abort = 0;
         mbar_init(smem_addr(&h->bar), (uint32_t)C);
         mbar_init(smem_addr(&h->dead_bar), 1u);
         fence_mbar_init_cluster();
+        // work units: (slot, spin-row, 32-column chunk) of this rank.  Units
+        // next to the diagonal (slower path) come first, so that unit u =
+        // j * kWarps + warp deals them evenly over the warps.
+        int nu = 0;
+        for (int pass = 0; pass < 2; ++pass)
+            for (int slot = 0; slot < S; ++slot)
+                for (int sr = rb0; sr < rb1; ++sr) {
+                    const int len = N - sr % N;
+                    for (int c = 0; c * 32 < len; ++c)
+                        if ((c < a.fast_chunk) == (pass == 0))
+                            s_units[nu++] = (uint32_t)c | ((uint32_t)sr << 3) | ((uint32_t)slot << 12);
+                }
+        h->n_units = nu;
     }
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         s_nbr[i] = a.nbr[i];
         for (int n = 0; n < 4; ++n) s_t[4 * i + n] = a.tnb[4 * i + n];
     }
-    // shared::cluster address of element (p, p) of every spin-row, buffer A
-    for (int idx = threadIdx.x; idx < S * 2 * N; idx += blockDim.x) {
-        const int slot = idx / (2 * N), sr = idx % (2 * N);
+    // row bases (slot 0, buffer A)
+    for (int sr = threadIdx.x; sr < twoN; sr += blockDim.x) {
         int owner = 0;
         while (owner + 1 < C && sr >= a.row_begin[owner + 1]) ++owner;
-        int e_slot = 0, off = 0;
-        for (int x = a.row_begin[owner]; x < a.row_begin[owner + 1]; ++x) {
-            if (x < sr) off += N - (x % N);
-            e_slot += N - (x % N);
+        int off = 0;
+        for (int x = a.row_begin[owner]; x < sr; ++x) off += N - (x % N);
+        const int p = sr % N;
+        // map the row's first stored element (p, p), then shift by -p so that
+        // (p, q) is at base + q * SZ (only q >= p is ever addressed)
+        const uint32_t start = bufA_s + (uint32_t)(off * SZ);
+        s_rowbase[sr] = (CLUSTER ? map_rank(start, owner) : start) - (uint32_t)(p * SZ);
+    }
+    __syncthreads();
+    for (int sr = threadIdx.x; sr < twoN; sr += blockDim.x) {
+        const int s = sr / N, p = sr % N;
+        RowDesc d;
+        d.p = p;
+        d.nbp = s_nbr[p];
+        d.deg = (d.nbp >> 24) & 0xFF;
+        d.remote = 0;
+        for (int n = 0; n < 3; ++n) {
+            const int k = (d.nbp >> (8 * n)) & 0xFF, r = s * N + k;
+            int owner = 0;
+            while (owner + 1 < C && r >= a.row_begin[owner + 1]) ++owner;
+            d.base_kc[n] = s_rowbase[r];
+            if (CLUSTER && owner != (int)rank) {
+                d.base_k[n] = s_rowbase[r];
+                d.remote |= 1 << n;
+            } else {
+                int off = 0;
+                for (int x = rb0; x < r; ++x) off += N - (x % N);
+                d.base_k[n] = bufA_s + (uint32_t)(off * SZ) - (uint32_t)(k * SZ);
+            }
         }
-        const uint32_t local = bufA_s + (uint32_t)((slot * e_slot + off) * (int)sizeof(V));
-        s_row[idx] = CLUSTER ? map_rank(local, owner) : local;
+        int off = 0;
+        for (int x = rb0; x < sr && x < rb1; ++x) off += N - (x % N);
+        d.base_local = bufA_s + (uint32_t)(off * SZ) - (uint32_t)(p * SZ);
+        d.pad = 0;
+        s_desc[sr] = d;
     }
     if (warp == 0) {
         tmem_alloc(smem_addr(&h->tmem_base), kTmemCols);
@@ -144,28 +399,8 @@ __global__ void __launch_bounds__(kThreads, 1) rk4_stepper(const StepArgs<T> a)
     tmem_fence_after();
     if constexpr (CLUSTER) cluster_sync_hw();   // barrier inits visible cluster-wide
 
-    const uint32_t tbase = h->tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(128 * (warp >> 2));
-    constexpr int WC = sizeof(V) / 4;           // tensor-memory words per complex value
-    const int E = a.E;
-    const uint32_t t_meta = tbase, t_y0 = tbase + a.meta_cols, t_acc = tbase + a.meta_cols + E * WC;
-
-    // ---- per-element metadata into tensor memory -----------------------------
-    for (int j = 0; j < E; ++j) {
-        const int e = (j * kWarps + warp) * 32 + lane;
-        uint32_t meta = 0xFFFFFFFFu;
-        if (e < n_elem) {
-            const int slot = e / eps;
-            int rem = e - slot * eps, sr = rb0;
-            while (rem >= N - (sr % N)) {
-                rem -= N - (sr % N);
-                ++sr;
-            }
-            const int p = sr % N, q = p + rem, s = sr / N;
-            meta = (uint32_t)q | ((uint32_t)p << 8) | ((uint32_t)s << 16) | ((uint32_t)slot << 17);
-        }
-        tmem_st1(t_meta + j, meta);
-    }
-    tmem_wait_st();
+    const int n_units = h->n_units;
+    const uint32_t t_state = h->tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(kTmemColsPerWarp * (warp >> 2));
 
     uint32_t phase = 0;
     const unsigned long long limit = a.timeout_ns;
@@ -179,41 +414,41 @@ __global__ void __launch_bounds__(kThreads, 1) rk4_stepper(const StepArgs<T> a)
     }
 
     const long long n_batches = (a.M + S - 1) / S;
-    const int twoN = 2 * N;
-    const T half_dt = a.dt * T(0.5), sixth_dt = a.dt / T(6);
-
     for (long long b = cid; b < n_batches && h->abort == 0; b += ncl) {
         // ---- load rho(0) ---------------------------------------------------------
-        for (int j = 0; j < E; ++j) {
+        for (int j = 0; j < a.E; ++j) {
+            const int u = j * kWarps + warp;
             __syncwarp();
-            const uint32_t meta = tmem_get1(t_meta + j);
             V v;
             v.x = T(0);
             v.y = T(0);
-            if (meta != 0xFFFFFFFFu) {
-                const int q = meta & 0xFF, p = (meta >> 8) & 0xFF, s = (meta >> 16) & 1, slot = meta >> 17;
-                const long long m = b * S + slot;
-                if (m < a.M) {
-                    v = a.rho[((m * 2 + s) * N + p) * (long long)N + q];
-                    if (p == q) {
-                        v.y = T(0);
-                        if (a.snap) a.snap[m * twoN + s * N + p] = v.x;
+            if (u < n_units) {
+                const uint32_t unit = s_units[u];
+                const int chunk = unit & 7, sr = (unit >> 3) & 511, slot = unit >> 12;
+                const int p = sr % N, s = sr / N, q = p + 32 * chunk + lane;
+                if (q < N) {
+                    const long long m = b * S + slot;
+                    if (m < a.M) {
+                        v = a.rho[((m * 2 + s) * N + p) * (long long)N + q];
+                        if (q == p) {
+                            v.y = T(0);
+                            if (a.snap) a.snap[m * twoN + s * N + p] = v.x;
+                        }
                     }
-                }
-                const int e = (j * kWarps + warp) * 32 + lane;
-                sts2(bufA_s + (uint32_t)(e * (int)sizeof(V)), v);
-                if (p == q) {
-                    const uint32_t d = diag_s + (uint32_t)((slot * twoN + s * N + p) * (int)sizeof(T));
-                    if constexpr (CLUSTER) {
-                        for (int r = 0; r < C; ++r) stc1(map_rank(d, r), v.x);
-                    } else {
-                        s_diag[slot * twoN + s * N + p] = v.x;
-                        (void)d;
+                    sts2(s_desc[sr].base_local + (uint32_t)(slot * eps_bytes + q * SZ), v);
+                    if (q == p) {
+                        const int di = slot * twoN + s * N + p;
+                        if constexpr (CLUSTER) {
+                            const uint32_t da = diag_s + (uint32_t)(di * (int)sizeof(T));
+                            for (int r = 0; r < C; ++r) stc1(map_rank(da, r), v.x);
+                        } else {
+                            s_diag[di] = v.x;
+                        }
                     }
                 }
             }
             __syncwarp();
-            tmem_put(t_y0 + j * WC, v);
+            tmem_put(t_state + (uint32_t)(j * 2 * WC), v);
         }
         tmem_wait_st();
         if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
@@ -222,110 +457,37 @@ __global__ void __launch_bounds__(kThreads, 1) rk4_stepper(const StepArgs<T> a)
         for (long long step = 0; step < a.n_steps && h->abort == 0; ++step) {
             const bool snap_now = a.snap && ((step + 1) % a.out_every == 0);
             const long long snap_row = (step + 1) / a.out_every;
-            for (int stage = 0; stage < 4; ++stage) {
-                const int cur = stage & 1;               // buffer read in this stage
-                const uint32_t boff_cur = cur ? (uint32_t)a.buf_bytes : 0u;
-                const uint32_t boff_nxt = cur ? 0u : (uint32_t)a.buf_bytes;
-                const T *dg = s_diag + cur * diag_stride;
-                for (int j = 0; j < E; ++j) {
-                    __syncwarp();
-                    const uint32_t meta = tmem_get1(t_meta + j);
-                    V y0, acc;
-                    tmem_get(t_y0 + j * WC, y0);
-                    if (stage > 0) tmem_get(t_acc + j * WC, acc);
-                    else acc = y0;
-                    if (meta != 0xFFFFFFFFu) {
-                        const int q = meta & 0xFF, p = (meta >> 8) & 0xFF, s = (meta >> 16) & 1, slot = meta >> 17;
-                        const int e = (j * kWarps + warp) * 32 + lane;
-                        const V own = lds2(bufA_s + boff_cur + (uint32_t)(e * (int)sizeof(V)), T());
-                        const uint32_t *rows = s_row + slot * twoN + s * N;
-                        const int nq = s_nbr[q], np = s_nbr[p];
-                        T hr = T(0), hi = T(0);
-                        // + sum_{k in nb(q)} t_qk rho_pk
-#pragma unroll
-                        for (int n = 0; n < 3; ++n) {
-                            const int k = (nq >> (8 * n)) & 0xFF;
-                            const T t = s_t[4 * q + n];
-                            const bool fwd = k >= p;
-                            const uint32_t ad =
-                                rows[fwd ? p : k] + boff_cur + (uint32_t)((fwd ? k - p : p - k) * (int)sizeof(V));
-                            const V v = CLUSTER ? ldc2(ad, T()) : lds2(ad, T());
-                            hr = fma(t, v.x, hr);
-                            hi = fma(t, fwd ? v.y : -v.y, hi);
-                        }
-                        // - sum_{k in nb(p)} t_pk rho_kq
-#pragma unroll
-                        for (int n = 0; n < 3; ++n) {
-                            const int k = (np >> (8 * n)) & 0xFF;
-                            const T t = s_t[4 * p + n];
-                            const bool fwd = k <= q;
-                            const uint32_t ad =
-                                rows[fwd ? k : q] + boff_cur + (uint32_t)((fwd ? q - k : k - q) * (int)sizeof(V));
-                            const V v = CLUSTER ? ldc2(ad, T()) : lds2(ad, T());
-                            hr = fma(-t, v.x, hr);
-                            hi = fma(-t, fwd ? v.y : -v.y, hi);
-                        }
-                        // + U (Re rho_pp,sbar - Re rho_qq,sbar) rho_pq
-                        const T *db = dg + slot * twoN + (1 - s) * N;
-                        const T g = a.U * (db[p] - db[q]);
-                        hr = fma(g, own.x, hr);
-                        hi = fma(g, own.y, hi);
-                        // k = i (hr + i hi); on the diagonal Eq. 9 is real, so its
-                        // imaginary part (pure rounding residue) is dropped
-                        const T kx = -hi, ky = (p == q) ? T(0) : hr;
-                        V nxt;
-                        if (stage == 0) {
-                            acc.x = kx;
-                            acc.y = ky;
-                            nxt.x = fma(half_dt, kx, y0.x);
-                            nxt.y = fma(half_dt, ky, y0.y);
-                        } else if (stage < 3) {
-                            acc.x = fma(T(2), kx, acc.x);
-                            acc.y = fma(T(2), ky, acc.y);
-                            const T c = stage == 1 ? half_dt : a.dt;
-                            nxt.x = fma(c, kx, y0.x);
-                            nxt.y = fma(c, ky, y0.y);
-                        } else {
-                            nxt.x = fma(sixth_dt, acc.x + kx, y0.x);
-                            nxt.y = fma(sixth_dt, acc.y + ky, y0.y);
-                            y0 = nxt;
-                        }
-                        sts2(bufA_s + boff_nxt + (uint32_t)(e * (int)sizeof(V)), nxt);
-                        if (p == q) {
-                            const uint32_t d =
-                                diag_s + (uint32_t)(((cur ^ 1) * diag_stride + slot * twoN + s * N + p) * (int)sizeof(T));
-                            if constexpr (CLUSTER) {
-                                for (int r = 0; r < C; ++r) stc1(map_rank(d, r), nxt.x);
-                            } else {
-                                s_diag[(cur ^ 1) * diag_stride + slot * twoN + s * N + p] = nxt.x;
-                                (void)d;
-                            }
-                            if (stage == 3 && snap_now) {
-                                const long long m = b * S + slot;
-                                if (m < a.M) a.snap[(snap_row * a.M + m) * twoN + s * N + p] = nxt.x;
-                            }
-                        }
-                    }
-                    __syncwarp();
-                    if (stage < 3) tmem_put(t_acc + j * WC, acc);
-                    else tmem_put(t_y0 + j * WC, y0);
-                }
-                tmem_wait_st();
-                if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
-            }
+            rk4_stage<0, T, CLUSTER, UNIFORM_T>(a, s_desc, s_rowbase, s_units, s_nbr, s_t, s_diag, diag_s, n_units,
+                                                warp, lane, t_state, eps_bytes, diag_stride, b, snap_now, snap_row);
+            tmem_wait_st();
+            if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
+            rk4_stage<1, T, CLUSTER, UNIFORM_T>(a, s_desc, s_rowbase, s_units, s_nbr, s_t, s_diag, diag_s, n_units,
+                                                warp, lane, t_state, eps_bytes, diag_stride, b, snap_now, snap_row);
+            tmem_wait_st();
+            if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
+            rk4_stage<2, T, CLUSTER, UNIFORM_T>(a, s_desc, s_rowbase, s_units, s_nbr, s_t, s_diag, diag_s, n_units,
+                                                warp, lane, t_state, eps_bytes, diag_stride, b, snap_now, snap_row);
+            tmem_wait_st();
+            if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
+            rk4_stage<3, T, CLUSTER, UNIFORM_T>(a, s_desc, s_rowbase, s_units, s_nbr, s_t, s_diag, diag_s, n_units,
+                                                warp, lane, t_state, eps_bytes, diag_stride, b, snap_now, snap_row);
+            tmem_wait_st();
+            if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
         }
         if (h->abort) break;
 
         // ---- write back rho(T) (full Hermitian matrix) ------------------------------
-        for (int j = 0; j < E; ++j) {
+        for (int j = 0; j < a.E; ++j) {
+            const int u = j * kWarps + warp;
             __syncwarp();
-            const uint32_t meta = tmem_get1(t_meta + j);
             V y0;
-            tmem_get(t_y0 + j * WC, y0);
-            if (meta == 0xFFFFFFFFu) continue;
-            const int q = meta & 0xFF, p = (meta >> 8) & 0xFF, s = (meta >> 16) & 1, slot = meta >> 17;
+            tmem_get(t_state + (uint32_t)(j * 2 * WC), y0);
+            if (u >= n_units) continue;
+            const uint32_t unit = s_units[u];
+            const int chunk = unit & 7, sr = (unit >> 3) & 511, slot = unit >> 12;
+            const int p = sr % N, s = sr / N, q = p + 32 * chunk + lane;
             const long long m = b * S + slot;
-            if (m >= a.M) continue;
+            if (q >= N || m >= a.M) continue;
             if (!(isfinite(y0.x) && isfinite(y0.y))) record_status(a.status, FTWA_ERR_NONFINITE);
             a.rho[((m * 2 + s) * N + p) * (long long)N + q] = y0;
             if (p != q) {
@@ -350,28 +512,35 @@ __global__ void __launch_bounds__(kThreads, 1) rk4_stepper(const StepArgs<T> a)
 // ---------------------------------------------------------------------------
 // Host side: launch-shape selection and launch.
 // ---------------------------------------------------------------------------
-static int smem_needed(int N, int S, int elem_bytes, int real_bytes, int buf_bytes)
+static int smem_needed(int N, int S, int real_bytes, int n_units, int buf_bytes)
 {
-    int b = 64 + 4 * 256 + real_bytes * 4 * 256;
-    b += ((4 * S * 2 * N + 15) / 16) * 16;
+    int b = 64 + 4 * 256 + real_bytes * 4 * 256 + (int)sizeof(RowDesc) * 2 * 256 + 4 * 2 * 256;
+    b += 4 * ((n_units + 3) / 4) * 4;
     b += ((real_bytes * 2 * S * 2 * N + 15) / 16) * 16;
     b += 2 * buf_bytes;
-    (void)elem_bytes;
     return b;
 }
 
-// Split the 2N spin-rows (row p of spin s has N - p packed elements) into C
-// contiguous ranges with balanced element counts.
-static void split_rows(int N, int C, int *rb)
+// Split the 2N spin-rows into C contiguous ranges of balanced cost.  Row p of
+// spin s has N - p packed elements in ceil((N - p)/32) work units; units next
+// to the diagonal take the slower conj-reading path, weighted 1.5.
+static double row_cost(int N, int sr, int fast_chunk)
 {
-    const long long total = (long long)N * (N + 1);
+    const int len = N - sr % N, units = (len + 31) / 32;
+    return units + 0.5 * std::min(units, fast_chunk);
+}
+
+static void split_rows(int N, int C, int fast_chunk, int *rb)
+{
+    double total = 0;
+    for (int sr = 0; sr < 2 * N; ++sr) total += row_cost(N, sr, fast_chunk);
     rb[0] = 0;
     int sr = 0;
-    long long acc = 0;
+    double acc = 0;
     for (int r = 1; r < C; ++r) {
-        const long long target = total * r / C;
-        while (sr < 2 * N && acc + (N - sr % N) / 2 < target) {
-            acc += N - sr % N;
+        const double target = total * r / C;
+        while (sr < 2 * N && acc + 0.5 * row_cost(N, sr, fast_chunk) < target) {
+            acc += row_cost(N, sr, fast_chunk);
             ++sr;
         }
         rb[r] = sr;
@@ -391,12 +560,16 @@ int choose_stepper_shape(Plan *p, int64_t M, StepperShape *out)
         if (p->cluster_override && C != p->cluster_override) continue;
         StepperShape sh;
         sh.cluster = C;
-        split_rows(N, C, sh.row_begin);
-        int eps_max = 0;
+        split_rows(N, C, (p->bandwidth + 31) / 32, sh.row_begin);
+        int eps_max = 0, upr_max = 0;   // elements and 32-column units per slot, max over ranks
         for (int r = 0; r < C; ++r) {
-            int eps = 0;
-            for (int sr = sh.row_begin[r]; sr < sh.row_begin[r + 1]; ++sr) eps += N - sr % N;
+            int eps = 0, upr = 0;
+            for (int sr = sh.row_begin[r]; sr < sh.row_begin[r + 1]; ++sr) {
+                eps += N - sr % N;
+                upr += (N - sr % N + 31) / 32;
+            }
             eps_max = std::max(eps_max, eps);
+            upr_max = std::max(upr_max, upr);
         }
         if (eps_max == 0) continue;
         // slots: as many samples per CTA as useful (C == 1 only), bounded by
@@ -408,21 +581,19 @@ int choose_stepper_shape(Plan *p, int64_t M, StepperShape *out)
         }
         int best = 0;
         for (int S = 1; S <= want; ++S) {
-            const int units = (S * eps_max + 31) / 32;
+            const int units = S * upr_max;
             const int E = (units + kWarps - 1) / kWarps;
-            const int meta_cols = ((E + 3) / 4) * 4;
-            if (meta_cols + 2 * E * WC > 128) break;
+            if (2 * E * WC > kTmemColsPerWarp) break;
             const int buf = ((S * eps_max * elem_bytes + 15) / 16) * 16;
-            if (smem_needed(N, S, elem_bytes, real_bytes, buf) > max_smem) break;
+            if (smem_needed(N, S, real_bytes, units, buf) > max_smem) break;
             best = S;
         }
         if (best == 0) continue;
         sh.slots = best;
-        const int units = (best * eps_max + 31) / 32;
-        sh.units_per_warp = (units + kWarps - 1) / kWarps;
-        sh.meta_cols = ((sh.units_per_warp + 3) / 4) * 4;
+        sh.n_units = best * upr_max;
+        sh.units_per_warp = (sh.n_units + kWarps - 1) / kWarps;
         sh.buf_bytes = ((best * eps_max * elem_bytes + 15) / 16) * 16;
-        sh.smem_bytes = std::max(kMinSmem, smem_needed(N, best, elem_bytes, real_bytes, sh.buf_bytes));
+        sh.smem_bytes = std::max(kMinSmem, smem_needed(N, best, real_bytes, sh.n_units, sh.buf_bytes));
         const long long batches = (M + best - 1) / best;
         const int max_groups = std::max(1, sm / C);
         sh.grid = (int)std::min<long long>(std::max<long long>(batches, 1), max_groups) * C;
@@ -432,7 +603,7 @@ int choose_stepper_shape(Plan *p, int64_t M, StepperShape *out)
     return FTWA_ERR_UNSUPPORTED;
 }
 
-template <typename T, bool CLUSTER>
+template <typename T, bool CLUSTER, bool UNIFORM_T>
 static int launch_t(Plan *p, const StepperShape &sh, void *rho, int64_t M, int64_t n_steps, void *snap,
                     cudaStream_t s)
 {
@@ -442,12 +613,14 @@ static int launch_t(Plan *p, const StepperShape &sh, void *rho, int64_t M, int64
                                            : reinterpret_cast<const T *>(p->d_t32);
     a.U = (T)p->U;
     a.dt = (T)p->dt;
+    a.t_uniform = p->t_bond.empty() ? T(0) : (T)p->t_bond[0];
     a.N = p->N;
     a.C = sh.cluster;
     a.S = sh.slots;
     a.E = sh.units_per_warp;
-    a.meta_cols = sh.meta_cols;
     a.buf_bytes = sh.buf_bytes;
+    a.n_units_max = sh.n_units;
+    a.fast_chunk = (p->bandwidth + 31) / 32;
     for (int i = 0; i <= kMaxCluster; ++i) a.row_begin[i] = sh.row_begin[i];
     a.M = M;
     a.n_steps = n_steps;
@@ -457,7 +630,7 @@ static int launch_t(Plan *p, const StepperShape &sh, void *rho, int64_t M, int64
     a.status = p->d_status;
     a.timeout_ns = p->timeout_ns;
     a.force_timeout = p->force_timeout;
-    auto kern = rk4_stepper<T, CLUSTER>;
+    auto kern = rk4_stepper<T, CLUSTER, UNIFORM_T>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem_bytes);
     if (e != cudaSuccess) return set_cuda_error(e);
     cudaLaunchConfig_t cfg{};
@@ -481,13 +654,14 @@ static int launch_t(Plan *p, const StepperShape &sh, void *rho, int64_t M, int64
     return FTWA_OK;
 }
 
-int launch_evolve(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s)
+template <typename T, bool CLUSTER>
+static int dispatch_t(Plan *p, StepperShape &sh, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s)
 {
-    StepperShape sh;
-    int rc = choose_stepper_shape(p, M, &sh);
-    if (rc != FTWA_OK) return rc;
-    if (sh.cluster > 1) {
+    if (CLUSTER) {
         // clamp the grid to the clusters that can be co-resident
+        auto kern = p->uniform_t ? rk4_stepper<T, true, true> : rk4_stepper<T, true, false>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem_bytes);
+        if (e != cudaSuccess) return set_cuda_error(e);
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(sh.grid, 1, 1);
         cfg.blockDim = dim3(kThreads, 1, 1);
@@ -500,25 +674,27 @@ int launch_evolve(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cu
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int n_clusters = 0;
-        cudaError_t e;
-        if (p->precision == FTWA_FP64) {
-            e = cudaFuncSetAttribute(rk4_stepper<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem_bytes);
-            if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n_clusters, rk4_stepper<double, true>, &cfg);
-        } else {
-            e = cudaFuncSetAttribute(rk4_stepper<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem_bytes);
-            if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n_clusters, rk4_stepper<float, true>, &cfg);
-        }
+        e = cudaOccupancyMaxActiveClusters(&n_clusters, kern, &cfg);
         if (e != cudaSuccess) return set_cuda_error(e);
         if (n_clusters < 1) return FTWA_ERR_UNSUPPORTED;
         sh.grid = std::min(sh.grid, n_clusters * sh.cluster);
     }
     p->shape = sh;
     if (M == 0) return FTWA_OK;
+    return p->uniform_t ? launch_t<T, CLUSTER, true>(p, sh, rho, M, n_steps, snap, s)
+                        : launch_t<T, CLUSTER, false>(p, sh, rho, M, n_steps, snap, s);
+}
+
+int launch_evolve(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s)
+{
+    StepperShape sh;
+    int rc = choose_stepper_shape(p, M, &sh);
+    if (rc != FTWA_OK) return rc;
     if (p->precision == FTWA_FP64)
-        return sh.cluster > 1 ? launch_t<double, true>(p, sh, rho, M, n_steps, snap, s)
-                              : launch_t<double, false>(p, sh, rho, M, n_steps, snap, s);
-    return sh.cluster > 1 ? launch_t<float, true>(p, sh, rho, M, n_steps, snap, s)
-                          : launch_t<float, false>(p, sh, rho, M, n_steps, snap, s);
+        return sh.cluster > 1 ? dispatch_t<double, true>(p, sh, rho, M, n_steps, snap, s)
+                              : dispatch_t<double, false>(p, sh, rho, M, n_steps, snap, s);
+    return sh.cluster > 1 ? dispatch_t<float, true>(p, sh, rho, M, n_steps, snap, s)
+                          : dispatch_t<float, false>(p, sh, rho, M, n_steps, snap, s);
 }
 
 }  // namespace ftwa

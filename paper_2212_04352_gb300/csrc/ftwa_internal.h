@@ -10,17 +10,20 @@
 namespace ftwa {
 
 constexpr int kMaxCluster = 8;
-constexpr int kThreads = 512;          // threads per CTA of the stepper
+constexpr int kThreads = 768;          // threads per CTA of the stepper
 constexpr int kWarps = kThreads / 32;
 constexpr int kTmemCols = 512;         // one CTA per SM holds all of tensor memory
+// tensor-memory columns of one warp: warps w, w+4, ... share lane quadrant
+// w % 4 and split the 512 columns (multiple of 8 for aligned x8 accesses)
+constexpr int kTmemColsPerWarp = (kTmemCols / (kWarps / 4)) / 8 * 8;
 constexpr int kMinSmem = 120 * 1024;   // forces one stepper CTA per SM
 
 // Launch shape of the RK4 stepper for one slot count.
 struct StepperShape {
     int cluster = 1;        // CTAs per sample group
     int slots = 1;          // samples per cluster (cluster == 1 only)
-    int units_per_warp = 0; // E: 32-element work units per warp
-    int meta_cols = 0;      // tensor-memory columns of the metadata block
+    int units_per_warp = 0; // E: 32-column work units per warp
+    int n_units = 0;        // work units of the busiest rank
     int smem_bytes = 0;
     int buf_bytes = 0;      // bytes of one stage buffer (max over ranks)
     int row_begin[kMaxCluster + 1] = {0};  // spin-row partition over ranks
@@ -38,6 +41,7 @@ struct Plan {
     int force_timeout = 0;
     int sm_count = 0;
     bool uniform_t = true;
+    int bandwidth = 1;                // max over bonds of j - i (site ordering)
     std::vector<int32_t> bonds;       // [B][2]
     std::vector<double> t_bond;       // [B]
     std::vector<double> n_up, n_dn;   // [N]

@@ -158,6 +158,8 @@ int ftwa_plan(const ftwa_lattice *lat, double U, double t, double filling, const
             return FTWA_ERR_UNSUPPORTED;
         }
     }
+    p->bandwidth = 1;
+    for (int b = 0; b < B; ++b) p->bandwidth = std::max(p->bandwidth, p->bonds[2 * b + 1] - p->bonds[2 * b]);
     p->uniform_t = true;
     for (int b = 1; b < B; ++b) p->uniform_t = p->uniform_t && p->t_bond[b] == p->t_bond[0];
 

@@ -94,10 +94,13 @@ typedef struct {
     double dt;                /* RK4 step in units of hbar/t (> 0)            */
     int32_t out_every;        /* snapshot cadence in steps (>= 1)             */
     int32_t cluster_override; /* CTAs per sample (1..8), 0 = automatic         */
-    int32_t threads_override; /* threads per CTA (128..1024, multiple of 128)  */
+    int32_t threads_override; /* threads per CTA: 0 (automatic) or 768         */
     int32_t autotune;         /* 1 = time candidate shapes on first evolve     */
     uint64_t timeout_us;      /* limit of every bounded in-kernel wait in
                                  microseconds, 0 = default (5 s)             */
+    int32_t variant;          /* stepper: 0 automatic, 1 banded (rows keep a
+                                 mirror band of width = lattice bandwidth),
+                                 2 general packed triangle                   */
 } ftwa_options;
 
 /* Launch shape chosen by the plan (for reporting and tests). */
@@ -110,6 +113,7 @@ typedef struct {
     int32_t tmem_cols;        /* tensor-memory columns per CTA                */
     int32_t grid_clusters;    /* persistent clusters launched                 */
     int32_t units_per_warp;   /* 32-lane work units per warp and sample slot  */
+    int32_t variant;          /* stepper chosen: 1 banded, 2 general          */
 } ftwa_plan_info;
 
 /* Create a plan: validates the lattice and initial state, builds the

@@ -39,13 +39,13 @@ class InitState(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("dt", ctypes.c_double), ("out_every", ctypes.c_int32),
                 ("cluster_override", ctypes.c_int32), ("threads_override", ctypes.c_int32),
-                ("autotune", ctypes.c_int32), ("timeout_us", ctypes.c_uint64)]
+                ("autotune", ctypes.c_int32), ("timeout_us", ctypes.c_uint64), ("variant", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in
                 ("n_sites", "n_bonds", "precision", "cluster", "threads", "samples_per_cta", "smem_bytes",
-                 "tmem_cols", "grid_clusters", "units_per_warp")]
+                 "tmem_cols", "grid_clusters", "units_per_warp", "variant")]
 
 
 class FtwaError(RuntimeError):

@@ -133,6 +133,20 @@ __device__ __forceinline__ void tmem_wait_ld_regs(uint32_t (&w)[2 * WC])
                      :: "memory");
     }
 }
+template <int WC>
+__device__ __forceinline__ void tmem_wait_ld_regs2(uint32_t (&w)[2 * WC], uint32_t (&v)[2 * WC])
+{
+    if constexpr (WC == 2) {
+        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                     : "+r"(w[0]), "+r"(w[1]), "+r"(w[2]), "+r"(w[3]), "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3])
+                     :: "memory");
+    } else {
+        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                     : "+r"(w[0]), "+r"(w[1]), "+r"(w[2]), "+r"(w[3]), "+r"(w[4]), "+r"(w[5]), "+r"(w[6]), "+r"(w[7]),
+                       "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7])
+                     :: "memory");
+    }
+}
 template <int WC, typename V>
 __device__ __forceinline__ void unpack_state(const uint32_t (&w)[2 * WC], V &y0, V &acc)
 {
@@ -510,6 +524,414 @@ __global__ void __launch_bounds__(kThreads, 1) rk4_stepper(const StepArgs<T> a)
 }
 
 // ---------------------------------------------------------------------------
+// Banded stepper.  Used when the site ordering has a small bandwidth bw (max
+// |i - j| over bonds), as for honeycomb flakes numbered row by row.
+//  - Every spin-row p stores columns [max(0, p - bw), N): the upper triangle
+//    plus a mirror band of bw entries below the diagonal, kept equal to
+//    conj of the transposed entries.  Every read of Eq. 9 is then a direct
+//    load; no conjugated reads near the diagonal.
+//  - A lane owns one column q = 32 b + lane of a column block b and walks the
+//    rows of its work items, so the column's neighbour offsets, hoppings,
+//    other-spin diagonal entry and mirror address stay in registers.
+//  - Work items (runs of rows of one spin, one column block) are assigned to
+//    warps on the host (longest-processing-time first).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct BandArgs {
+    const int32_t *nbr;
+    const T *tnb;
+    T U, dt, t_uniform;
+    int N, bw, C, S, E, k_items, buf_bytes;
+    int row_begin[kMaxCluster + 1];
+    const uint32_t *items;      // [C][kWarps][k_items]: count | b << 6 | sr << 9 | slot << 18
+    long long M, n_steps;
+    int out_every;
+    typename C2<T>::type *rho;
+    T *snap;
+    int *status;
+    unsigned long long timeout_ns;
+    int force_timeout;
+};
+
+struct __align__(16) BandRow {
+    uint32_t base_local;   // own row p: element (p, k) at base_local + k * SZ (shared::cta)
+    uint32_t base_k[3];    // neighbour rows: shared::cluster addresses in a cluster, else shared::cta
+    int32_t p, deg, pad0, pad1;
+};
+
+__device__ __forceinline__ void cfma(float t, float2 v, float2 &acc) { acc = __ffma2_rn(make_float2(t, t), v, acc); }
+__device__ __forceinline__ void cfma(double t, double2 v, double2 &acc)
+{
+    acc.x = fma(t, v.x, acc.x);
+    acc.y = fma(t, v.y, acc.y);
+}
+
+template <int STAGE, typename T, bool CLUSTER, bool UNIFORM_T>
+__device__ __forceinline__ void band_stage(unsigned char *smem, const BandArgs<T> &a, const BandRow *s_row,
+                                           const uint32_t *s_rowbase,
+                                           const uint32_t *my_items, const int32_t *s_nbr, const T *s_t, T *s_diag,
+                                           uint32_t diag_s, int lane, uint32_t t_state, int eps_bytes,
+                                           int diag_stride, long long b, bool snap_now, long long snap_row)
+{
+    using V = typename C2<T>::type;
+    constexpr int SZ = sizeof(V);
+    constexpr int WC = SZ / 4;
+    constexpr int CUR = STAGE & 1;
+    const int N = a.N, twoN = 2 * N;
+    const uint32_t boff_cur = CUR ? (uint32_t)a.buf_bytes : 0u;
+    const uint32_t boff_nxt = CUR ? 0u : (uint32_t)a.buf_bytes;
+    const T *dg = s_diag + CUR * diag_stride;
+    const T half_dt = a.dt * T(0.5), sixth_dt = a.dt / T(6);
+    // local shared-memory accesses go through the __shared__ array (plain
+    // loads the compiler can schedule); cluster accesses use PTX
+    const uint32_t sbase = smem_addr(smem);
+    auto ld_local = [&](uint32_t addr) -> V { return *reinterpret_cast<const V *>(smem + (addr - sbase)); };
+    auto st_local = [&](uint32_t addr, V v) { *reinterpret_cast<V *>(smem + (addr - sbase)) = v; };
+    int e = 0;
+    for (int it = 0; it < a.k_items; ++it) {
+        const uint32_t item = my_items[it];
+        if (item == 0xFFFFFFFFu) break;
+        const int count = item & 63, blk = (item >> 6) & 7, sr0 = (item >> 9) & 511, slot = item >> 18;
+        const int s = sr0 >= N ? 1 : 0;
+        const int q = 32 * blk + lane;
+        const bool qa = q < N;
+        const int qc = qa ? q : N - 1;
+        // per-column registers for the whole item
+        const int nq = s_nbr[qc];
+        uint32_t koff[3];
+        T tq[3];
+#pragma unroll
+        for (int n = 0; n < 3; ++n) {
+            koff[n] = (uint32_t)(((nq >> (8 * n)) & 0xFF) * SZ);
+            tq[n] = UNIFORM_T ? (n < (nq >> 24) ? a.t_uniform : T(0)) : s_t[4 * qc + n];
+        }
+        const uint32_t soff = (uint32_t)(slot * eps_bytes);
+        const uint32_t qsz = (uint32_t)(qc * SZ);
+        const uint32_t mirror = s_rowbase[s * N + qc] + soff + boff_nxt;
+        const T *dgo = dg + slot * twoN + (1 - s) * N;       // other spin's diagonal
+        const T dq = dgo[qc];
+        // rows are processed two at a time: independent work for the same warp
+        for (int r = 0; r < count; r += 2, e += 2) {
+            const bool two = r + 1 < count;
+            const int e1 = two ? e + 1 : e;
+            uint32_t w0[2 * WC], w1[2 * WC];
+            __syncwarp();
+            tmem_ld_state<WC>(t_state + (uint32_t)(e * 2 * WC), w0);
+            tmem_ld_state<WC>(t_state + (uint32_t)(e1 * 2 * WC), w1);
+            tmem_wait_ld_regs2<WC>(w0, w1);
+            V y0[2], acc[2];
+            unpack_state<WC>(w0, y0[0], acc[0]);
+            unpack_state<WC>(w1, y0[1], acc[1]);
+            const BandRow d0 = s_row[sr0 + r];
+            const BandRow d1 = s_row[sr0 + (two ? r + 1 : r)];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const BandRow &d = i == 0 ? d0 : d1;
+                const int p = d.p;
+                // every lane computes (inactive lanes on clamped, valid
+                // addresses); only the stores are predicated
+                const bool active = qa && q >= p && (i == 0 || two);
+                const uint32_t rb = d.base_local + soff + boff_cur;
+                const V own = lds2(rb + qsz, T());
+                V h;
+                h.x = T(0);
+                h.y = T(0);
+                // + sum_{k in nb(q)} t_qk rho_pk   (row p, this CTA)
+#pragma unroll
+                for (int n = 0; n < 3; ++n) cfma(tq[n], lds2(rb + koff[n], T()), h);
+                // - sum_{k in nb(p)} t_pk rho_kq
+#pragma unroll
+                for (int n = 0; n < 3; ++n) {
+                    const T t = UNIFORM_T ? (n < d.deg ? a.t_uniform : T(0)) : s_t[4 * p + n];
+                    const uint32_t ad = d.base_k[n] + soff + boff_cur + qsz;
+                    cfma(-t, CLUSTER ? ldc2(ad, T()) : lds2(ad, T()), h);
+                }
+                // + U (Re rho_pp,sbar - Re rho_qq,sbar) rho_pq
+                cfma(a.U * (dgo[p] - dq), own, h);
+                // k = i h; the diagonal of Eq. 9 is real (its imaginary part is
+                // rounding residue and is dropped)
+                V kk;
+                kk.x = -h.y;
+                kk.y = (q == p) ? T(0) : h.x;
+                V nxt;
+                if constexpr (STAGE == 0) {
+                    acc[i] = kk;
+                    nxt.x = fma(half_dt, kk.x, y0[i].x);
+                    nxt.y = fma(half_dt, kk.y, y0[i].y);
+                } else if constexpr (STAGE < 3) {
+                    acc[i].x = fma(T(2), kk.x, acc[i].x);
+                    acc[i].y = fma(T(2), kk.y, acc[i].y);
+                    const T c = STAGE == 1 ? half_dt : a.dt;
+                    nxt.x = fma(c, kk.x, y0[i].x);
+                    nxt.y = fma(c, kk.y, y0[i].y);
+                } else {
+                    nxt.x = fma(sixth_dt, acc[i].x + kk.x, y0[i].x);
+                    nxt.y = fma(sixth_dt, acc[i].y + kk.y, y0[i].y);
+                    y0[i] = nxt;
+                }
+                if (active) sts2(d.base_local + soff + boff_nxt + qsz, nxt);
+                if (active && q != p && q - p <= a.bw) {
+                    // mirror entry (q, p) = conj(rho_pq) in row q
+                    V c;
+                    c.x = nxt.x;
+                    c.y = -nxt.y;
+                    if constexpr (CLUSTER) stc2(mirror + (uint32_t)(p * SZ), c);
+                    else sts2(mirror + (uint32_t)(p * SZ), c);
+                }
+                if (active && q == p) {
+                    const int di = (CUR ^ 1) * diag_stride + slot * twoN + s * N + p;
+                    if constexpr (CLUSTER) {
+                        const uint32_t da = diag_s + (uint32_t)(di * (int)sizeof(T));
+                        for (int rr = 0; rr < a.C; ++rr) stc1(map_rank(da, rr), nxt.x);
+                    } else {
+                        s_diag[di] = nxt.x;
+                    }
+                    if (STAGE == 3 && snap_now) {
+                        const long long m = b * a.S + slot;
+                        if (m < a.M) a.snap[(snap_row * a.M + m) * twoN + s * N + p] = nxt.x;
+                    }
+                }
+            }
+            __syncwarp();
+            if constexpr (STAGE < 3) {
+                tmem_put(t_state + (uint32_t)(e * 2 * WC + WC), acc[0]);
+                if (two) tmem_put(t_state + (uint32_t)(e1 * 2 * WC + WC), acc[1]);
+            } else {
+                tmem_put(t_state + (uint32_t)(e * 2 * WC), y0[0]);
+                if (two) tmem_put(t_state + (uint32_t)(e1 * 2 * WC), y0[1]);
+            }
+        }
+        e -= (count & 1);   // an odd item consumed one slot, not two
+    }
+}
+
+template <typename T, bool CLUSTER, bool UNIFORM_T>
+__global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
+{
+    using V = typename C2<T>::type;
+    constexpr int SZ = sizeof(V);
+    constexpr int WC = SZ / 4;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int N = a.N, S = a.S, C = a.C, twoN = 2 * N, bw = a.bw;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = CLUSTER ? cluster_ctarank() : 0u;
+    const uint32_t cid = CLUSTER ? cluster_id_x() : blockIdx.x;
+    const uint32_t ncl = CLUSTER ? n_clusters_x() : gridDim.x;
+
+    // shared-memory carve-up (mirrors band_smem on the host)
+    unsigned char *ptr = smem;
+    SmemHeader *h = reinterpret_cast<SmemHeader *>(ptr);
+    ptr += 64;
+    BandRow *s_row = reinterpret_cast<BandRow *>(ptr);
+    ptr += sizeof(BandRow) * twoN;
+    int32_t *s_nbr = reinterpret_cast<int32_t *>(ptr);
+    ptr += 16 * ((4 * N + 15) / 16);
+    T *s_t = reinterpret_cast<T *>(ptr);
+    ptr += 16 * ((sizeof(T) * 4 * N + 15) / 16);
+    uint32_t *s_rowbase = reinterpret_cast<uint32_t *>(ptr);
+    ptr += 16 * ((4 * twoN + 15) / 16);
+    T *s_diag = reinterpret_cast<T *>(ptr);
+    ptr += 16 * ((sizeof(T) * 2 * S * twoN + 15) / 16);
+    const uint32_t bufA_s = smem_addr(ptr);
+    const uint32_t diag_s = smem_addr(s_diag);
+    const int diag_stride = S * twoN;
+
+    const int rb0 = a.row_begin[rank], rb1 = a.row_begin[rank + 1];
+    int eps = 0;                       // stored elements per slot of this rank
+    for (int sr = rb0; sr < rb1; ++sr) {
+        const int p = sr % N;
+        eps += N - (p > bw ? p - bw : 0);
+    }
+    const int eps_bytes = eps * SZ;
+
+    if (threadIdx.x == 0) {
+        h->abort = 0;
+        mbar_init(smem_addr(&h->bar), (uint32_t)C);
+        mbar_init(smem_addr(&h->dead_bar), 1u);
+        fence_mbar_init_cluster();
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        s_nbr[i] = a.nbr[i];
+        for (int n = 0; n < 4; ++n) s_t[4 * i + n] = a.tnb[4 * i + n];
+    }
+    // row bases: element (p, k) of spin-row sr (slot 0, buffer A) at base + k * SZ
+    for (int sr = threadIdx.x; sr < twoN; sr += blockDim.x) {
+        int owner = 0;
+        while (owner + 1 < C && sr >= a.row_begin[owner + 1]) ++owner;
+        int off = 0;
+        for (int x = a.row_begin[owner]; x < sr; ++x) {
+            const int px = x % N;
+            off += N - (px > bw ? px - bw : 0);
+        }
+        const int p = sr % N, lo = p > bw ? p - bw : 0;
+        const uint32_t start = bufA_s + (uint32_t)(off * SZ);   // element (p, lo)
+        s_rowbase[sr] = (CLUSTER ? map_rank(start, owner) : start) - (uint32_t)(lo * SZ);
+    }
+    __syncthreads();
+    for (int sr = threadIdx.x; sr < twoN; sr += blockDim.x) {
+        const int s = sr / N, p = sr % N;
+        BandRow d;
+        d.p = p;
+        const int nbp = s_nbr[p];
+        d.deg = (nbp >> 24) & 0xFF;
+        for (int n = 0; n < 3; ++n) d.base_k[n] = s_rowbase[s * N + ((nbp >> (8 * n)) & 0xFF)];
+        int off = 0;
+        for (int x = rb0; x < sr && x < rb1; ++x) {
+            const int px = x % N;
+            off += N - (px > bw ? px - bw : 0);
+        }
+        const int lo = p > bw ? p - bw : 0;
+        d.base_local = bufA_s + (uint32_t)(off * SZ) - (uint32_t)(lo * SZ);
+        d.pad0 = 0;
+        d.pad1 = 0;
+        s_row[sr] = d;
+    }
+    if (warp == 0) {
+        tmem_alloc(smem_addr(&h->tmem_base), kTmemCols);
+        tmem_relinquish();
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if constexpr (CLUSTER) cluster_sync_hw();
+
+    const uint32_t t_state = h->tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(kTmemColsPerWarp * (warp >> 2));
+    const uint32_t *my_items = a.items + ((size_t)rank * kWarps + warp) * a.k_items;
+
+    uint32_t phase = 0;
+    const unsigned long long limit = a.timeout_ns;
+    if (a.force_timeout) {
+        if (threadIdx.x == 0 && !mbar_wait_bounded(smem_addr(&h->dead_bar), 0u, limit)) {
+            h->abort = 1;
+            record_status(a.status, FTWA_ERR_DEVICE_TIMEOUT);
+        }
+        __syncthreads();
+    }
+
+    const long long n_batches = (a.M + S - 1) / S;
+    for (long long b = cid; b < n_batches && h->abort == 0; b += ncl) {
+        // ---- load: stored elements of own rows (upper part and mirror band) ----
+        for (int slot = 0; slot < S; ++slot) {
+            const long long m = b * S + slot;
+            for (int sr = rb0 + warp; sr < rb1; sr += kWarps) {
+                const int s = sr / N, p = sr % N, lo = p > bw ? p - bw : 0;
+                const uint32_t base = s_row[sr].base_local + (uint32_t)(slot * eps_bytes);
+                for (int k = lo + lane; k < N; k += 32) {
+                    V v;
+                    v.x = T(0);
+                    v.y = T(0);
+                    if (m < a.M) {
+                        if (k >= p) {
+                            v = a.rho[((m * 2 + s) * N + p) * (long long)N + k];
+                        } else {
+                            v = a.rho[((m * 2 + s) * N + k) * (long long)N + p];
+                            v.y = -v.y;
+                        }
+                    }
+                    if (k == p) {
+                        v.y = T(0);
+                        if (a.snap && m < a.M) a.snap[m * twoN + s * N + p] = v.x;
+                        const int di = slot * twoN + s * N + p;
+                        if constexpr (CLUSTER) {
+                            const uint32_t da = diag_s + (uint32_t)(di * (int)sizeof(T));
+                            for (int rr = 0; rr < C; ++rr) stc1(map_rank(da, rr), v.x);
+                        } else {
+                            s_diag[di] = v.x;
+                        }
+                    }
+                    sts2(base + (uint32_t)(k * SZ), v);
+                }
+            }
+        }
+        // y0 of computed elements into tensor memory
+        {
+            int e = 0;
+            for (int it = 0; it < a.k_items; ++it) {
+                const uint32_t item = my_items[it];
+                if (item == 0xFFFFFFFFu) break;
+                const int count = item & 63, blk = (item >> 6) & 7, sr0 = (item >> 9) & 511, slot = item >> 18;
+                const int s = sr0 >= N ? 1 : 0, q = 32 * blk + lane;
+                const long long m = b * S + slot;
+                for (int r = 0; r < count; ++r, ++e) {
+                    const int p = (sr0 + r) % N;
+                    V v;
+                    v.x = T(0);
+                    v.y = T(0);
+                    if (q < N && q >= p && m < a.M) {
+                        v = a.rho[((m * 2 + s) * N + p) * (long long)N + q];
+                        if (q == p) v.y = T(0);
+                    }
+                    __syncwarp();
+                    tmem_put(t_state + (uint32_t)(e * 2 * WC), v);
+                }
+            }
+        }
+        tmem_wait_st();
+        if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
+
+        for (long long step = 0; step < a.n_steps && h->abort == 0; ++step) {
+            const bool snap_now = a.snap && ((step + 1) % a.out_every == 0);
+            const long long snap_row = (step + 1) / a.out_every;
+            band_stage<0, T, CLUSTER, UNIFORM_T>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag, diag_s, lane,
+                                                 t_state, eps_bytes, diag_stride, b, snap_now, snap_row);
+            tmem_wait_st();
+            if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
+            band_stage<1, T, CLUSTER, UNIFORM_T>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag, diag_s, lane,
+                                                 t_state, eps_bytes, diag_stride, b, snap_now, snap_row);
+            tmem_wait_st();
+            if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
+            band_stage<2, T, CLUSTER, UNIFORM_T>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag, diag_s, lane,
+                                                 t_state, eps_bytes, diag_stride, b, snap_now, snap_row);
+            tmem_wait_st();
+            if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
+            band_stage<3, T, CLUSTER, UNIFORM_T>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag, diag_s, lane,
+                                                 t_state, eps_bytes, diag_stride, b, snap_now, snap_row);
+            tmem_wait_st();
+            if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
+        }
+        if (h->abort) break;
+
+        // ---- write back rho(T) (full Hermitian matrix) ------------------------------
+        {
+            int e = 0;
+            for (int it = 0; it < a.k_items; ++it) {
+                const uint32_t item = my_items[it];
+                if (item == 0xFFFFFFFFu) break;
+                const int count = item & 63, blk = (item >> 6) & 7, sr0 = (item >> 9) & 511, slot = item >> 18;
+                const int s = sr0 >= N ? 1 : 0, q = 32 * blk + lane;
+                const long long m = b * S + slot;
+                for (int r = 0; r < count; ++r, ++e) {
+                    const int p = (sr0 + r) % N;
+                    __syncwarp();
+                    V y0;
+                    tmem_get(t_state + (uint32_t)(e * 2 * WC), y0);
+                    if (q < N && q >= p && m < a.M) {
+                        if (!(isfinite(y0.x) && isfinite(y0.y))) record_status(a.status, FTWA_ERR_NONFINITE);
+                        a.rho[((m * 2 + s) * N + p) * (long long)N + q] = y0;
+                        if (p != q) {
+                            V c;
+                            c.x = y0.x;
+                            c.y = -y0.y;
+                            a.rho[((m * 2 + s) * N + q) * (long long)N + p] = c;
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        // the next batch overwrites both stage buffers' own rows; peers read
+        // this CTA's rows only after the post-load barrier
+        if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
+    }
+
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (warp == 0) tmem_dealloc(h->tmem_base, kTmemCols);
+    if constexpr (CLUSTER) cluster_sync_hw();
+}
+
+// ---------------------------------------------------------------------------
 // Host side: launch-shape selection and launch.
 // ---------------------------------------------------------------------------
 static int smem_needed(int N, int S, int real_bytes, int n_units, int buf_bytes)
@@ -680,13 +1102,249 @@ static int dispatch_t(Plan *p, StepperShape &sh, void *rho, int64_t M, int64_t n
         sh.grid = std::min(sh.grid, n_clusters * sh.cluster);
     }
     p->shape = sh;
+    p->shape.variant = 2;
     if (M == 0) return FTWA_OK;
     return p->uniform_t ? launch_t<T, CLUSTER, true>(p, sh, rho, M, n_steps, snap, s)
                         : launch_t<T, CLUSTER, false>(p, sh, rho, M, n_steps, snap, s);
 }
 
+// ---- banded stepper: shape and work items ------------------------------------
+static int band_row_len(int N, int bw, int sr)
+{
+    const int p = sr % N;
+    return N - (p > bw ? p - bw : 0);
+}
+
+// Work items of one rank: runs of <= R consecutive spin-rows of one spin with
+// at least one element in column block b, for every block and slot; assigned
+// to warps longest-first under the tensor-memory cap.
+static bool band_items(int N, int S, int rb0, int rb1, int e_cap, int R, std::vector<uint32_t> &out, int &E, int &K)
+{
+    const int nblk = (N + 31) / 32;
+    std::vector<std::pair<int, uint32_t>> items;   // (rows, packed)
+    long long total = 0;
+    for (int slot = 0; slot < S; ++slot)
+        for (int b = 0; b < nblk; ++b)
+            for (int s = 0; s < 2; ++s) {
+                const int lo = std::max(rb0, s * N), hi = std::min(rb1, s * N + N);
+                // rows with p <= 32 b + 31
+                const int last = std::min(hi, s * N + std::min(N, 32 * b + 32));
+                for (int sr = lo; sr < last;) {
+                    const int cnt = std::min(R, last - sr);
+                    items.push_back({cnt, (uint32_t)cnt | ((uint32_t)b << 6) | ((uint32_t)sr << 9) | ((uint32_t)slot << 18)});
+                    total += cnt;
+                    sr += cnt;
+                }
+            }
+    std::stable_sort(items.begin(), items.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
+    std::vector<int> load(kWarps, 0);
+    std::vector<std::vector<uint32_t>> per(kWarps);
+    for (const auto &it : items) {
+        int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        if (load[w] + it.first > e_cap) return false;
+        load[w] += it.first;
+        per[w].push_back(it.second);
+    }
+    E = *std::max_element(load.begin(), load.end());
+    K = 1;
+    for (auto &v : per) K = std::max<int>(K, (int)v.size());
+    out.assign((size_t)kWarps * K, 0xFFFFFFFFu);
+    for (int w = 0; w < kWarps; ++w)
+        for (size_t i = 0; i < per[w].size(); ++i) out[(size_t)w * K + i] = per[w][i];
+    (void)total;
+    return true;
+}
+
+static int band_smem(int N, int S, int real_bytes, int buf_bytes)
+{
+    auto r16 = [](int x) { return 16 * ((x + 15) / 16); };
+    int b = 64 + (int)sizeof(BandRow) * 2 * N + r16(4 * N) + r16(real_bytes * 4 * N) + r16(4 * 2 * N);
+    b += r16(real_bytes * 2 * S * 2 * N);
+    return b + 2 * buf_bytes;
+}
+
+int choose_band_shape(Plan *p, int64_t M, BandShape *out)
+{
+    const int N = p->N, bw = p->bandwidth;
+    if (N > 256) return FTWA_ERR_UNSUPPORTED;
+    const int real_bytes = p->precision == FTWA_FP64 ? 8 : 4;
+    const int SZ = 2 * real_bytes, WC = SZ / 4;
+    const int e_cap = kTmemColsPerWarp / (2 * WC);
+    const int max_smem = 227 * 1024;
+    const int sm = p->sm_count > 0 ? p->sm_count : 1;
+    const int nblk = (N + 31) / 32;
+    for (int C = 1; C <= kMaxCluster; C *= 2) {
+        if (p->cluster_override && C != p->cluster_override) continue;
+        BandShape sh;
+        sh.cluster = C;
+        // split spin-rows by their number of column-block slices
+        double tot = 0;
+        for (int sr = 0; sr < 2 * N; ++sr) tot += nblk - (sr % N) / 32;
+        sh.row_begin[0] = 0;
+        int sr = 0;
+        double acc = 0;
+        for (int r = 1; r < C; ++r) {
+            const double target = tot * r / C;
+            while (sr < 2 * N && acc + 0.5 * (nblk - (sr % N) / 32) < target) {
+                acc += nblk - (sr % N) / 32;
+                ++sr;
+            }
+            sh.row_begin[r] = sr;
+        }
+        sh.row_begin[C] = 2 * N;
+        int eps_max = 0;
+        for (int r = 0; r < C; ++r) {
+            int e = 0;
+            for (int x = sh.row_begin[r]; x < sh.row_begin[r + 1]; ++x) e += band_row_len(N, bw, x);
+            eps_max = std::max(eps_max, e);
+        }
+        int want = 1;
+        if (C == 1) want = (int)std::max<long long>(1, std::min<long long>((M + sm - 1) / sm, 255));
+        int best = 0;
+        std::vector<std::vector<uint32_t>> best_items;
+        int bestE = 0, bestK = 0;
+        for (int S = 1; S <= want; ++S) {
+            const int buf = ((S * eps_max * SZ + 15) / 16) * 16;
+            if (band_smem(N, S, real_bytes, buf) > max_smem) break;
+            std::vector<std::vector<uint32_t>> its(C);
+            int E = 0, K = 0;
+            bool ok = true;
+            for (int r = 0; r < C && ok; ++r) {
+                // longest runs first; shorter runs pack the tensor-memory budget tighter
+                bool placed = false;
+                for (int R = 8; R >= 1 && !placed; R /= 2) {
+                    int e, k;
+                    placed = band_items(N, S, sh.row_begin[r], sh.row_begin[r + 1], e_cap, R, its[r], e, k);
+                    if (placed) {
+                        E = std::max(E, e);
+                        K = std::max(K, k);
+                    }
+                }
+                ok = placed;
+            }
+            if (!ok) break;
+            best = S;
+            best_items = its;
+            bestE = E;
+            bestK = K;
+        }
+        if (best == 0) continue;
+        sh.slots = best;
+        sh.E = bestE;
+        sh.k_items = bestK;
+        sh.items.assign((size_t)C * kWarps * bestK, 0xFFFFFFFFu);
+        for (int r = 0; r < C; ++r) {
+            // re-pack each rank's table to the common width bestK
+            const int Kr = (int)(best_items[r].size() / kWarps);
+            for (int w = 0; w < kWarps; ++w)
+                for (int i = 0; i < Kr; ++i)
+                    sh.items[((size_t)r * kWarps + w) * bestK + i] = best_items[r][(size_t)w * Kr + i];
+        }
+        sh.buf_bytes = ((best * eps_max * SZ + 15) / 16) * 16;
+        sh.smem_bytes = std::max(kMinSmem, band_smem(N, best, real_bytes, sh.buf_bytes));
+        const long long batches = (M + best - 1) / best;
+        sh.grid = (int)std::min<long long>(std::max<long long>(batches, 1), std::max(1, sm / C)) * C;
+        *out = sh;
+        return FTWA_OK;
+    }
+    return FTWA_ERR_UNSUPPORTED;
+}
+
+template <typename T, bool CLUSTER, bool UNIFORM_T>
+static int band_launch(Plan *p, BandShape &sh, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s)
+{
+    auto kern = band_stepper<T, CLUSTER, UNIFORM_T>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem_bytes);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(sh.grid, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = sh.smem_bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = sh.cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = CLUSTER ? 1 : 0;
+    if (CLUSTER) {
+        int n_clusters = 0;
+        e = cudaOccupancyMaxActiveClusters(&n_clusters, kern, &cfg);
+        if (e != cudaSuccess) return set_cuda_error(e);
+        if (n_clusters < 1) return FTWA_ERR_UNSUPPORTED;
+        sh.grid = std::min(sh.grid, n_clusters * sh.cluster);
+        cfg.gridDim = dim3(sh.grid, 1, 1);
+    }
+    // upload the item table (plan-owned, reused while the shape is unchanged)
+    const size_t bytes = sh.items.size() * sizeof(uint32_t);
+    if (p->items_bytes < bytes) {
+        cudaFree(p->d_items);
+        p->d_items = nullptr;
+        p->items_bytes = 0;
+        e = cudaMalloc(&p->d_items, bytes);
+        if (e != cudaSuccess) return set_cuda_error(e);
+        p->items_bytes = bytes;
+    }
+    e = cudaMemcpyAsync(p->d_items, sh.items.data(), bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    p->shape.cluster = sh.cluster;
+    p->shape.slots = sh.slots;
+    p->shape.units_per_warp = sh.E;
+    p->shape.smem_bytes = sh.smem_bytes;
+    p->shape.grid = sh.grid;
+    p->shape.variant = 1;
+    if (M == 0) return FTWA_OK;
+    BandArgs<T> a{};
+    a.nbr = p->d_nbr;
+    a.tnb = std::is_same<T, double>::value ? reinterpret_cast<const T *>(p->d_t64)
+                                           : reinterpret_cast<const T *>(p->d_t32);
+    a.U = (T)p->U;
+    a.dt = (T)p->dt;
+    a.t_uniform = p->t_bond.empty() ? T(0) : (T)p->t_bond[0];
+    a.N = p->N;
+    a.bw = p->bandwidth;
+    a.C = sh.cluster;
+    a.S = sh.slots;
+    a.E = sh.E;
+    a.k_items = sh.k_items;
+    a.buf_bytes = sh.buf_bytes;
+    for (int i = 0; i <= kMaxCluster; ++i) a.row_begin[i] = sh.row_begin[i];
+    a.items = p->d_items;
+    a.M = M;
+    a.n_steps = n_steps;
+    a.out_every = p->out_every;
+    a.rho = reinterpret_cast<typename C2<T>::type *>(rho);
+    a.snap = reinterpret_cast<T *>(snap);
+    a.status = p->d_status;
+    a.timeout_ns = p->timeout_ns;
+    a.force_timeout = p->force_timeout;
+    e = cudaLaunchKernelEx(&cfg, kern, a);
+    return set_cuda_error(e);
+}
+
+template <typename T>
+static int band_dispatch(Plan *p, BandShape &sh, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s)
+{
+    if (sh.cluster > 1)
+        return p->uniform_t ? band_launch<T, true, true>(p, sh, rho, M, n_steps, snap, s)
+                            : band_launch<T, true, false>(p, sh, rho, M, n_steps, snap, s);
+    return p->uniform_t ? band_launch<T, false, true>(p, sh, rho, M, n_steps, snap, s)
+                        : band_launch<T, false, false>(p, sh, rho, M, n_steps, snap, s);
+}
+
 int launch_evolve(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s)
 {
+    // automatic choice: the banded stepper for FP32; for FP64 (DFMA-bound on
+    // this part) the packed-triangle stepper, which does fewer flops per element
+    const bool try_band = p->variant_override == 1 || (p->variant_override == 0 && p->precision == FTWA_FP32);
+    if (try_band) {
+        BandShape bs;
+        if (choose_band_shape(p, M, &bs) == FTWA_OK)
+            return p->precision == FTWA_FP64 ? band_dispatch<double>(p, bs, rho, M, n_steps, snap, s)
+                                             : band_dispatch<float>(p, bs, rho, M, n_steps, snap, s);
+        if (p->variant_override == 1) return FTWA_ERR_UNSUPPORTED;
+    }
     StepperShape sh;
     int rc = choose_stepper_shape(p, M, &sh);
     if (rc != FTWA_OK) return rc;

@@ -28,6 +28,14 @@ struct StepperShape {
     int buf_bytes = 0;      // bytes of one stage buffer (max over ranks)
     int row_begin[kMaxCluster + 1] = {0};  // spin-row partition over ranks
     int grid = 0;           // CTAs launched
+    int variant = 0;        // 1 = banded stepper, 2 = general packed-triangle stepper
+};
+
+// Launch shape of the banded stepper.
+struct BandShape {
+    int cluster = 1, slots = 1, E = 0, k_items = 0, buf_bytes = 0, smem_bytes = 0, grid = 0;
+    int row_begin[kMaxCluster + 1] = {0};
+    std::vector<uint32_t> items;   // [cluster][kWarps][k_items]
 };
 
 struct Plan {
@@ -56,6 +64,9 @@ struct Plan {
     int32_t *d_bonds = nullptr;       // [B][2]
     int *d_status = nullptr;          // device status word
     void *d_ws = nullptr;             // plan-owned workspace (moments, adjoint)
+    uint32_t *d_items = nullptr;      // banded stepper work items
+    size_t items_bytes = 0;
+    int variant_override = 0;         // 0 auto, 1 banded only, 2 general only
     size_t ws_bytes = 0;
     StepperShape shape;               // chosen for the full machine
 };
@@ -68,6 +79,7 @@ int launch_philox(uint64_t seed, int64_t m, int32_t spin, int64_t p0, int64_t co
                   cudaStream_t s);
 int launch_evolve(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s);
 int choose_stepper_shape(Plan *p, int64_t M, StepperShape *out);
+int choose_band_shape(Plan *p, int64_t M, BandShape *out);
 int launch_moments(Plan *p, const void *snap, int64_t M, int32_t T, double *occ, double *conn, double *g2,
                    int32_t mode, cudaStream_t s);
 int launch_adjoint(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, int32_t ckpt_every, const double *dL,

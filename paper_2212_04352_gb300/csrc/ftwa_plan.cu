@@ -31,6 +31,9 @@ static void free_tables(Plan *p)
     cudaFree(p->d_bonds);
     cudaFree(p->d_status);
     cudaFree(p->d_ws);
+    cudaFree(p->d_items);
+    p->d_items = nullptr;
+    p->items_bytes = 0;
     p->d_ws = nullptr;
     p->ws_bytes = 0;
     p->d_nbr = nullptr;
@@ -122,6 +125,7 @@ int ftwa_plan(const ftwa_lattice *lat, double U, double t, double filling, const
         (o.cluster_override & (o.cluster_override - 1)) != 0)
         return FTWA_ERR_INVALID_ARGUMENT;
     if (o.threads_override != 0 && o.threads_override != kThreads) return FTWA_ERR_UNSUPPORTED;
+    if (o.variant < 0 || o.variant > 2) return FTWA_ERR_INVALID_ARGUMENT;
 
     ftwa_plan_t *p = new (std::nothrow) ftwa_plan_t();
     if (!p) return FTWA_ERR_OUT_OF_MEMORY;
@@ -134,6 +138,7 @@ int ftwa_plan(const ftwa_lattice *lat, double U, double t, double filling, const
     p->cluster_override = o.cluster_override;
     p->threads_override = o.threads_override;
     p->autotune = o.autotune;
+    p->variant_override = o.variant;
     if (o.timeout_us) p->timeout_ns = o.timeout_us * 1000ull;
 
     // bonds: 0 <= i < j < N, unique, degree <= 3
@@ -249,7 +254,24 @@ int ftwa_plan(const ftwa_lattice *lat, double U, double t, double filling, const
         delete p;
         return rc;
     }
-    rc = choose_stepper_shape(p, (int64_t)p->sm_count, &p->shape);
+    {
+        BandShape bs;
+        const bool try_band = p->variant_override == 1 || (p->variant_override == 0 && p->precision == FTWA_FP32);
+        if (try_band && choose_band_shape(p, (int64_t)p->sm_count, &bs) == FTWA_OK) {
+            p->shape.cluster = bs.cluster;
+            p->shape.slots = bs.slots;
+            p->shape.units_per_warp = bs.E;
+            p->shape.smem_bytes = bs.smem_bytes;
+            p->shape.grid = bs.grid;
+            p->shape.variant = 1;
+            rc = FTWA_OK;
+        } else if (p->variant_override == 1) {
+            rc = FTWA_ERR_UNSUPPORTED;
+        } else {
+            rc = choose_stepper_shape(p, (int64_t)p->sm_count, &p->shape);
+            p->shape.variant = 2;
+        }
+    }
     if (rc != FTWA_OK) {
         free_tables(p);
         delete p;
@@ -283,6 +305,7 @@ int ftwa_get_info(const ftwa_plan_t *p, ftwa_plan_info *info)
     info->tmem_cols = kTmemCols;
     info->grid_clusters = p->shape.grid / std::max(1, p->shape.cluster);
     info->units_per_warp = p->shape.units_per_warp;
+    info->variant = p->shape.variant;
     return FTWA_OK;
 }
 

@@ -52,7 +52,7 @@ def _plan(lib, bonds, n, nu=None, nd=None, U=1.0, filling=0.0, precision=0, dt=0
         nu = np.ascontiguousarray(nu, dtype=np.float64)
         nd = np.ascontiguousarray(nd, dtype=np.float64)
         init = _lib.InitState(nu.ctypes.data, nd.ctypes.data)
-    opts = _lib.Options(precision, dt, out_every, 0, 0, 0, 0)
+    opts = _lib.Options(precision, dt, out_every, 0, 0, 0, 0, 0)
     h = ctypes.c_void_p()
     rc = lib.ftwa_plan(ctypes.byref(lat), U, 1.0, filling, None if init is None else ctypes.byref(init),
                        ctypes.byref(opts), ctypes.byref(h))

@@ -100,17 +100,19 @@ def test_evolve_fp64_matches_oracle(ftwa, name, make, U, kind, M):
     assert np.max(np.abs(X - snap_o)) <= 1e-10
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("cluster", [1, 2, 4, 8])
-def test_evolve_cluster_shapes(ftwa, cluster):
-    """Every cluster split of the spin-rows gives the oracle's trajectory
-    (oracle-drawn rho(0) fed to the GPU; ragged M)."""
+def test_evolve_cluster_shapes(ftwa, cluster, variant):
+    """Both steppers (1: banded, 2: packed triangle), every cluster split of
+    the spin-rows: the oracle's trajectory (oracle-drawn rho(0) fed to the
+    GPU; ragged M)."""
     lat = W.hexagonal_flake(3)          # 54 sites
     nu, nd = W.neel_state(lat)
     M, steps = 3, 200
     rho0 = _oracle_states(lat, nu, nd, 9, M)
     fin_o = np.stack([oracle.evolve(lat, 1.6, rho0[m], 0.01, steps)[0] for m in range(M)])
-    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=0, cluster=cluster) as P:
-        assert P.info()["cluster"] == cluster
+    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=0, cluster=cluster, variant=variant) as P:
+        assert P.info()["cluster"] == cluster and P.info()["variant"] == variant
         rho = torch.from_numpy(rho0).cuda()
         P.evolve(rho, steps, snap=None)
         assert P.status() == 0
@@ -119,14 +121,15 @@ def test_evolve_cluster_shapes(ftwa, cluster):
         assert _rel(fin[m], fin_o[m]) <= 1e-11
 
 
-def test_evolve_198_sites_fp64(ftwa):
+@pytest.mark.parametrize("variant", [1, 2])
+def test_evolve_198_sites_fp64(ftwa, variant):
     """The 198-site brick-wall flake, charge-imbalanced start: a few sampled
     trajectories, full T = 10."""
     lat = W.brick_wall_flake()
     nu, nd = W.charge_imbalanced_state(lat)
     M, steps = 2, 1000
     snap_o, fin_o = oracle.run(lat, 1.6, nu, nd, 2, 0, M, 0.01, steps, 100, want_final=True)
-    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=0, out_every=100) as P:
+    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=0, out_every=100, variant=variant) as P:
         rho = P.sample(2, M)
         X = P.evolve(rho, steps)
         assert P.status() == 0
@@ -136,14 +139,16 @@ def test_evolve_198_sites_fp64(ftwa):
     assert np.max(np.abs(X.cpu().numpy() - snap_o)) <= 1e-10
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("lat_name", ["periodic8", "brick198"])
-def test_evolve_fp32_short(ftwa, lat_name):
+def test_evolve_fp32_short(ftwa, lat_name, variant):
     lat = W.periodic_honeycomb() if lat_name == "periodic8" else W.brick_wall_flake()
     nu, nd = W.neel_state(lat)
     M, steps = 3, 100
     rho0 = _oracle_states(lat, nu, nd, 4, M)
     fin_o = np.stack([oracle.evolve(lat, 1.6, rho0[m], 0.01, steps)[0] for m in range(M)])
-    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=1) as P:
+    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=1, variant=variant) as P:
+        assert P.info()["variant"] == variant
         rho = torch.from_numpy(rho0.astype(np.complex64)).cuda()
         P.evolve(rho, steps, snap=None)
         assert P.status() == 0
@@ -194,8 +199,9 @@ def test_timeout_hook_returns_status(ftwa):
     FTWA_ERR_DEVICE_TIMEOUT; the context stays usable afterwards."""
     lat = W.hexagonal_flake(3)
     nu, nd = W.neel_state(lat)
-    for cluster in [1, 2]:
-        with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=0, cluster=cluster, timeout_us=2000) as P:
+    for cluster, variant in [(1, 1), (2, 1), (1, 2), (2, 2)]:
+        with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=0, cluster=cluster, timeout_us=2000,
+                       variant=variant) as P:
             rho = P.sample(1, 2)
             r0 = rho.clone()
             P.debug_force_timeout(True)

@@ -179,9 +179,11 @@ int ftwa_evolve(ftwa_plan_t *plan, void *rho_dev, int64_t M, int64_t n_steps,
  * gram_mode FTWA_GRAM_FP64 forms the Gram in double; FTWA_GRAM_BF16X3 forms
  * it on the tensor cores from centred data split as x = hi + lo (bf16) with
  * products hi*hi + hi*lo + lo*hi in fp32, reduced across sample blocks in
- * double.  All outputs are device double arrays.  Errors:
- * FTWA_ERR_INVALID_ARGUMENT (null pointers, M < 1, n_times < 1, bad mode),
- * FTWA_ERR_CUDA. */
+ * double (FP32 plans only).  All outputs are device double arrays.  The
+ * plan keeps a workspace for the means and the per-split partial tiles
+ * (grown on demand).  Errors: FTWA_ERR_INVALID_ARGUMENT (null pointers,
+ * M < 1, n_times < 1, bad mode), FTWA_ERR_UNSUPPORTED (BF16X3 on an FP64
+ * plan), FTWA_ERR_OUT_OF_MEMORY, FTWA_ERR_CUDA. */
 int ftwa_moments(ftwa_plan_t *plan, const void *snap_dev, int64_t M, int32_t n_times,
                  double *occ_dev, double *conn_dev, double *g2_dev, int32_t gram_mode,
                  void *stream);

@@ -10,6 +10,8 @@
 // products on the tcgen05 tensor cores (ftwa_gram_tc.cu).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "ftwa_internal.h"
 
 namespace ftwa {
@@ -98,6 +100,7 @@ __global__ void gram_fp64_kernel(const T *__restrict__ X, long long M, int K, co
 
 int launch_gram_bf16x3(Plan *p, const void *snap, int64_t M, int32_t T, const double *mu, double *conn,
                        double *g2, cudaStream_t s);
+size_t gram_bf16x3_workspace(Plan *p, int64_t M, int32_t T);
 
 static int ensure_workspace(Plan *p, size_t bytes)
 {
@@ -115,7 +118,10 @@ int launch_moments(Plan *p, const void *snap, int64_t M, int32_t T, double *occ,
                    int32_t mode, cudaStream_t s)
 {
     const int K = 2 * p->N;
-    int rc = ensure_workspace(p, sizeof(double) * (size_t)T * K);
+    if (mode == FTWA_GRAM_BF16X3 && p->precision != FTWA_FP32) return FTWA_ERR_UNSUPPORTED;
+    size_t need = sizeof(double) * (size_t)T * K;
+    if (mode == FTWA_GRAM_BF16X3) need = std::max(need, gram_bf16x3_workspace(p, M, T));
+    int rc = ensure_workspace(p, need);
     if (rc != FTWA_OK) return rc;
     double *mu = reinterpret_cast<double *>(p->d_ws);
     dim3 gm((K + 31) / 32, T);

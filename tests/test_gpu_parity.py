@@ -249,3 +249,28 @@ def test_full_path_config1_against_oracle(ftwa):
     assert X.shape == (101, M, 16)
     assert np.max(np.abs(occ.cpu().numpy() - occ_o)) <= 1e-10
     assert np.max(np.abs(conn.cpu().numpy() - conn_o)) <= 1e-10
+
+
+# ------------------------------------------------------------------ tensor-core Gram
+@pytest.mark.parametrize("lat_name,M,steps", [("periodic8", 1000, 50), ("hexflake54", 777, 30),
+                                              ("hexflake96", 2000, 20), ("brick198", 1500, 20)])
+def test_gram_bf16x3_matches_fp64(ftwa, lat_name, M, steps):
+    """BF16x3 tensor-core Gram against the FP64 Gram of the same FP32
+    snapshots.  Each product y_k y_l loses at most the lo*lo term (2^-16
+    relative), so |C_bf16 - C_fp64| <= 3e-5 sqrt(C_kk C_ll) (+ FP32
+    accumulation); ragged M, 1 to 10 output tiles, split sample ranges."""
+    lat = {"periodic8": W.periodic_honeycomb, "hexflake54": lambda: W.hexagonal_flake(3),
+           "hexflake96": lambda: W.hexagonal_flake(4), "brick198": W.brick_wall_flake}[lat_name]()
+    nu, nd = W.neel_state(lat)
+    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=1, out_every=10) as P:
+        rho = P.sample(3, M)
+        X = P.evolve(rho, steps)
+        occ64, c64, g64 = P.moments(X, gram_mode=ftwa.FTWA_GRAM_FP64)
+        occ16, c16, g16 = P.moments(X, gram_mode=ftwa.FTWA_GRAM_BF16X3)
+        assert P.status() == 0
+    c64, c16 = c64.cpu().numpy(), c16.cpu().numpy()
+    assert torch.equal(occ64, occ16)
+    d = np.sqrt(np.abs(np.einsum("tkk->tk", c64)))
+    bound = 3e-5 * d[:, :, None] * d[:, None, :] + 1e-7
+    assert np.all(np.abs(c16 - c64) <= bound)
+    assert np.array_equal(c16, np.transpose(c16, (0, 2, 1)))

@@ -205,6 +205,32 @@ int ftwa_adjoint(ftwa_plan_t *plan, uint64_t seed, int64_t M, int64_t n_steps, i
                  const double *dL_docc_dev, double *grad_U_dev, double *grad_t_dev,
                  double *grad_n0_dev, void *stream);
 
+/* Allocation-free variant of ftwa_moments with gram_mode FTWA_GRAM_FP64.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc, such as applications whose device memory is owned
+ * by another allocator (a framework's caching allocator, a pool sized at
+ * start-up) and latency-critical loops that cannot accept cudaMalloc's
+ * implicit device synchronisation.  It needs no plan and allocates nothing:
+ * the caller passes the snapshots (snap_dev, [n_times][M][2 n_sites] of
+ * `precision`) and the outputs, with the same layout and meaning as for
+ * ftwa_moments (occ_dev [n_times][2N], conn_dev and the nullable g2_dev
+ * [n_times][2N][2N], device doubles).  The only scratch, the per-time sample
+ * means, is a static device array of FTWA_MOMENTS_NOALLOC_MAX_TK doubles
+ * (1 MiB, held by every device that loads the library until the process
+ * exits); n_times * 2 n_sites beyond that limit is rejected with
+ * FTWA_ERR_UNSUPPORTED.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call shares the array and
+ * overwrites the entries it uses before reading them, so nothing needs
+ * clearing; calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller.  Errors:
+ * FTWA_ERR_INVALID_ARGUMENT (null snap/occ/conn, M < 1, n_times < 1,
+ * n_sites outside [1, FTWA_MAX_SITES], bad precision), FTWA_ERR_UNSUPPORTED
+ * (size limit), FTWA_ERR_CUDA. */
+#define FTWA_MOMENTS_NOALLOC_MAX_TK  131072
+int ftwa_moments_noalloc(const void *snap_dev, int32_t precision, int32_t n_sites, int64_t M, int32_t n_times,
+                         double *occ_dev, double *conn_dev, double *g2_dev, void *stream);
+
 /* Synchronise `stream`, then return and clear the plan's device status word
  * (FTWA_OK, FTWA_ERR_DEVICE_TIMEOUT or FTWA_ERR_NONFINITE), or FTWA_ERR_CUDA
  * if the synchronisation itself failed. */

@@ -20,7 +20,7 @@ from ._lib import (  # noqa: F401
     FTWA_FP32, FTWA_FP64, FTWA_GRAM_BF16X3, FTWA_GRAM_FP64, FtwaError, check, load,
 )
 
-__all__ = ["Plan", "plan", "philox", "FTWA_FP32", "FTWA_FP64", "FTWA_GRAM_FP64", "FTWA_GRAM_BF16X3",
+__all__ = ["Plan", "plan", "philox", "moments_noalloc", "FTWA_FP32", "FTWA_FP64", "FTWA_GRAM_FP64", "FTWA_GRAM_BF16X3",
            "FtwaError", "load"]
 
 
@@ -158,6 +158,24 @@ class Plan:
 
 def plan(lattice, U, **kw) -> Plan:
     return Plan(lattice, U, **kw)
+
+
+def moments_noalloc(X, precision, n_sites, g2=True, stream=None, out=None):
+    """ftwa_moments_noalloc: FP64 estimators without any allocation inside the
+    library (for callers that cannot call cudaMalloc).  X is [T, M, 2N] of the
+    given precision; ``out`` = (occ, conn, g2-or-None) preallocated float64
+    tensors, or None to have them allocated here by torch."""
+    import torch
+    T, M, K = X.shape
+    if out is None:
+        occ = torch.empty((T, K), dtype=torch.float64, device=X.device)
+        conn = torch.empty((T, K, K), dtype=torch.float64, device=X.device)
+        g = torch.empty((T, K, K), dtype=torch.float64, device=X.device) if g2 else None
+    else:
+        occ, conn, g = out
+    check(load().ftwa_moments_noalloc(_ptr(X), int(precision), int(n_sites), int(M), int(T), _ptr(occ), _ptr(conn),
+                                      _ptr(g), _stream(stream)), "ftwa_moments_noalloc")
+    return occ, conn, g
 
 
 def philox(seed, m, spin, p0, count, stream=None):

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "ftwa_internal.h"
 
@@ -141,4 +142,66 @@ int launch_moments(Plan *p, const void *snap, int64_t M, int32_t T, double *occ,
     return set_cuda_error(cudaGetLastError());
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free moments (ftwa_moments_noalloc).
+//
+// For callers that cannot call cudaMalloc: applications whose device memory
+// is owned by another allocator (a framework's caching allocator or a pool
+// sized at start-up) and latency-critical loops that cannot accept
+// cudaMalloc's implicit device synchronisation.  The only scratch the FP64
+// estimators need, the per-time sample means, lives in the file-scope device
+// array below (FTWA_MOMENTS_NOALLOC_MAX_TK doubles, 1 MiB, resident on every
+// device that loads the library until the process exits).  Host code must
+// not use the array's name as a device address: its device address is looked
+// up with cudaGetSymbolAddress, once per device, on the first call made with
+// that device current.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double g_noalloc_mu[FTWA_MOMENTS_NOALLOC_MAX_TK];
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_lock;
+double *g_noalloc_addr[kNoallocMaxDevices] = {nullptr};
+}  // namespace
+
 }  // namespace ftwa
+
+extern "C" int ftwa_moments_noalloc(const void *snap_dev, int32_t precision, int32_t n_sites, int64_t M,
+                                    int32_t n_times, double *occ_dev, double *conn_dev, double *g2_dev, void *stream)
+{
+    using namespace ftwa;
+    if (!snap_dev || !occ_dev || !conn_dev || M < 1 || n_times < 1 || n_sites < 1 || n_sites > FTWA_MAX_SITES)
+        return FTWA_ERR_INVALID_ARGUMENT;
+    if (precision != FTWA_FP64 && precision != FTWA_FP32) return FTWA_ERR_INVALID_ARGUMENT;
+    const int K = 2 * n_sites;
+    if ((int64_t)n_times * K > FTWA_MOMENTS_NOALLOC_MAX_TK) return FTWA_ERR_UNSUPPORTED;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FTWA_ERR_CUDA;
+    if (dev < 0 || dev >= kNoallocMaxDevices) return FTWA_ERR_UNSUPPORTED;
+    double *mu = nullptr;
+    {
+        std::lock_guard<std::mutex> guard(g_noalloc_lock);
+        if (!g_noalloc_addr[dev]) {
+            void *a = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_mu);
+            if (e != cudaSuccess || !a) return FTWA_ERR_CUDA;
+            g_noalloc_addr[dev] = static_cast<double *>(a);
+        }
+        mu = g_noalloc_addr[dev];
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the mean kernel writes every mu[t][k] (t < n_times, k < 2N) before the
+    // Gram kernel reads it, so the shared array needs no clearing
+    dim3 gm((K + 31) / 32, n_times);
+    const int nt = (K + 63) / 64;
+    dim3 gg(nt, nt, n_times);
+    if (precision == FTWA_FP64) {
+        mean_kernel<double><<<gm, 256, 0, s>>>(static_cast<const double *>(snap_dev), M, K, mu, occ_dev);
+        gram_fp64_kernel<double><<<gg, 256, 0, s>>>(static_cast<const double *>(snap_dev), M, K, mu, conn_dev, g2_dev);
+    } else {
+        mean_kernel<float><<<gm, 256, 0, s>>>(static_cast<const float *>(snap_dev), M, K, mu, occ_dev);
+        gram_fp64_kernel<float><<<gg, 256, 0, s>>>(static_cast<const float *>(snap_dev), M, K, mu, conn_dev, g2_dev);
+    }
+    return set_cuda_error(cudaGetLastError());
+}
+

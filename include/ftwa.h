@@ -188,19 +188,24 @@ int ftwa_moments(ftwa_plan_t *plan, const void *snap_dev, int64_t M, int32_t n_t
                  double *occ_dev, double *conn_dev, double *g2_dev, int32_t gram_mode,
                  void *stream);
 
-/* Discrete adjoint of the RK4 integration of Eq. 9 for the loss
- * L = sum_{t=1..T} sum_k g_t,k <n_k>(t) (linearised: the caller supplies
- * dL_docc_dev[t][k] = dL/d<n_k>(t) for the output rows t = 0 .. T,
- * T = n_steps/out_every, [T+1][2N] device double).  Samples m = 0 .. M-1 of
- * `seed` are regenerated (Eq. 12), integrated forward with a checkpoint
- * every ckpt_every steps, and swept backward stage by stage.  Outputs
- * (device double, overwritten): grad_U_dev[1] = dL/dU, grad_t_dev[n_bonds] =
- * dL/dt_b (bond order of the lattice), grad_n0_dev[2][N] = dL/dn_i,s through
- * both rho_ii(0) = n - 1/2 and the noise scale s_ij(n) of Eq. 12 (finite only
- * where every s_ij > 0, e.g. fractional occupations).  Any output pointer
- * may be NULL.  ckpt_every must divide n_steps and be a multiple of
- * out_every.  Errors: FTWA_ERR_INVALID_ARGUMENT, FTWA_ERR_OUT_OF_MEMORY,
- * FTWA_ERR_CUDA. */
+/* Discrete adjoint of the RK4 integration of Eq. 9.  The loss is given
+ * through its gradient with respect to the occupations: the caller supplies
+ * dL_docc_dev[t][k] = dL/d<n_k>(t) for the output rows t = 0 .. T (T =
+ * n_steps/out_every, [T+1][2N] device doubles, k = s*N + i); for a loss
+ * L(<n>) this is exact at the point where it was evaluated.  Samples
+ * m = 0 .. M-1 of `seed` are regenerated exactly as ftwa_sample draws them
+ * (Eq. 12), integrated forward with a checkpoint every ckpt_every steps, and
+ * swept backward stage by stage (each segment replayed from its checkpoint).
+ * Outputs (device doubles, overwritten; any may be NULL): grad_U_dev[1] =
+ * dL/dU, grad_t_dev[n_bonds] = dL/dt_b in the lattice's bond order,
+ * grad_n0_dev[2][N] = dL/dn_i,s through rho_ii(0) = n - 1/2 and through the
+ * noise scale s_ij(n) of Eq. 12; pairs with s_ij = 0 (e.g. two filled or two
+ * empty sites of a Fock state) are skipped, since n -> s_ij is not
+ * differentiable there.  ckpt_every must divide n_steps and be a multiple of
+ * out_every.  The plan keeps a per-CTA workspace (checkpoints, one replayed
+ * segment, stage states; grown on demand).  Errors:
+ * FTWA_ERR_INVALID_ARGUMENT, FTWA_ERR_UNSUPPORTED (lattice too large for
+ * the per-sample tables), FTWA_ERR_OUT_OF_MEMORY, FTWA_ERR_CUDA. */
 int ftwa_adjoint(ftwa_plan_t *plan, uint64_t seed, int64_t M, int64_t n_steps, int32_t ckpt_every,
                  const double *dL_docc_dev, double *grad_U_dev, double *grad_t_dev,
                  double *grad_n0_dev, void *stream);

@@ -1,12 +1,527 @@
 // Discrete adjoint of the RK4 integration of Eq. 9.
+//
+// Loss (linearised by the caller): L = sum_t sum_k g_t,k <n_k>(t), with
+// <n_k>(t) = (1/M) sum_m Re rho^m_kk(t) + 1/2 (Eq. 5), so each sample's
+// cotangent gets g_t,k / M on the diagonal at every output step.
+//
+// Per sample (one CTA): forward integration storing a checkpoint every
+// ckpt_every steps; then, segment by segment backwards, the segment is
+// replayed from its checkpoint (all its states kept), and each step is
+// reversed stage by stage.  For y_{n+1} = y_n + h/6 (k1 + 2 k2 + 2 k3 + k4)
+// with stage states Y1 = y_n, Y2 = y_n + h/2 k1, Y3 = y_n + h/2 k2,
+// Y4 = y_n + h k3 and cotangent lam of y_{n+1}:
+//   G4 = h/6 lam;  w4 = VJP(Y4)[G4];  G3 = h/3 lam + h w4
+//   w3 = VJP(Y3)[G3];  G2 = h/3 lam + h/2 w3
+//   w2 = VJP(Y2)[G2];  G1 = h/6 lam + h/2 w2
+//   w1 = VJP(Y1)[G1];  lam_n = lam + w1 + w2 + w3 + w4
+// Under the real inner product <A, B> = Re tr(A^dagger B):
+//   VJP_f(Y)[v] = -f_D(v)  with D = diag(Re Y_kk,sbar + 1/2) held fixed, plus
+//   the coupling of f's U term to the other spin's diagonal,
+//   (w_sbar)_kk += c_k = -2U sum_j Im(conj(v_kj) Y_kj)  (full row k of spin s);
+//   dL/dU    += sum_ij (d_i - d_j)(-Im(conj(v_ij) Y_ij));
+//   dL/dt_b  += sum over elements (i, j) of -Im(conj(v_ij) Y_ik) for the
+//               row-part neighbours k of j (bond (j, k)) and
+//               +Im(conj(v_ij) Y_kj) for the column-part neighbours k of i
+//               (bond (i, k)).
+// Sums over all ordered (i, j) are taken over the stored upper triangle with
+// weight 2 off the diagonal and 1 on it (v and Y are Hermitian).  Finally
+// rho_ii(0) = n_i - 1/2 and rho_ij(0) = xi_ij s_ij(n) (Eq. 12) give
+//   dL/dn_i += Re lam_ii(0) + sum_{j != i} Re(conj(lam_ij) xi_ij) (1 - 2 n_j)/(2 s_ij)
+// (pairs with s_ij = 0 are skipped: the map n -> s is not differentiable there).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
 #include "ftwa_internal.h"
 
 namespace ftwa {
 
-int launch_adjoint(Plan *, uint64_t, int64_t, int64_t, int32_t, const double *, double *, double *, double *,
-                   cudaStream_t)
+namespace adj {
+
+template <typename T> struct C2T;
+template <> struct C2T<float> { using type = float2; };
+template <> struct C2T<double> { using type = double2; };
+
+constexpr int kThreadsA = 512;
+
+template <typename T>
+struct AdjArgs {
+    int N, B, NE;                 // sites, bonds, packed elements (both spins)
+    const int32_t *nbr;           // [N] packed slots
+    const int32_t *nbr_bond;      // [N][3] bond of each slot (-1 if none)
+    const T *tnb;                 // [N][4]
+    const double *nocc;           // [2][N] initial occupations
+    T U, dt;
+    int out_every, ckpt_every;
+    long long n_steps, M;
+    unsigned long long seed;
+    const double *dL;             // [n_out][2N]
+    double *gU, *gt, *gn;         // outputs (accumulated with atomics)
+    typename C2T<T>::type *ws;    // per-CTA workspace
+    long long ws_stride;          // elements per CTA
+    int *status;
+};
+
+// packed index of (s, a, b), a <= b
+__device__ __forceinline__ int pidx(int N, int s, int a, int b)
 {
-    return FTWA_ERR_UNSUPPORTED;
+    return s * (N * (N + 1) / 2) + a * N - a * (a - 1) / 2 + (b - a);
+}
+
+template <typename V>
+__device__ __forceinline__ V getc(const V *buf, int N, int s, int a, int b)
+{
+    if (a <= b) return buf[pidx(N, s, a, b)];
+    V v = buf[pidx(N, s, b, a)];
+    v.y = -v.y;
+    return v;
+}
+
+// Philox4x32-10 and the Box-Muller normal of Eq. 12 (same counter layout as
+// the sampler: key (seed_lo, seed_hi), counter (m_lo, m_hi, s, p))
+__device__ __forceinline__ double2 xi_of(unsigned long long seed, long long m, int s, uint32_t p)
+{
+    uint32_t c0 = (uint32_t)m, c1 = (uint32_t)((unsigned long long)m >> 32), c2 = (uint32_t)s, c3 = p;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    const unsigned long long b1 = ((unsigned long long)c1 << 32) | c0;
+    const unsigned long long b2 = ((unsigned long long)c3 << 32) | c2;
+    const double u1 = (double)(b1 >> 11) * 0x1p-53 + 0x1p-54;
+    const double u2 = (double)(b2 >> 11) * 0x1p-53 + 0x1p-54;
+    const double r = sqrt(-2.0 * log(u1)) * 0.70710678118654752440;
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    return make_double2(r * cs, r * sn);
+}
+
+struct Smem {
+    uint32_t *elem;     // [NE]: a | b << 8 | s << 16
+    int32_t *nbr;       // [N]
+    int32_t *bond;      // [N][3]
+    double *cdiag;      // [2][N] diagonal coupling accumulator
+    double *gt;         // [B]
+    double *gn;         // [2][N]
+};
+
+// out = f(y) (Eq. 9) on the packed upper triangle
+template <typename T>
+__device__ void f_eval(const AdjArgs<T> &a, const Smem &sm, const typename C2T<T>::type *y,
+                       typename C2T<T>::type *out)
+{
+    using V = typename C2T<T>::type;
+    const int N = a.N;
+    for (int e = threadIdx.x; e < a.NE; e += blockDim.x) {
+        const uint32_t d = sm.elem[e];
+        const int i = d & 0xFF, j = (d >> 8) & 0xFF, s = d >> 16;
+        const int nj = sm.nbr[j], ni = sm.nbr[i];
+        T hr = T(0), hi = T(0);
+        for (int n = 0; n < ((nj >> 24) & 0xFF); ++n) {
+            const V v = getc(y, N, s, i, (nj >> (8 * n)) & 0xFF);
+            const T t = a.tnb[4 * j + n];
+            hr = fma(t, v.x, hr);
+            hi = fma(t, v.y, hi);
+        }
+        for (int n = 0; n < ((ni >> 24) & 0xFF); ++n) {
+            const V v = getc(y, N, s, (ni >> (8 * n)) & 0xFF, j);
+            const T t = a.tnb[4 * i + n];
+            hr = fma(-t, v.x, hr);
+            hi = fma(-t, v.y, hi);
+        }
+        const V own = y[e];
+        const T g = a.U * (y[pidx(N, 1 - s, i, i)].x - y[pidx(N, 1 - s, j, j)].x);
+        hr = fma(g, own.x, hr);
+        hi = fma(g, own.y, hi);
+        V o;
+        o.x = -hi;
+        o.y = (i == j) ? T(0) : hr;
+        out[e] = o;
+    }
+}
+
+// w = VJP_f(Y)[v]; accumulates dL/dU (register), dL/dt_b and the diagonal
+// coupling (shared memory).  The coupling is added to w after a barrier.
+template <typename T>
+__device__ void vjp(const AdjArgs<T> &a, const Smem &sm, const typename C2T<T>::type *Y,
+                    const typename C2T<T>::type *v, typename C2T<T>::type *w, double &gU)
+{
+    using V = typename C2T<T>::type;
+    const int N = a.N;
+    for (int e = threadIdx.x; e < 2 * N; e += blockDim.x) sm.cdiag[e] = 0.0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < a.NE; e += blockDim.x) {
+        const uint32_t d = sm.elem[e];
+        const int i = d & 0xFF, j = (d >> 8) & 0xFF, s = d >> 16;
+        const int nj = sm.nbr[j], ni = sm.nbr[i];
+        const double wgt = i == j ? 1.0 : 2.0;
+        const V vo = v[e], yo = Y[e];
+        T hr = T(0), hi = T(0);
+        // row part: neighbours k of j, bond (j, k)
+        for (int n = 0; n < ((nj >> 24) & 0xFF); ++n) {
+            const int k = (nj >> (8 * n)) & 0xFF;
+            const T t = a.tnb[4 * j + n];
+            const V vk = getc(v, N, s, i, k), yk = getc(Y, N, s, i, k);
+            hr = fma(t, vk.x, hr);
+            hi = fma(t, vk.y, hi);
+            // -Im(conj(v_ij) Y_ik)
+            const double im = (double)vo.x * yk.y - (double)vo.y * yk.x;
+            atomicAdd(&sm.gt[sm.bond[3 * j + n]], -wgt * im);
+        }
+        // column part: neighbours k of i, bond (i, k)
+        for (int n = 0; n < ((ni >> 24) & 0xFF); ++n) {
+            const int k = (ni >> (8 * n)) & 0xFF;
+            const T t = a.tnb[4 * i + n];
+            const V vk = getc(v, N, s, k, j), yk = getc(Y, N, s, k, j);
+            hr = fma(-t, vk.x, hr);
+            hi = fma(-t, vk.y, hi);
+            // +Im(conj(v_ij) Y_kj)
+            const double im = (double)vo.x * yk.y - (double)vo.y * yk.x;
+            atomicAdd(&sm.gt[sm.bond[3 * i + n]], wgt * im);
+        }
+        const T di = Y[pidx(N, 1 - s, i, i)].x, dj = Y[pidx(N, 1 - s, j, j)].x;
+        const T g = a.U * (di - dj);
+        hr = fma(g, vo.x, hr);
+        hi = fma(g, vo.y, hi);
+        // w = -i (hr + i hi) = (hi, -hr)
+        V o;
+        o.x = hi;
+        o.y = (i == j) ? T(0) : -hr;
+        w[e] = o;
+        if (i != j) {
+            // P = Im(conj(v_ij) Y_ij)
+            const double P = (double)vo.x * yo.y - (double)vo.y * yo.x;
+            gU += wgt * (double)(di - dj) * (-P);
+            atomicAdd(&sm.cdiag[s * N + i], -2.0 * (double)a.U * P);
+            atomicAdd(&sm.cdiag[s * N + j], 2.0 * (double)a.U * P);
+        }
+    }
+    __syncthreads();
+    // coupling to the other spin's diagonal
+    for (int e = threadIdx.x; e < 2 * N; e += blockDim.x) {
+        const int s = e / N, k = e % N;
+        V &x = w[pidx(N, 1 - s, k, k)];
+        x.x += (T)sm.cdiag[e];
+    }
+    __syncthreads();
+}
+
+template <typename V, typename T>
+__device__ __forceinline__ void axpy(int NE, V *out, const V *x, T c, const V *y)   // out = x + c y
+{
+    for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+        V r;
+        r.x = fma(c, y[e].x, x[e].x);
+        r.y = fma(c, y[e].y, x[e].y);
+        out[e] = r;
+    }
+    __syncthreads();
+}
+
+// one RK4 step: y1 = y0 + h/6 (k1 + 2 k2 + 2 k3 + k4) (k, ys, acc scratch)
+template <typename T>
+__device__ void rk4(const AdjArgs<T> &a, const Smem &sm, const typename C2T<T>::type *y0,
+                    typename C2T<T>::type *y1, typename C2T<T>::type *k, typename C2T<T>::type *ys,
+                    typename C2T<T>::type *acc)
+{
+    const T h = a.dt;
+    f_eval(a, sm, y0, k);
+    __syncthreads();
+    for (int e = threadIdx.x; e < a.NE; e += blockDim.x) {
+        acc[e] = k[e];
+        ys[e].x = fma(h * T(0.5), k[e].x, y0[e].x);
+        ys[e].y = fma(h * T(0.5), k[e].y, y0[e].y);
+    }
+    __syncthreads();
+    f_eval(a, sm, ys, k);
+    __syncthreads();
+    for (int e = threadIdx.x; e < a.NE; e += blockDim.x) {
+        acc[e].x = fma(T(2), k[e].x, acc[e].x);
+        acc[e].y = fma(T(2), k[e].y, acc[e].y);
+        ys[e].x = fma(h * T(0.5), k[e].x, y0[e].x);
+        ys[e].y = fma(h * T(0.5), k[e].y, y0[e].y);
+    }
+    __syncthreads();
+    f_eval(a, sm, ys, k);
+    __syncthreads();
+    for (int e = threadIdx.x; e < a.NE; e += blockDim.x) {
+        acc[e].x = fma(T(2), k[e].x, acc[e].x);
+        acc[e].y = fma(T(2), k[e].y, acc[e].y);
+        ys[e].x = fma(h, k[e].x, y0[e].x);
+        ys[e].y = fma(h, k[e].y, y0[e].y);
+    }
+    __syncthreads();
+    f_eval(a, sm, ys, k);
+    __syncthreads();
+    for (int e = threadIdx.x; e < a.NE; e += blockDim.x) {
+        y1[e].x = fma(h / T(6), acc[e].x + k[e].x, y0[e].x);
+        y1[e].y = fma(h / T(6), acc[e].y + k[e].y, y0[e].y);
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreadsA, 1) adjoint_kernel(const AdjArgs<T> a)
+{
+    using V = typename C2T<T>::type;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int N = a.N, NE = a.NE;
+    Smem sm;
+    unsigned char *p = smem;
+    sm.cdiag = reinterpret_cast<double *>(p);
+    p += sizeof(double) * 2 * N;
+    sm.gt = reinterpret_cast<double *>(p);
+    p += sizeof(double) * std::max(a.B, 1);
+    sm.gn = reinterpret_cast<double *>(p);
+    p += sizeof(double) * 2 * N;
+    sm.nbr = reinterpret_cast<int32_t *>(p);
+    p += sizeof(int32_t) * N;
+    sm.bond = reinterpret_cast<int32_t *>(p);
+    p += sizeof(int32_t) * 3 * N;
+    sm.elem = reinterpret_cast<uint32_t *>(p);
+
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        sm.nbr[i] = a.nbr[i];
+        for (int n = 0; n < 3; ++n) sm.bond[3 * i + n] = a.nbr_bond[3 * i + n];
+    }
+    for (int i = threadIdx.x; i < a.B; i += blockDim.x) sm.gt[i] = 0.0;
+    for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) sm.gn[i] = 0.0;
+    for (int s = 0; s < 2; ++s)
+        for (int i = 0; i < N; ++i)
+            for (int j = i + threadIdx.x; j < N; j += blockDim.x) sm.elem[pidx(N, s, i, j)] = i | (j << 8) | (s << 16);
+    __syncthreads();
+
+    const int n_seg = (int)(a.n_steps / a.ckpt_every);
+    V *ws = a.ws + (long long)blockIdx.x * a.ws_stride;
+    V *ckpt = ws;                                         // [n_seg][NE]
+    V *seg = ckpt + (long long)n_seg * NE;                // [ckpt_every + 1][NE]
+    V *Y2 = seg + (long long)(a.ckpt_every + 1) * NE;
+    V *Y3 = Y2 + NE, *Y4 = Y3 + NE, *K = Y4 + NE, *A = K + NE, *lam = A + NE, *G = lam + NE, *W = G + NE,
+      *lam_new = W + NE, *cur = lam_new + NE, *nxt = cur + NE;
+    const T h = a.dt;
+    const int twoN = 2 * N;
+    const double invM = 1.0 / (double)a.M;
+    double gU = 0.0;
+
+    for (long long m = blockIdx.x; m < a.M; m += gridDim.x) {
+        // ---- rho(0) of sample m (Eq. 12) --------------------------------------
+        for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+            const uint32_t d = sm.elem[e];
+            const int i = d & 0xFF, j = (d >> 8) & 0xFF, s = d >> 16;
+            const double ni = a.nocc[s * N + i], nj = a.nocc[s * N + j];
+            V v;
+            if (i == j) {
+                v.x = (T)(ni - 0.5);
+                v.y = T(0);
+            } else {
+                const double var = 0.5 * (ni + nj - 2.0 * ni * nj);
+                const double sd = var > 0.0 ? sqrt(var) : 0.0;
+                const double2 x = xi_of(a.seed, m, s, (uint32_t)(i * N - i * (i + 1) / 2 + (j - i - 1)));
+                v.x = (T)(x.x * sd);
+                v.y = (T)(x.y * sd);
+            }
+            cur[e] = v;
+        }
+        __syncthreads();
+        // ---- forward with checkpoints ------------------------------------------
+        for (long long step = 0; step < a.n_steps; ++step) {
+            if (step % a.ckpt_every == 0) {
+                V *c = ckpt + (step / a.ckpt_every) * NE;
+                for (int e = threadIdx.x; e < NE; e += blockDim.x) c[e] = cur[e];
+                __syncthreads();
+            }
+            rk4(a, sm, cur, nxt, K, Y2, A);
+            V *t = cur;
+            cur = nxt;
+            nxt = t;
+        }
+        // ---- cotangent at the final step --------------------------------------------
+        for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+            lam[e].x = T(0);
+            lam[e].y = T(0);
+        }
+        __syncthreads();
+        auto inject = [&](long long step) {
+            if (step % a.out_every) return;
+            const double *g = a.dL + (step / a.out_every) * twoN;
+            for (int e = threadIdx.x; e < twoN; e += blockDim.x) {
+                const int s = e / N, k = e % N;
+                lam[pidx(N, s, k, k)].x += (T)(g[e] * invM);
+            }
+            __syncthreads();
+        };
+        inject(a.n_steps);
+        // ---- reverse sweep ----------------------------------------------------------
+        for (int sg = n_seg - 1; sg >= 0; --sg) {
+            for (int e = threadIdx.x; e < NE; e += blockDim.x) seg[e] = ckpt[(long long)sg * NE + e];
+            __syncthreads();
+            for (int r = 0; r < a.ckpt_every; ++r) rk4(a, sm, seg + (long long)r * NE, seg + (long long)(r + 1) * NE, K, Y2, A);
+            for (int r = a.ckpt_every - 1; r >= 0; --r) {
+                const V *y = seg + (long long)r * NE;
+                // stage states
+                f_eval(a, sm, y, K);
+                __syncthreads();
+                axpy(NE, Y2, y, h * T(0.5), K);
+                f_eval(a, sm, Y2, K);
+                __syncthreads();
+                axpy(NE, Y3, y, h * T(0.5), K);
+                f_eval(a, sm, Y3, K);
+                __syncthreads();
+                axpy(NE, Y4, y, h, K);
+                // stage 4
+                for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+                    G[e].x = h / T(6) * lam[e].x;
+                    G[e].y = h / T(6) * lam[e].y;
+                    lam_new[e] = lam[e];
+                }
+                __syncthreads();
+                vjp(a, sm, Y4, G, W, gU);
+                for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+                    lam_new[e].x += W[e].x;
+                    lam_new[e].y += W[e].y;
+                    G[e].x = fma(h, W[e].x, h / T(3) * lam[e].x);
+                    G[e].y = fma(h, W[e].y, h / T(3) * lam[e].y);
+                }
+                __syncthreads();
+                vjp(a, sm, Y3, G, W, gU);
+                for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+                    lam_new[e].x += W[e].x;
+                    lam_new[e].y += W[e].y;
+                    G[e].x = fma(h * T(0.5), W[e].x, h / T(3) * lam[e].x);
+                    G[e].y = fma(h * T(0.5), W[e].y, h / T(3) * lam[e].y);
+                }
+                __syncthreads();
+                vjp(a, sm, Y2, G, W, gU);
+                for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+                    lam_new[e].x += W[e].x;
+                    lam_new[e].y += W[e].y;
+                    G[e].x = fma(h * T(0.5), W[e].x, h / T(6) * lam[e].x);
+                    G[e].y = fma(h * T(0.5), W[e].y, h / T(6) * lam[e].y);
+                }
+                __syncthreads();
+                vjp(a, sm, y, G, W, gU);
+                for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+                    lam[e].x = lam_new[e].x + W[e].x;
+                    lam[e].y = lam_new[e].y + W[e].y;
+                }
+                __syncthreads();
+                inject((long long)sg * a.ckpt_every + r);
+            }
+        }
+        // ---- initial occupations -------------------------------------------------------
+        for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+            const uint32_t d = sm.elem[e];
+            const int i = d & 0xFF, j = (d >> 8) & 0xFF, s = d >> 16;
+            if (i == j) {
+                atomicAdd(&sm.gn[s * N + i], (double)lam[e].x);
+            } else {
+                const double ni = a.nocc[s * N + i], nj = a.nocc[s * N + j];
+                const double var = 0.5 * (ni + nj - 2.0 * ni * nj);
+                if (var > 0.0) {
+                    const double sd = sqrt(var);
+                    const double2 x = xi_of(a.seed, m, s, (uint32_t)(i * N - i * (i + 1) / 2 + (j - i - 1)));
+                    const double re = (double)lam[e].x * x.x + (double)lam[e].y * x.y;   // Re(conj(lam) xi)
+                    atomicAdd(&sm.gn[s * N + i], re * (1.0 - 2.0 * nj) / (2.0 * sd));
+                    atomicAdd(&sm.gn[s * N + j], re * (1.0 - 2.0 * ni) / (2.0 * sd));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // ---- publish this CTA's sums -------------------------------------------------
+    __shared__ double red[kThreadsA / 32];
+    double v = gU;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+        if (a.gU) atomicAdd(a.gU, t);
+    }
+    for (int i = threadIdx.x; i < a.B; i += blockDim.x)
+        if (a.gt) atomicAdd(&a.gt[i], sm.gt[i]);
+    for (int i = threadIdx.x; i < 2 * N; i += blockDim.x)
+        if (a.gn) atomicAdd(&a.gn[i], sm.gn[i]);
+}
+
+__global__ void zero_kernel(double *x, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = 0.0;
+}
+
+}  // namespace adj
+
+template <typename T>
+static int launch_adjoint_t(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, int32_t ckpt_every, const double *dL,
+                            double *gU, double *gt, double *gn, cudaStream_t s)
+{
+    using namespace adj;
+    using V = typename C2T<T>::type;
+    const int N = p->N;
+    const int NE = N * (N + 1);
+    const int n_seg = (int)(n_steps / ckpt_every);
+    const long long stride = (long long)(n_seg + ckpt_every + 1 + 12) * NE;
+    const int grid = (int)std::min<long long>(M, std::max(1, p->sm_count));
+    const size_t bytes = sizeof(V) * (size_t)stride * grid;
+    if (p->adj_ws_bytes < bytes) {
+        cudaFree(p->d_adj_ws);
+        p->d_adj_ws = nullptr;
+        p->adj_ws_bytes = 0;
+        cudaError_t e = cudaMalloc(&p->d_adj_ws, bytes);
+        if (e != cudaSuccess) return set_cuda_error(e);
+        p->adj_ws_bytes = bytes;
+    }
+    // the kernel accumulates with atomics: start from zero
+    if (gU) zero_kernel<<<1, 32, 0, s>>>(gU, 1);
+    if (gt && p->B) zero_kernel<<<(p->B + 255) / 256, 256, 0, s>>>(gt, p->B);
+    if (gn) zero_kernel<<<(2 * N + 255) / 256, 256, 0, s>>>(gn, 2 * N);
+    AdjArgs<T> a;
+    a.N = N;
+    a.B = p->B;
+    a.NE = NE;
+    a.nbr = p->d_nbr;
+    a.nbr_bond = p->d_nbr_bond;
+    a.tnb = std::is_same<T, double>::value ? reinterpret_cast<const T *>(p->d_t64)
+                                           : reinterpret_cast<const T *>(p->d_t32);
+    a.nocc = p->d_n;
+    a.U = (T)p->U;
+    a.dt = (T)p->dt;
+    a.out_every = p->out_every;
+    a.ckpt_every = ckpt_every;
+    a.n_steps = n_steps;
+    a.M = M;
+    a.seed = seed;
+    a.dL = dL;
+    a.gU = gU;
+    a.gt = gt;
+    a.gn = gn;
+    a.ws = reinterpret_cast<V *>(p->d_adj_ws);
+    a.ws_stride = stride;
+    a.status = p->d_status;
+    const int smem = (int)(sizeof(double) * (4 * N + std::max(p->B, 1)) + sizeof(int32_t) * 4 * N +
+                           sizeof(uint32_t) * NE + 64);
+    if (smem > 227 * 1024) return FTWA_ERR_UNSUPPORTED;
+    cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    adjoint_kernel<T><<<grid, kThreadsA, smem, s>>>(a);
+    return set_cuda_error(cudaGetLastError());
+}
+
+int launch_adjoint(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, int32_t ckpt_every, const double *dL,
+                   double *gU, double *gt, double *gn, cudaStream_t s)
+{
+    if (p->precision == FTWA_FP64) return launch_adjoint_t<double>(p, seed, M, n_steps, ckpt_every, dL, gU, gt, gn, s);
+    return launch_adjoint_t<float>(p, seed, M, n_steps, ckpt_every, dL, gU, gt, gn, s);
 }
 
 }  // namespace ftwa

@@ -64,6 +64,8 @@ struct Plan {
     int32_t *d_bonds = nullptr;       // [B][2]
     int *d_status = nullptr;          // device status word
     void *d_ws = nullptr;             // plan-owned workspace (moments, adjoint)
+    void *d_adj_ws = nullptr;         // adjoint per-CTA workspace
+    size_t adj_ws_bytes = 0;
     uint32_t *d_items = nullptr;      // banded stepper work items
     size_t items_bytes = 0;
     int variant_override = 0;         // 0 auto, 1 banded only, 2 general only

@@ -32,6 +32,9 @@ static void free_tables(Plan *p)
     cudaFree(p->d_status);
     cudaFree(p->d_ws);
     cudaFree(p->d_items);
+    cudaFree(p->d_adj_ws);
+    p->d_adj_ws = nullptr;
+    p->adj_ws_bytes = 0;
     p->d_items = nullptr;
     p->items_bytes = 0;
     p->d_ws = nullptr;

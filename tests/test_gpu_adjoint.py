@@ -1,0 +1,87 @@
+"""GPU discrete adjoint against central finite differences of the CPU oracle.
+
+Loss L = sum_{t=0..T} sum_k (<n_k>(t) - target_tk)^2 over the output rows;
+its gradient with respect to U, every bond hopping t_b and every initial
+occupation n_i,s is computed by the adjoint from dL/d<n> = 2(<n> - target)
+and compared with central differences (h = 1e-5, common random numbers:
+same seed) of the oracle.  Occupations are softened (0.05 / 0.95) so that
+every noise scale s_ij of Eq. 12 is positive.  Gate (FP64): relative error
+<= 1e-6.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ftwa():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2212_04352_gb300 as F
+    F.load()
+    return F
+
+
+def _loss(lat, U, nu, nd, seed, M, steps, every, target, t_bond):
+    snap, _ = oracle.run(lat, U, nu, nd, seed, 0, M, 0.01, steps, every, t_bond=t_bond)
+    occ = snap.mean(axis=1) + 0.5
+    return float(((occ - target) ** 2).sum()), occ
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-6), (1, 2e-3)])
+def test_adjoint_matches_finite_differences(ftwa, precision, tol):
+    lat = W.hexagon_chain(2)
+    n0u, n0d = W.neel_state(lat)
+    nu, nd = W.softened(n0u), W.softened(n0d)
+    U, seed, M, steps, every, ckpt = 1.6, 5, 6, 40, 10, 20
+    rng = np.random.default_rng(0)
+    target = 0.5 + 0.1 * rng.standard_normal((steps // every + 1, 2 * lat.n_sites))
+    tb = np.array(lat.t_bond, dtype=np.float64)
+    L0, occ = _loss(lat, U, nu, nd, seed, M, steps, every, target, tb)
+    g = torch.from_numpy(2.0 * (occ - target)).cuda()
+    with ftwa.Plan(lat, U, n_up=nu, n_dn=nd, precision=precision, out_every=every) as P:
+        gU, gt, gn = P.adjoint(seed, M, steps, ckpt, g)
+        assert P.status() == 0
+    gU, gt, gn = gU.item(), gt.cpu().numpy(), gn.cpu().numpy()
+
+    h = 1e-5
+    def fd(fn):
+        return (fn(h) - fn(-h)) / (2 * h)
+    fdU = fd(lambda d: _loss(lat, U + d, nu, nd, seed, M, steps, every, target, tb)[0])
+    fdt = np.array([fd(lambda d, b=b: _loss(lat, U, nu, nd, seed, M, steps, every, target,
+                                            tb + d * (np.arange(lat.n_bonds) == b))[0])
+                    for b in range(lat.n_bonds)])
+    fdn = np.zeros((2, lat.n_sites))
+    for s in range(2):
+        for i in range(lat.n_sites):
+            def Ln(d):
+                a, b = nu.copy(), nd.copy()
+                (a if s == 0 else b)[i] += d
+                return _loss(lat, U, a, b, seed, M, steps, every, target, tb)[0]
+            fdn[s, i] = fd(Ln)
+    scale = max(abs(fdU), np.abs(fdt).max(), np.abs(fdn).max())
+    assert abs(gU - fdU) <= tol * scale
+    assert np.max(np.abs(gt - fdt)) <= tol * scale
+    assert np.max(np.abs(gn - fdn)) <= tol * scale
+
+
+def test_adjoint_checkpoint_invariance(ftwa):
+    """The gradient does not depend on the checkpoint spacing (FP64)."""
+    lat = W.periodic_honeycomb()
+    nu, nd = W.softened(W.neel_state(lat)[0]), W.softened(W.neel_state(lat)[1])
+    g = torch.full((5, 16), 0.3, dtype=torch.float64, device="cuda")
+    out = []
+    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=0, out_every=10) as P:
+        for ck in (10, 20, 40):
+            out.append([x.cpu().numpy() for x in P.adjoint(3, 4, 40, ck, g)])
+        assert P.status() == 0
+    for o in out[1:]:
+        for a, b in zip(o, out[0]):
+            np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-14)

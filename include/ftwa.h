@@ -236,6 +236,31 @@ int ftwa_adjoint(ftwa_plan_t *plan, uint64_t seed, int64_t M, int64_t n_steps, i
 int ftwa_moments_noalloc(const void *snap_dev, int32_t precision, int32_t n_sites, int64_t M, int32_t n_times,
                          double *occ_dev, double *conn_dev, double *g2_dev, void *stream);
 
+/* Launch-shape autotuner: times every feasible stepper shape of the plan
+ * (variant 1 banded / 2 packed triangle x CTAs per sample 1, 2, 4, 8) on a
+ * probe integration of probe_steps steps of min(M, 8192) samples and pins the
+ * fastest in the plan (ftwa_get_info reports it).  Synchronous: allocates
+ * and frees a temporary state buffer and waits for the probes on `stream`.
+ * Errors: FTWA_ERR_INVALID_ARGUMENT, FTWA_ERR_UNSUPPORTED (no feasible
+ * shape), FTWA_ERR_OUT_OF_MEMORY, FTWA_ERR_CUDA. */
+int ftwa_autotune(ftwa_plan_t *plan, int64_t M, int32_t probe_steps, void *stream);
+
+/* Batched launch of heterogeneous problems (lattices of uneven size,
+ * several U): one CUDA graph whose branches are the persistent steppers of
+ * the n plans (plans[i] advancing rho_dev[i], M[i] samples, n_steps steps,
+ * snapshots into snap_dev[i] if snap_dev and snap_dev[i] are not NULL), all
+ * launched by one ftwa_batch_launch.  Shapes are fixed when the batch is
+ * created (run ftwa_autotune first to tune them); plans and buffers must
+ * outlive the batch.  Errors: FTWA_ERR_INVALID_ARGUMENT, FTWA_ERR_UNSUPPORTED,
+ * FTWA_ERR_OUT_OF_MEMORY, FTWA_ERR_CUDA. */
+typedef struct ftwa_batch ftwa_batch_t;
+int ftwa_batch_create(ftwa_plan_t *const *plans, int32_t n, void *const *rho_dev, const int64_t *M, int64_t n_steps,
+                      void *const *snap_dev, ftwa_batch_t **out);
+/* Replay the batch's graph on `stream`. */
+int ftwa_batch_launch(ftwa_batch_t *batch, void *stream);
+/* Release a batch (NULL is accepted). */
+void ftwa_batch_destroy(ftwa_batch_t *batch);
+
 /* Synchronise `stream`, then return and clear the plan's device status word
  * (FTWA_OK, FTWA_ERR_DEVICE_TIMEOUT or FTWA_ERR_NONFINITE), or FTWA_ERR_CUDA
  * if the synchronisation itself failed. */

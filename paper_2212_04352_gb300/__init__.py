@@ -20,7 +20,7 @@ from ._lib import (  # noqa: F401
     FTWA_FP32, FTWA_FP64, FTWA_GRAM_BF16X3, FTWA_GRAM_FP64, FtwaError, check, load,
 )
 
-__all__ = ["Plan", "plan", "philox", "moments_noalloc", "FTWA_FP32", "FTWA_FP64", "FTWA_GRAM_FP64", "FTWA_GRAM_BF16X3",
+__all__ = ["Plan", "Batch", "plan", "philox", "moments_noalloc", "FTWA_FP32", "FTWA_FP64", "FTWA_GRAM_FP64", "FTWA_GRAM_BF16X3",
            "FtwaError", "load"]
 
 
@@ -148,6 +148,11 @@ class Plan:
                                   _ptr(gt), _ptr(gn), _stream(stream)), "ftwa_adjoint")
         return gU, gt, gn
 
+    def autotune(self, M, probe_steps=20, stream=None):
+        """Time every feasible stepper shape and pin the fastest (synchronous)."""
+        check(load().ftwa_autotune(self._h, int(M), int(probe_steps), _stream(stream)), "ftwa_autotune")
+        return self.info()
+
     def status(self, stream=None):
         """Synchronise the stream and return (and clear) the device status word."""
         return int(load().ftwa_status(self._h, _stream(stream)))
@@ -158,6 +163,40 @@ class Plan:
 
 def plan(lattice, U, **kw) -> Plan:
     return Plan(lattice, U, **kw)
+
+
+class Batch:
+    """One CUDA graph advancing several plans' samples (ftwa_batch_*)."""
+
+    def __init__(self, plans, rhos, n_steps, snaps=None):
+        n = len(plans)
+        self._plans = list(plans)          # keep the plans and buffers alive
+        self._rhos = list(rhos)
+        self._snaps = list(snaps) if snaps is not None else None
+        P = ctypes.c_void_p
+        hp = (P * n)(*[pl._h for pl in plans])
+        hr = (P * n)(*[r.data_ptr() for r in rhos])
+        hm = (ctypes.c_int64 * n)(*[r.shape[0] for r in rhos])
+        hs = None
+        if snaps is not None:
+            hs = (P * n)(*[0 if x is None else x.data_ptr() for x in snaps])
+        h = P()
+        check(load().ftwa_batch_create(hp, n, hr, hm, int(n_steps), hs, ctypes.byref(h)), "ftwa_batch_create")
+        self._h = h
+
+    def launch(self, stream=None):
+        check(load().ftwa_batch_launch(self._h, _stream(stream)), "ftwa_batch_launch")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ftwa_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def moments_noalloc(X, precision, n_sites, g2=True, stream=None, out=None):

@@ -24,8 +24,9 @@ FTWA_MOMENTS_NOALLOC_MAX_TK = 131072
 
 # every symbol include/ftwa.h declares
 EXPORTS = ("ftwa_plan", "ftwa_destroy", "ftwa_get_info", "ftwa_sample", "ftwa_philox", "ftwa_evolve",
-           "ftwa_moments", "ftwa_moments_noalloc", "ftwa_adjoint", "ftwa_status", "ftwa_debug_force_timeout",
-           "ftwa_error_string", "ftwa_version")
+           "ftwa_moments", "ftwa_moments_noalloc", "ftwa_adjoint", "ftwa_autotune", "ftwa_batch_create",
+           "ftwa_batch_launch", "ftwa_batch_destroy", "ftwa_status", "ftwa_debug_force_timeout", "ftwa_error_string",
+           "ftwa_version")
 
 
 class Lattice(ctypes.Structure):
@@ -79,13 +80,18 @@ def load(path: str = LIB_PATH):
     lib.ftwa_moments.argtypes = [P, P, i64, i32, P, P, P, i32, P]
     lib.ftwa_moments_noalloc.argtypes = [P, i32, i32, i64, i32, P, P, P, P]
     lib.ftwa_adjoint.argtypes = [P, u64, i64, i64, i32, P, P, P, P, P]
+    lib.ftwa_autotune.argtypes = [P, i64, i32, P]
+    lib.ftwa_batch_create.argtypes = [P, i32, P, P, i64, P, ctypes.POINTER(P)]
+    lib.ftwa_batch_launch.argtypes = [P, P]
+    lib.ftwa_batch_destroy.argtypes = [P]
+    lib.ftwa_batch_destroy.restype = None
     lib.ftwa_status.argtypes = [P, P]
     lib.ftwa_debug_force_timeout.argtypes = [P, i32]
     lib.ftwa_error_string.argtypes = [ctypes.c_int]
     lib.ftwa_error_string.restype = ctypes.c_char_p
     lib.ftwa_version.restype = ctypes.c_int
     for name in ("ftwa_plan", "ftwa_get_info", "ftwa_sample", "ftwa_philox", "ftwa_evolve", "ftwa_moments",
-                 "ftwa_moments_noalloc",
+                 "ftwa_moments_noalloc", "ftwa_autotune", "ftwa_batch_create", "ftwa_batch_launch",
                  "ftwa_adjoint", "ftwa_status", "ftwa_debug_force_timeout"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib

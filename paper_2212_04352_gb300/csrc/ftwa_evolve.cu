@@ -1103,7 +1103,7 @@ static int dispatch_t(Plan *p, StepperShape &sh, void *rho, int64_t M, int64_t n
     }
     p->shape = sh;
     p->shape.variant = 2;
-    if (M == 0) return FTWA_OK;
+    if (M == 0 || p->dry_run) return FTWA_OK;
     return p->uniform_t ? launch_t<T, CLUSTER, true>(p, sh, rho, M, n_steps, snap, s)
                         : launch_t<T, CLUSTER, false>(p, sh, rho, M, n_steps, snap, s);
 }
@@ -1286,15 +1286,20 @@ static int band_launch(Plan *p, BandShape &sh, void *rho, int64_t M, int64_t n_s
         if (e != cudaSuccess) return set_cuda_error(e);
         p->items_bytes = bytes;
     }
-    e = cudaMemcpyAsync(p->d_items, sh.items.data(), bytes, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return set_cuda_error(e);
+    if (p->items_host != sh.items) {
+        // a changed table is uploaded (never during stream capture: batch
+        // creation prepares every plan first)
+        e = cudaMemcpyAsync(p->d_items, sh.items.data(), bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return set_cuda_error(e);
+        p->items_host = sh.items;
+    }
     p->shape.cluster = sh.cluster;
     p->shape.slots = sh.slots;
     p->shape.units_per_warp = sh.E;
     p->shape.smem_bytes = sh.smem_bytes;
     p->shape.grid = sh.grid;
     p->shape.variant = 1;
-    if (M == 0) return FTWA_OK;
+    if (M == 0 || p->dry_run) return FTWA_OK;
     BandArgs<T> a{};
     a.nbr = p->d_nbr;
     a.tnb = std::is_same<T, double>::value ? reinterpret_cast<const T *>(p->d_t64)

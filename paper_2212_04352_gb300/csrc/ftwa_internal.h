@@ -68,6 +68,8 @@ struct Plan {
     size_t adj_ws_bytes = 0;
     uint32_t *d_items = nullptr;      // banded stepper work items
     size_t items_bytes = 0;
+    std::vector<uint32_t> items_host; // copy of the table last uploaded
+    bool dry_run = false;             // choose the shape and upload tables, launch nothing
     int variant_override = 0;         // 0 auto, 1 banded only, 2 general only
     size_t ws_bytes = 0;
     StepperShape shape;               // chosen for the full machine
@@ -88,3 +90,6 @@ int launch_adjoint(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, int32_t c
                    double *gU, double *gt, double *gn, cudaStream_t s);
 
 }  // namespace ftwa
+
+// The opaque handle of the C ABI is the plan itself.
+struct ftwa_plan : public ftwa::Plan {};

@@ -10,8 +10,6 @@
 
 #include "ftwa_internal.h"
 
-struct ftwa_plan : public ftwa::Plan {};
-
 namespace ftwa {
 
 int set_cuda_error(cudaError_t e)

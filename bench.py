@@ -204,6 +204,153 @@ def run_reference(args):
                       "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def bench_adjoint(F, args):
+    """Config 4: 96-site hexagonal flake (k = 4), U/t = 1.6, M samples, T = 5
+    (500 RK4 steps, dt = 0.01), checkpoints every 50 steps, outputs every 10
+    steps; loss sum_t,k (<n_k>(t) - target)^2 with a seeded synthetic target;
+    gradients w.r.t. U, all 132 bond hoppings and the 192 initial
+    occupations (softened Fock state 0.05/0.95 so that every noise scale is
+    positive).  Reports the adjoint's wall time and its ratio to the forward
+    pass of the same samples."""
+    import numpy as np
+    import torch
+    import workloads as W
+    lat = W.hexagonal_flake(4)
+    nu, nd = W.neel_state(lat)
+    nu, nd = W.softened(nu), W.softened(nd)
+    M, steps, ck, every = args.adjoint_samples, 500, 50, 10
+    rng = np.random.default_rng(4)
+    target = torch.from_numpy(0.5 + 0.05 * rng.standard_normal((steps // every + 1, 2 * lat.n_sites))).cuda()
+    out = {"workload": f"96-site flake, U/t=1.6, M={M}, T=5 (500 steps), checkpoints every 50",
+           "samples": M}
+    for name, prec in (("fp64", F.FTWA_FP64), ("fp32", F.FTWA_FP32)):
+        P = F.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=prec, out_every=every)
+        rho = P.sample(21, M)
+        a, b = _events()
+        a.record()
+        X = P.evolve(rho, steps)
+        b.record()
+        occ, _, _ = P.moments(X, g2=False)
+        torch.cuda.synchronize()
+        fwd_ms = a.elapsed_time(b)
+        loss = float(((occ - target) ** 2).sum())
+        g = 2.0 * (occ - target)
+        a, b = _events()
+        a.record()
+        gU, gt, gn = P.adjoint(21, M, steps, ck, g)
+        b.record()
+        torch.cuda.synchronize()
+        if P.status() != 0:
+            raise RuntimeError("adjoint device status")
+        out[name] = {"adjoint_s": a.elapsed_time(b) / 1000.0, "forward_s": fwd_ms / 1000.0,
+                     "ratio_to_forward": a.elapsed_time(b) / fwd_ms, "loss": loss, "dL_dU": gU.item(),
+                     "dL_dt_norm": float(gt.norm()), "dL_dn0_norm": float(gn.norm())}
+        P.close()
+        del rho, X
+    return out
+
+
+def bench_batched(F, args):
+    """Config 3: honeycomb flakes of 24, 54, 96, 150 and 198 sites x U/t in
+    {0.5, 1.0, 1.6, 2.5}, M samples each, FP32 state, one CUDA-graph launch
+    of the 20 problems' persistent steppers with autotuned shapes; timed over
+    args.batch_steps RK4 steps."""
+    import torch
+    import workloads as W
+    lats = [W.hexagonal_flake(2), W.hexagonal_flake(3), W.hexagonal_flake(4), W.hexagonal_flake(5),
+            W.brick_wall_flake(11, 18)]
+    Us = [0.5, 1.0, 1.6, 2.5]
+    M, steps = args.batch_samples, args.batch_steps
+    plans, rhos, shapes = [], [], {}
+    t0 = time.perf_counter()
+    for lat in lats:
+        nu, nd = W.neel_state(lat)
+        tuner = F.Plan(lat, Us[0], n_up=nu, n_dn=nd, precision=F.FTWA_FP32)
+        info = tuner.autotune(M, probe_steps=10)
+        shapes[lat.n_sites] = {"variant": info["variant"], "cluster": info["cluster"]}
+        tuner.close()
+        for U in Us:
+            P = F.Plan(lat, U, n_up=nu, n_dn=nd, precision=F.FTWA_FP32, variant=info["variant"],
+                       cluster=info["cluster"])
+            plans.append(P)
+            rhos.append(P.sample(31, M))
+    tune_s = time.perf_counter() - t0
+    B = F.Batch(plans, rhos, steps)
+    B.launch()                      # warm-up
+    torch.cuda.synchronize()
+    a, b = _events()
+    a.record()
+    B.launch()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    for P in plans:
+        if P.status() != 0:
+            raise RuntimeError("batched device status")
+    total = len(plans) * M * steps
+    out = {"workload": f"flakes 24/54/96/150/198 sites x U in {Us}, M={M} each, FP32, {steps} RK4 steps",
+           "problems": len(plans), "value": total / (ms / 1000.0), "unit": UNIT, "ms": ms,
+           "shapes": shapes, "autotune_s": tune_s, "graph_launches": 1}
+    B.close()
+    for P in plans:
+        P.close()
+    return out
+
+
+def bench_gram(F, args):
+    """Config 5 shape: all-pairs connected correlator of M = 65536 samples x
+    396 site-spin occupations at 200 output times, BF16x3 tensor-core Gram
+    against the FP64 Gram.  Snapshots are synthetic FP32 values with the
+    value range of Re rho_ii (uniform in [-1/2, 1/2] plus a per-site mean)."""
+    import torch
+    M, K, T = args.gram_samples, 396, args.gram_times
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    X = (torch.rand((T, M, K), generator=g, device="cuda", dtype=torch.float32) - 0.5)
+    X += 0.1 * torch.rand((1, 1, K), generator=g, device="cuda")
+    import workloads as W
+    lat = W.brick_wall_flake(11, 18)
+    nu, nd = W.neel_state(lat)
+    P = F.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=F.FTWA_FP32)
+    res = {}
+    for name, mode in (("bf16x3", F.FTWA_GRAM_BF16X3), ("fp64", F.FTWA_GRAM_FP64)):
+        P.moments(X, gram_mode=mode, g2=True)       # warm-up (workspace)
+        torch.cuda.synchronize()
+        a, b = _events()
+        a.record()
+        occ, conn, g2 = P.moments(X, gram_mode=mode, g2=True)
+        b.record()
+        torch.cuda.synchronize()
+        res[name] = (a.elapsed_time(b), conn)
+    if P.status() != 0:
+        raise RuntimeError("gram device status")
+    c16, c64 = res["bf16x3"][1], res["fp64"][1]
+    d = torch.sqrt(torch.diagonal(c64, dim1=1, dim2=2).clamp_min(0))
+    stat = d[:, :, None] * d[:, None, :] / (M ** 0.5)        # statistical error scale of C_kl
+    err = ((c16 - c64).abs() / stat.clamp_min(1e-30)).max().item()
+    n_kt = (K + 127) // 128
+    tiles = n_kt * (n_kt + 1) // 2
+    mma_flops = 3 * 2.0 * M * 128 * 128 * tiles * T
+    useful = 2.0 * M * K * (K + 1) / 2 * T
+    pk = peaks()
+    ms16 = res["bf16x3"][0]
+    out = {"workload": f"M={M} samples x K={K} x T={T} times, synthetic FP32 snapshots",
+           "bf16x3_ms": ms16, "fp64_ms": res["fp64"][0], "speedup": res["fp64"][0] / ms16,
+           "bf16_mma_tflops": mma_flops / (ms16 / 1000) / 1e12,
+           "useful_tflops": useful / (ms16 / 1000) / 1e12,
+           "frac_of_bf16_peak": mma_flops / (ms16 / 1000) / 1e12 / pk.get("bf16_tflops", 1912.7),
+           "max_err_over_stat_err": err}
+    P.close()
+    del X, res, c16, c64
+    torch.cuda.empty_cache()
+    return out
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -326,6 +473,14 @@ def run_gpu(args):
                 "fp32_occ_err_over_stderr_max": ratio}
         P64.close()
 
+    extra = {}
+    if not args.no_adjoint:
+        extra["adjoint"] = bench_adjoint(F, args)
+    if not args.no_batch:
+        extra["batched"] = bench_batched(F, args)
+    if not args.no_gram:
+        extra["gram"] = bench_gram(F, args)
+
     # ---- roofline of the dominant kernel (the RK4 stepper) -----------------------
     pk = peaks()
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
@@ -344,7 +499,7 @@ def run_gpu(args):
             "config": config_dict(wl, {"parallelism": f"samples split over {ws} GPU(s), no collective",
                                        "launch": info}),
             "e2e": e2e, "roofline": roof, "clocks": clk, "gpu_launches": 4 * args.steps,
-            "evolve_ms": evolve_ms, "fp64": fp64}
+            "evolve_ms": evolve_ms, "fp64": fp64, **extra}
     if rank == 0 and ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -375,6 +530,28 @@ def run_profile_case(args):
         raise SystemExit(1)
 
 
+def run_profile_gram(args):
+    """A small Gram case for ncu: T = 4 times of M = 65536 synthetic FP32
+    snapshots of the 198-site workload's 396 site-spin occupations."""
+    import torch
+    import paper_2212_04352_gb300 as F
+    import workloads as W
+    M, K, T = 65536, 396, 4
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    X = torch.rand((T, M, K), generator=g, device="cuda", dtype=torch.float32) - 0.5
+    lat = W.brick_wall_flake(11, 18)
+    nu, nd = W.neel_state(lat)
+    P = F.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=F.FTWA_FP32)
+    for _ in range(args.prof_repeat):
+        P.moments(X, gram_mode=F.FTWA_GRAM_BF16X3)
+    torch.cuda.synchronize()
+    st = P.status()
+    print(json.dumps({"profile_gram": True, "M": M, "K": K, "T": T, "status": st}))
+    if st != 0:
+        raise SystemExit(1)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -387,7 +564,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-gram", action="store_true")
+    ap.add_argument("--adjoint-samples", type=int, default=4096)
+    ap.add_argument("--batch-samples", type=int, default=4096)
+    ap.add_argument("--batch-steps", type=int, default=100)
+    ap.add_argument("--gram-samples", type=int, default=65536)
+    ap.add_argument("--gram-times", type=int, default=200)
     ap.add_argument("--profile", action="store_true", help="small case for ncu captures")
+    ap.add_argument("--profile-gram", action="store_true", help="small Gram case for ncu captures")
     ap.add_argument("--prof-steps", type=int, default=20)
     ap.add_argument("--prof-repeat", type=int, default=2)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
@@ -395,6 +581,9 @@ def main():
     args = ap.parse_args()
     if args.profile:
         run_profile_case(args)
+        return
+    if args.profile_gram:
+        run_profile_gram(args)
         return
     if args.warmup < 3 and args.impl == "native":
         print("note: fewer than 3 warm-up steps; the timing contract asks for >= 3", file=sys.stderr)

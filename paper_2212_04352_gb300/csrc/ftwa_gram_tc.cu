@@ -298,6 +298,20 @@ __global__ void gram_reduce_kernel(const float *partial, int splits, int T, int 
 
 }  // namespace gram
 
+// Sample splits: enough CTAs to fill the machine twice, and every split's
+// FP32 tensor-memory accumulation limited to kMaxChunksPerSplit chunks (1024
+// samples), so that the FP32 rounding of a long same-sign sum (the
+// variances) stays far below the sampling error; splits are summed in FP64.
+static void gram_splits(Plan *p, long long n_chunks, long long base_ctas, long long &splits, long long &cps)
+{
+    constexpr long long kMaxChunksPerSplit = 16;
+    splits = std::max<long long>(1, (2LL * std::max(1, p->sm_count) + base_ctas - 1) / base_ctas);
+    splits = std::min<long long>(splits, std::max<long long>(1, n_chunks / 4));
+    splits = std::max<long long>(splits, (n_chunks + kMaxChunksPerSplit - 1) / kMaxChunksPerSplit);
+    cps = (n_chunks + splits - 1) / splits;
+    splits = (n_chunks + cps - 1) / cps;
+}
+
 int launch_gram_bf16x3(Plan *p, const void *snap, int64_t M, int32_t T, const double *mu, double *conn, double *g2,
                        cudaStream_t s)
 {
@@ -307,12 +321,9 @@ int launch_gram_bf16x3(Plan *p, const void *snap, int64_t M, int32_t T, const do
     const int n_kt = (K + kTile - 1) / kTile;
     const int n_tiles = n_kt * (n_kt + 1) / 2;
     const long long n_chunks = (M + kChunk - 1) / kChunk;
-    // enough CTAs to fill the machine twice; each split covers >= 4 chunks
     const long long base_ctas = (long long)T * n_tiles;
-    long long splits = std::max<long long>(1, (2LL * std::max(1, p->sm_count) + base_ctas - 1) / base_ctas);
-    splits = std::min<long long>(splits, std::max<long long>(1, n_chunks / 4));
-    const long long cps = (n_chunks + splits - 1) / splits;
-    splits = (n_chunks + cps - 1) / cps;
+    long long splits, cps;
+    gram_splits(p, n_chunks, base_ctas, splits, cps);
     // workspace: mu already occupies the first T*K doubles
     const size_t mu_bytes = ((sizeof(double) * (size_t)T * K + 255) / 256) * 256;
     const size_t part_bytes = sizeof(float) * (size_t)splits * T * n_tiles * kTile * kTile;
@@ -351,10 +362,8 @@ size_t gram_bf16x3_workspace(Plan *p, int64_t M, int32_t T)
     const int n_tiles = n_kt * (n_kt + 1) / 2;
     const long long n_chunks = (M + kChunk - 1) / kChunk;
     const long long base_ctas = (long long)T * n_tiles;
-    long long splits = std::max<long long>(1, (2LL * std::max(1, p->sm_count) + base_ctas - 1) / base_ctas);
-    splits = std::min<long long>(splits, std::max<long long>(1, n_chunks / 4));
-    const long long cps = (n_chunks + splits - 1) / splits;
-    splits = (n_chunks + cps - 1) / cps;
+    long long splits, cps;
+    gram_splits(p, n_chunks, base_ctas, splits, cps);
     const size_t mu_bytes = ((sizeof(double) * (size_t)T * K + 255) / 256) * 256;
     return mu_bytes + sizeof(float) * (size_t)splits * T * n_tiles * kTile * kTile;
 }

@@ -274,3 +274,23 @@ def test_gram_bf16x3_matches_fp64(ftwa, lat_name, M, steps):
     bound = 3e-5 * d[:, :, None] * d[:, None, :] + 1e-7
     assert np.all(np.abs(c16 - c64) <= bound)
     assert np.array_equal(c16, np.transpose(c16, (0, 2, 1)))
+
+
+def test_gram_bf16x3_error_below_tenth_of_sampling_error(ftwa):
+    """At M = 65536 samples (the correlator workload's size) the BF16x3 Gram
+    differs from the FP64 Gram by less than 10% of the sampling error
+    sigma_k sigma_l / sqrt(M) of each entry."""
+    M, K, T = 65536, 396, 3
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    X = torch.rand((T, M, K), generator=g, device="cuda", dtype=torch.float32) - 0.5
+    X += 0.1 * torch.rand((1, 1, K), generator=g, device="cuda")
+    lat = W.brick_wall_flake()
+    nu, nd = W.neel_state(lat)
+    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=1) as P:
+        _, c64, _ = P.moments(X, gram_mode=ftwa.FTWA_GRAM_FP64, g2=False)
+        _, c16, _ = P.moments(X, gram_mode=ftwa.FTWA_GRAM_BF16X3, g2=False)
+        assert P.status() == 0
+    d = torch.sqrt(torch.diagonal(c64, dim1=1, dim2=2))
+    stat = d[:, :, None] * d[:, None, :] / M ** 0.5
+    assert ((c16 - c64).abs() / stat).max().item() < 0.1

@@ -122,13 +122,8 @@ def barrier(ws):
 
 
 def max_over_ranks(x, ws):
-    if ws == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2212_04352_gb300 import shard
+    return shard.max_over_ranks(x, ws)
 
 
 def traffic_record(kernel_src):
@@ -362,7 +357,8 @@ def run_gpu(args):
     wl = workload(M=args.samples)
     lat, M, steps, every = wl["lat"], wl["M"], wl["steps"], wl["every"]
     N = lat.n_sites
-    first = rank * M
+    from paper_2212_04352_gb300 import shard
+    first, _ = shard.sample_range(rank, ws, M)
     P = F.Plan(lat, wl["U"], n_up=wl["n_up"], n_dn=wl["n_dn"], precision=F.FTWA_FP32, out_every=every)
     stream = torch.cuda.current_stream()
     rho = P.new_state(M)

@@ -10,14 +10,14 @@
  * with nearest-neighbour hoppings j_ij = t_b on the bonds of a lattice of
  * degree <= 3 and on-site U.  A sample is one complex one-body matrix
  * rho_ij,s per spin s, drawn from the Gaussian Wigner distribution of a
- * diagonal initial state (Eq. 12) and advanced by the fTWA equation of
- * motion (Eq. 9)
+ * diagonal initial state (Eq. 7) and advanced by the fTWA equation of
+ * motion (Eq. 6)
  *
  *   d/dt rho_s = i (rho_s J - J rho_s) + i U (D_sbar rho_s - rho_s D_sbar),
  *   D_sbar = diag(Re rho_kk,sbar + 1/2),
  *
  * with classical RK4 (the paper names no integrator).  Occupations and
- * density-density correlators are sample means (Eqs. 5 and 11).
+ * density-density correlators are sample means (Eqs. 5 and 10).
  *
  * Conventions (all entry points):
  *  - Every call returns an int status: FTWA_OK (0) or a negative FTWA_ERR_*
@@ -80,7 +80,7 @@ typedef struct {
     const double *t_bond;    /* host, [n_bonds] or NULL */
 } ftwa_lattice;
 
-/* Diagonal initial state of Eq. 12: occupations n_i,s in [0, 1] (Fock
+/* Diagonal initial state of Eq. 7: occupations n_i,s in [0, 1] (Fock
  * states use 0/1; fractional values describe a thermal diagonal state). */
 typedef struct {
     const double *n_up;      /* host, [n_sites] */
@@ -136,7 +136,7 @@ void ftwa_destroy(ftwa_plan_t *plan);
 /* Report the plan's launch shape. */
 int ftwa_get_info(const ftwa_plan_t *plan, ftwa_plan_info *info);
 
-/* Eq. 12 (ic_fTWA): write M initial samples m = first_sample ..
+/* Eq. 7 (ic_fTWA): write M initial samples m = first_sample ..
  * first_sample + M - 1 into rho_dev ([M][2][N][N] complex, plan precision):
  * rho_ii,s = n_i,s - 1/2 and, for i < j, rho_ij,s = xi_ij,s sqrt((n_i,s +
  * n_j,s - 2 n_i,s n_j,s)/2), rho_ji,s = conj(rho_ij,s), xi standard complex
@@ -155,7 +155,7 @@ int ftwa_sample(ftwa_plan_t *plan, uint64_t seed, int64_t first_sample, int64_t 
 int ftwa_philox(uint64_t seed, int64_t m, int32_t spin, int64_t p0, int64_t count,
                 uint32_t *out_dev, void *stream);
 
-/* Eq. 9 (drho) with classical RK4: advance the M samples in rho_dev
+/* Eq. 6 (drho) with classical RK4: advance the M samples in rho_dev
  * (in place, [M][2][N][N] complex, plan precision) by n_steps steps of
  * size dt.  When snap_dev is not NULL, X[t][m][s*N+i] = Re rho_ii,s after
  * t*out_every steps is written for t = 0 .. n_steps/out_every ([n_out][M][2N],
@@ -168,13 +168,13 @@ int ftwa_philox(uint64_t seed, int64_t m, int32_t spin, int64_t p0, int64_t coun
 int ftwa_evolve(ftwa_plan_t *plan, void *rho_dev, int64_t M, int64_t n_steps,
                 void *snap_dev, void *stream);
 
-/* Eqs. 5 and 11 (fTWA_moments, g2_fTWA) from snapshots snap_dev
+/* Eqs. 5 and 10 (fTWA_moments, g2_fTWA) from snapshots snap_dev
  * ([n_times][M][2N], plan precision), accumulated in double:
  *   occ_dev[t][k]     = <n_k>(t) = mean_m X[t][m][k] + 1/2,   k = s*N + i
  *   conn_dev[t][k][l] = (1/M) sum_m (X_k - mu_k)(X_l - mu_l)  (connected
  *                       <n_k n_l> - <n_k><n_l> for k != l; the diagonal is
  *                       the sample variance of X_k)
- *   g2_dev[t][k][l]   = mean((X_k + 1/2)(X_l + 1/2)) / (<n_k><n_l>)  (Eq. 11;
+ *   g2_dev[t][k][l]   = mean((X_k + 1/2)(X_l + 1/2)) / (<n_k><n_l>)  (Eq. 10;
  *                       nullable; the k == l entries are not a g2)
  * gram_mode FTWA_GRAM_FP64 forms the Gram in double; FTWA_GRAM_BF16X3 forms
  * it on the tensor cores from centred data split as x = hi + lo (bf16) with
@@ -188,18 +188,18 @@ int ftwa_moments(ftwa_plan_t *plan, const void *snap_dev, int64_t M, int32_t n_t
                  double *occ_dev, double *conn_dev, double *g2_dev, int32_t gram_mode,
                  void *stream);
 
-/* Discrete adjoint of the RK4 integration of Eq. 9.  The loss is given
+/* Discrete adjoint of the RK4 integration of Eq. 6.  The loss is given
  * through its gradient with respect to the occupations: the caller supplies
  * dL_docc_dev[t][k] = dL/d<n_k>(t) for the output rows t = 0 .. T (T =
  * n_steps/out_every, [T+1][2N] device doubles, k = s*N + i); for a loss
  * L(<n>) this is exact at the point where it was evaluated.  Samples
  * m = 0 .. M-1 of `seed` are regenerated exactly as ftwa_sample draws them
- * (Eq. 12), integrated forward with a checkpoint every ckpt_every steps, and
+ * (Eq. 7), integrated forward with a checkpoint every ckpt_every steps, and
  * swept backward stage by stage (each segment replayed from its checkpoint).
  * Outputs (device doubles, overwritten; any may be NULL): grad_U_dev[1] =
  * dL/dU, grad_t_dev[n_bonds] = dL/dt_b in the lattice's bond order,
  * grad_n0_dev[2][N] = dL/dn_i,s through rho_ii(0) = n - 1/2 and through the
- * noise scale s_ij(n) of Eq. 12; pairs with s_ij = 0 (e.g. two filled or two
+ * noise scale s_ij(n) of Eq. 7; pairs with s_ij = 0 (e.g. two filled or two
  * empty sites of a Fock state) are skipped, since n -> s_ij is not
  * differentiable there.  ckpt_every must divide n_steps and be a multiple of
  * out_every.  The plan keeps a per-CTA workspace (checkpoints, one replayed

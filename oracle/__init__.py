@@ -100,7 +100,7 @@ def normals(N, seed, m):
 
 
 def sample(N, n_up, n_dn, seed, m):
-    """One initial sample rho(0) of Eq. 12, shape [2, N, N] complex."""
+    """One initial sample rho(0) of Eq. 7, shape [2, N, N] complex."""
     lib = _load()
     nu = np.ascontiguousarray(n_up, dtype=np.float64)
     nd = np.ascontiguousarray(n_dn, dtype=np.float64)
@@ -110,7 +110,7 @@ def sample(N, n_up, n_dn, seed, m):
 
 
 def rhs(lat, U, rho, t_bond=None):
-    """Right-hand side of Eq. 9 for a state [2, N, N]."""
+    """Right-hand side of Eq. 6 for a state [2, N, N]."""
     lib = _load()
     b, t = _lat_arrays(lat, t_bond)
     r = np.ascontiguousarray(rho, dtype=np.complex128)
@@ -150,7 +150,7 @@ def run(lat, U, n_up, n_dn, seed, m0, M, dt, n_steps, out_every, t_bond=None,
 
 
 def energy(lat, U, rho, t_bond=None):
-    """Classical energy H_W of Eq. A.8 (complex; the imaginary part is 0)."""
+    """Classical energy H_W of Eq. A10 (complex; the imaginary part is 0)."""
     lib = _load()
     b, t = _lat_arrays(lat, t_bond)
     r = np.ascontiguousarray(rho, dtype=np.complex128)

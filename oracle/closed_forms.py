@@ -56,7 +56,7 @@ def free_fermion_one_body(lat, n0, t):
 
 
 def wick_same_spin(nmat):
-    """Same-spin <n_i n_j> (i != j) of a Slater determinant, Eq. A.4 (wickthm):
+    """Same-spin <n_i n_j> (i != j) of a Slater determinant, Eq. A4 (wickthm):
     <c+_i c+_j c_j c_i> = n_ii n_jj - |n_ij|^2."""
     d = np.real(np.diag(nmat))
     out = d[:, None] * d[None, :] - np.abs(nmat) ** 2
@@ -71,18 +71,18 @@ def dimer_eigenvalues(U, t=1.0):
 
 
 def g2_long_time(n):
-    """Table 1 (Eq. C.15): g2(inf) = 2 C(n-2, n/2-2) / C(n-1, n/2-1), half filling."""
+    """Table 1 (Eq. C11): g2(inf) = 2 C(n-2, n/2-2) / C(n-1, n/2-1), half filling."""
     return 2 * math.comb(n - 2, n // 2 - 2) / math.comb(n - 1, n // 2 - 1)
 
 
 def g2_short_time(j12, j2):
-    """Eq. C.13 (form_g_st_2): g2_12(0+) = (sum_i j_2i^2 - j_12^2) / sum_i j_2i^2."""
+    """Eq. C8 (form_g_st_2): g2_12(0+) = (sum_i j_2i^2 - j_12^2) / sum_i j_2i^2."""
     s = float(np.sum(np.asarray(j2) ** 2))
     return (s - j12 ** 2) / s
 
 
 def rho11_taylor(eps, j1, xi1, U):
-    """Eq. C.7 (ro11u), filled site 1 whose neighbours are empty (Neel start):
+    """Eq. C3 (ro11u), filled site 1 whose neighbours are empty (Neel start):
     rho_11(eps) = 1/2 - sum_i j_1i eta2_1i eps - sum_i j_1i^2 eps^2
                   + U/2 sum_i j_1i eta1_1i eps^2 + O(eps^3),
     with eta1 = sqrt(2) Re xi and eta2 = sqrt(2) Im xi (App. C: xi/sqrt(2) =

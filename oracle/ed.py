@@ -2,7 +2,7 @@
 
 The comparison method of Sec. III.A / App. B: the many-body state is written
 in the basis of Slater determinants with fixed N_up, N_dn, and propagated
-exactly.  The paper's Eq. 13 (shro) prints the propagator as exp(+iHt); the
+exactly.  The paper's Eq. 8 (shro) prints the propagator as exp(+iHt); the
 Schroedinger form |Psi(t)> = exp(-iHt)|Psi_0> is used here (hbar = 1).  The
 paper propagates with Krylov subspaces (expokit); scipy's expm_multiply is
 used here, exact to its tolerance.

@@ -14,15 +14,15 @@
  * What is computed, in the paper's order:
  *   1. Hamiltonian of Eq. 1 (FHeq1) with j_ij = t_b on bond b (both orders)
  *      and u_ij = U delta_ij (Sec. II).
- *   2. Initial Gaussian Wigner sample of Eq. 12 (ic_fTWA): rho_ii = n_i - 1/2,
+ *   2. Initial Gaussian Wigner sample of Eq. 7 (ic_fTWA): rho_ii = n_i - 1/2,
  *      rho_ij = xi_ij sqrt((n_i + n_j - 2 n_i n_j)/2) for i < j, rho_ji =
  *      conj(rho_ij), with xi complex normal, E|xi|^2 = 1 (the covariance of
- *      App. A.3, Eq. after ftwa_h).
- *   3. Equation of motion Eq. 9 (drho), integrated with classical RK4 (the
+ *      App. A.3, Eqs. A11-A12).
+ *   3. Equation of motion Eq. 6 (drho), integrated with classical RK4 (the
  *      paper states no integrator; RK4 with dt = 0.01 is the reading used).
- *   4. Estimators of Eq. 5 (fTWA_moments) and Eq. 11 (g2_fTWA) as sample
+ *   4. Estimators of Eq. 5 (fTWA_moments) and Eq. 10 (g2_fTWA) as sample
  *      means, plus the connected correlator as a two-pass covariance.
- *   5. The classical energy H_W of Eq. A.8 (ftwa_h), conserved per trajectory.
+ *   5. The classical energy H_W of Eq. A10 (ftwa_h), conserved per trajectory.
  *
  * Random numbers (the paper names no generator): Philox4x32-10 from its
  * published definition (Salmon, Moraes, Dror, Shaw, SC'11), key = (seed_lo,
@@ -114,7 +114,7 @@ void orc_normals(int32_t N, uint64_t seed, int64_t m, double *xi /* [2][N][N] co
             }
 }
 
-/* Eq. 12: one Gaussian Wigner sample of the diagonal state n (per spin). */
+/* Eq. 7: one Gaussian Wigner sample of the diagonal state n (per spin). */
 void orc_sample(int32_t N, const double *n_up, const double *n_dn, uint64_t seed, int64_t m,
                 double *rho_out)
 {
@@ -175,7 +175,7 @@ static void free_adjacency(adjacency *a)
     free(a->start); free(a->nbr); free(a->hop);
 }
 
-/* Eq. 9 (drho), for both spins:
+/* Eq. 6 (drho), for both spins:
  *   d/dt rho_ij,s = i sum_k ( j_jk rho_ik,s - j_ki rho_kj,s
  *                            + (u_ki - u_kj)(rho_kk,sbar + 1/2) rho_ij,s )
  * With u_ij = U delta_ij the k-sum of the interaction term reduces to
@@ -210,7 +210,7 @@ void orc_rhs(int32_t N, int32_t B, const int32_t *bonds, const double *t_bond, d
     free_adjacency(&a);
 }
 
-/* Classical fourth-order Runge-Kutta step of Eq. 9, both spins together. */
+/* Classical fourth-order Runge-Kutta step of Eq. 6, both spins together. */
 static void rk4_step(const adjacency *a, double U, double dt, cplx *y, cplx *k, cplx *ys, cplx *acc)
 {
     const size_t n = 2 * (size_t)a->N * a->N;
@@ -297,7 +297,7 @@ int orc_max_threads(void)
 #endif
 }
 
-/* Eq. A.8 (ftwa_h): H_W = - sum_{ij s} j_ij rho_ij,s
+/* Eq. A10 (ftwa_h): H_W = - sum_{ij s} j_ij rho_ij,s
  *                        + sum_{i>=j} u_ij (rho_ii,up + 1/2)(rho_jj,dn + 1/2),
  * with u_ij = U delta_ij.  Returned as a complex pair (re, im). */
 void orc_energy(int32_t N, int32_t B, const int32_t *bonds, const double *t_bond, double U,
@@ -319,7 +319,7 @@ void orc_energy(int32_t N, int32_t B, const int32_t *bonds, const double *t_bond
 /* Estimators, two passes in FP64 over X[t][m][k] = Re rho_kk (k = s*N + i):
  *   occ[t][k]      = mean_m X + 1/2                         (Eq. 5, first line)
  *   conn[t][k][l]  = (1/M) sum_m (X_k - mu_k)(X_l - mu_l)     (connected <n n>)
- *   g2[t][k][l]    = mean((X_k + 1/2)(X_l + 1/2)) / (occ_k occ_l)   (Eq. 11)
+ *   g2[t][k][l]    = mean((X_k + 1/2)(X_l + 1/2)) / (occ_k occ_l)   (Eq. 10)
  * g2 may be NULL. */
 void orc_moments(int64_t T, int64_t M, int64_t K, const double *X, double *occ, double *conn, double *g2)
 {

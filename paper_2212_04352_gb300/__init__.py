@@ -1,9 +1,9 @@
 """GB300 (sm_103a) fTWA hot path: Python binding of the libftwa C ABI.
 
 fermionic truncated Wigner approximation for the Fermi-Hubbard model of
-arXiv:2212.04352: Gaussian Wigner samples of a diagonal state (Eq. 12),
-RK4 integration of the fTWA equation of motion (Eq. 9) and sample-mean
-estimators (Eqs. 5 and 11), each a hand-written CUDA kernel behind
+arXiv:2212.04352: Gaussian Wigner samples of a diagonal state (Eq. 7),
+RK4 integration of the fTWA equation of motion (Eq. 6) and sample-mean
+estimators (Eqs. 5 and 10), each a hand-written CUDA kernel behind
 include/ftwa.h.  This module only marshals arguments: device buffers are
 torch CUDA tensors, passed to the library as raw pointers on torch's current
 stream.  There is no CPU fallback; a missing libftwa.so raises.

@@ -1,4 +1,4 @@
-// Discrete adjoint of the RK4 integration of Eq. 9.
+// Discrete adjoint of the RK4 integration of Eq. 6.
 //
 // Loss (linearised by the caller): L = sum_t sum_k g_t,k <n_k>(t), with
 // <n_k>(t) = (1/M) sum_m Re rho^m_kk(t) + 1/2 (Eq. 5), so each sample's
@@ -25,7 +25,7 @@
 //               (bond (i, k)).
 // Sums over all ordered (i, j) are taken over the stored upper triangle with
 // weight 2 off the diagonal and 1 on it (v and Y are Hermitian).  Finally
-// rho_ii(0) = n_i - 1/2 and rho_ij(0) = xi_ij s_ij(n) (Eq. 12) give
+// rho_ii(0) = n_i - 1/2 and rho_ij(0) = xi_ij s_ij(n) (Eq. 7) give
 //   dL/dn_i += Re lam_ii(0) + sum_{j != i} Re(conj(lam_ij) xi_ij) (1 - 2 n_j)/(2 s_ij)
 // (pairs with s_ij = 0 are skipped: the map n -> s is not differentiable there).
 #include <cuda_runtime.h>
@@ -77,7 +77,7 @@ __device__ __forceinline__ V getc(const V *buf, int N, int s, int a, int b)
     return v;
 }
 
-// Philox4x32-10 and the Box-Muller normal of Eq. 12 (same counter layout as
+// Philox4x32-10 and the Box-Muller normal of Eq. 7 (same counter layout as
 // the sampler: key (seed_lo, seed_hi), counter (m_lo, m_hi, s, p))
 __device__ __forceinline__ double2 xi_of(unsigned long long seed, long long m, int s, uint32_t p)
 {
@@ -114,7 +114,7 @@ struct Smem {
     double *gn;         // [2][N]
 };
 
-// out = f(y) (Eq. 9) on the packed upper triangle
+// out = f(y) (Eq. 6) on the packed upper triangle
 template <typename T>
 __device__ void f_eval(const AdjArgs<T> &a, const Smem &sm, const typename C2T<T>::type *y,
                        typename C2T<T>::type *out)
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(kThreadsA, 1) adjoint_kernel(const AdjArgs<T> 
     double gU = 0.0;
 
     for (long long m = blockIdx.x; m < a.M; m += gridDim.x) {
-        // ---- rho(0) of sample m (Eq. 12) --------------------------------------
+        // ---- rho(0) of sample m (Eq. 7) --------------------------------------
         for (int e = threadIdx.x; e < NE; e += blockDim.x) {
             const uint32_t d = sm.elem[e];
             const int i = d & 0xFF, j = (d >> 8) & 0xFF, s = d >> 16;

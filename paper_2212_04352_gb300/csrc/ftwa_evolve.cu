@@ -1,4 +1,4 @@
-// Persistent RK4 stepper for the fTWA equation of motion (Eq. 9).
+// Persistent RK4 stepper for the fTWA equation of motion (Eq. 6).
 //
 // One sample's state (both spins, Hermitian, packed upper triangle) stays
 // on chip for the whole integration:
@@ -9,12 +9,12 @@
 //  - the private RK4 registers of every element (y0 and the stage
 //    accumulator) and its index metadata live in tensor memory, which the
 //    stepper uses as a 256 KB per-SM extension of the register file;
-//  - the diagonal Re rho_kk of both spins (the U coupling of Eq. 9) is
+//  - the diagonal Re rho_kk of both spins (the U coupling of Eq. 6) is
 //    replicated into every CTA of the cluster at each stage.
 // Work unit: 32 consecutive packed elements, one per lane.  A CTA owns a set
 // of spin-rows (and, for small lattices, several samples, "slots").
 //
-// Per element (p, q), p <= q, spin s, the right-hand side of Eq. 9 is
+// Per element (p, q), p <= q, spin s, the right-hand side of Eq. 6 is
 //   k_pq = i [ sum_{k in nb(q)} t_qk rho_pk - sum_{k in nb(p)} t_pk rho_kq
 //              + U (Re rho_pp,sbar - Re rho_qq,sbar) rho_pq ]
 // with rho_ab = conj(rho_ba) for a > b read from the stored triangle.
@@ -260,7 +260,7 @@ __device__ __forceinline__ void rk4_stage(const StepArgs<T> &a, const RowDesc *s
                 const T g = a.U * (db[p] - db[q]);
                 hr = fma(g, own.x, hr);
                 hi = fma(g, own.y, hi);
-                // k = i (hr + i hi); on the diagonal Eq. 9 is real, so its imaginary
+                // k = i (hr + i hi); on the diagonal Eq. 6 is real, so its imaginary
                 // part (pure rounding residue) is dropped
                 const T kx = -hi, ky = (q == p) ? T(0) : hr;
                 V nxt;
@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(kThreads, 1) rk4_stepper(const StepArgs<T> a)
 // |i - j| over bonds), as for honeycomb flakes numbered row by row.
 //  - Every spin-row p stores columns [max(0, p - bw), N): the upper triangle
 //    plus a mirror band of bw entries below the diagonal, kept equal to
-//    conj of the transposed entries.  Every read of Eq. 9 is then a direct
+//    conj of the transposed entries.  Every read of Eq. 6 is then a direct
 //    load; no conjugated reads near the diagonal.
 //  - A lane owns one column q = 32 b + lane of a column block b and walks the
 //    rows of its work items, so the column's neighbour offsets, hoppings,
@@ -648,7 +648,7 @@ __device__ __forceinline__ void band_stage(unsigned char *smem, const BandArgs<T
                 }
                 // + U (Re rho_pp,sbar - Re rho_qq,sbar) rho_pq
                 cfma(a.U * (dgo[p] - dq), own, h);
-                // k = i h; the diagonal of Eq. 9 is real (its imaginary part is
+                // k = i h; the diagonal of Eq. 6 is real (its imaginary part is
                 // rounding residue and is dropped)
                 V kk;
                 kk.x = -h.y;

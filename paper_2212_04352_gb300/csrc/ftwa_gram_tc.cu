@@ -1,4 +1,4 @@
-// Connected density correlator of Eqs. 5 and 11 as a Gram contraction on
+// Connected density correlator of Eqs. 5 and 10 as a Gram contraction on
 // the tcgen05 tensor cores, in BF16x3 split precision.
 //
 //   C_t = (1/M) (X_t - mu_t)^T (X_t - mu_t),   X_t: M samples x K = 2N sites

@@ -1,9 +1,9 @@
-// Sample-mean estimators of Eqs. 5 and 11 from diagonal snapshots.
+// Sample-mean estimators of Eqs. 5 and 10 from diagonal snapshots.
 //
 //   mu[t][k]   = (1/M) sum_m X[t][m][k]                 (double, fixed order)
 //   occ[t][k]  = mu + 1/2                               (Eq. 5, first line)
 //   conn[t]    = (1/M) (X - mu)^T (X - mu)              (connected Gram)
-//   g2[t][k][l] = (conn_kl + occ_k occ_l) / (occ_k occ_l)   (Eq. 11: the sample
+//   g2[t][k][l] = (conn_kl + occ_k occ_l) / (occ_k occ_l)   (Eq. 10: the sample
 //                mean of (X_k + 1/2)(X_l + 1/2) equals conn_kl + occ_k occ_l)
 //
 // Two Gram paths: FP64 on the CUDA cores (reference), and BF16x3 split

@@ -1,4 +1,4 @@
-// Gaussian Wigner samples of a diagonal state (Eq. 12) from a counter-based
+// Gaussian Wigner samples of a diagonal state (Eq. 7) from a counter-based
 // generator.  Philox4x32-10 follows its published definition (Salmon,
 // Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64 multiplies with
 // the multipliers 0xD2511F53 / 0xCD9E8D57, the key bumped by the Weyl

@@ -5,7 +5,7 @@ its gradient with respect to U, every bond hopping t_b and every initial
 occupation n_i,s is computed by the adjoint from dL/d<n> = 2(<n> - target)
 and compared with central differences (h = 1e-5, common random numbers:
 same seed) of the oracle.  Occupations are softened (0.05 / 0.95) so that
-every noise scale s_ij of Eq. 12 is positive.  Gate (FP64): relative error
+every noise scale s_ij of Eq. 7 is positive.  Gate (FP64): relative error
 <= 1e-6.
 """
 

@@ -67,6 +67,18 @@ def test_sample_parity(ftwa, precision):
         assert np.max(np.abs(rho - ref)) <= 2e-6
 
 
+def test_sample_independent_of_split(ftwa):
+    """Sample m depends only on (seed, m): drawing [0, 10) at once or as
+    [0, 4) + [4, 10) gives the same states (what lets ranks shard samples)."""
+    lat = W.hexagonal_flake(2)
+    nu, nd = W.neel_state(lat)
+    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=0) as P:
+        full = P.sample(5, 10)
+        a = P.sample(5, 4, first_sample=0)
+        b = P.sample(5, 6, first_sample=4)
+    assert torch.equal(full, torch.cat([a, b]))
+
+
 # ------------------------------------------------------------------ stepper
 CASES = [
     ("periodic8", lambda: W.periodic_honeycomb(), 1.6, "neel", 7),

@@ -56,7 +56,7 @@ def test_complex_normal_moments():
 
 
 def test_sample_structure_eq12():
-    """Eq. 12: rho_ii = n_i - 1/2; rho Hermitian; rho_ij = xi_ij s_ij with
+    """Eq. 7: rho_ii = n_i - 1/2; rho Hermitian; rho_ij = xi_ij s_ij with
     s_ij = sqrt((n_i + n_j - 2 n_i n_j)/2)."""
     lat = W.hexagon_chain(2)
     rng = np.random.default_rng(0)
@@ -128,7 +128,7 @@ def test_initial_derivative_paper_value():
 
 
 def test_short_time_taylor_paper():
-    """Eq. C.7 (ro11u): rho_11(eps) to second order; the residual is O(eps^3)."""
+    """Eq. C3 (ro11u): rho_11(eps) to second order; the residual is O(eps^3)."""
     lat = W.brick_wall_flake(4, 6)
     nu, nd = W.neel_state(lat)
     U = 1.6
@@ -148,7 +148,7 @@ def test_short_time_taylor_paper():
 
 
 def test_hartree_fock_identity():
-    """Sec. III.A: with zero noise the fTWA flow is Hartree-Fock.  Eq. A.6
+    """Sec. III.A: with zero noise the fTWA flow is Hartree-Fock.  Eq. A6
     (Heis_HF2) is integrated here independently on n = rho + 1/2 and compared."""
     lat = W.hexagon_chain(2)
     nu, nd = W.neel_state(lat)
@@ -178,7 +178,7 @@ def test_hartree_fock_identity():
 
 def test_invariants_per_trajectory():
     """Per trajectory: trace per spin is conserved, rho stays Hermitian, and the
-    classical energy H_W (Eq. A.8) and the spectrum of each rho_s drift only by
+    classical energy H_W (Eq. A10) and the spectrum of each rho_s drift only by
     the RK4 error (halving dt cuts the drift by ~16)."""
     lat = W.hexagonal_flake(2)
     nu, nd = W.neel_state(lat)
@@ -191,7 +191,7 @@ def test_invariants_per_trajectory():
         rho, _ = oracle.evolve(lat, U, rho0, dt, steps)
         for s, n in enumerate([nu, nd]):
             assert abs(np.trace(rho[s]) - (n.sum() - lat.n_sites / 2)) < 1e-11
-            # the two neighbour sums of Eq. 9 associate differently for
+            # the two neighbour sums of Eq. 6 associate differently for
             # (i, j) and (j, i), so Hermiticity holds to rounding
             assert np.max(np.abs(rho[s] - rho[s].conj().T)) < 1e-13
         e = oracle.energy(lat, U, rho)
@@ -212,7 +212,7 @@ def test_ed_dimer_closed_form():
 
 
 def test_ed_free_fermions():
-    """ED at U = 0 against the one-body propagator and Wick's theorem (Eq. A.4)."""
+    """ED at U = 0 against the one-body propagator and Wick's theorem (Eq. A4)."""
     lat = W.periodic_honeycomb()
     nu, nd = W.neel_state(lat)
     ed = HubbardED(lat, 0.0, 4, 4)

@@ -1,6 +1,6 @@
 """Diagonal initial occupations n_{i sigma} (input data only).
 
-The fTWA initial distribution of Eq. 12 is built from a diagonal state with
+The fTWA initial distribution of Eq. 7 is built from a diagonal state with
 site occupations n_{ii sigma}; these helpers only choose those occupations.
 """
 

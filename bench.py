@@ -513,7 +513,8 @@ def run_profile_case(args):
     import paper_2212_04352_gb300 as F
     wl = workload(M=args.samples, steps=args.prof_steps)
     prec = F.FTWA_FP64 if args.precision == "fp64" else F.FTWA_FP32
-    P = F.Plan(wl["lat"], wl["U"], n_up=wl["n_up"], n_dn=wl["n_dn"], precision=prec, out_every=wl["every"])
+    P = F.Plan(wl["lat"], wl["U"], n_up=wl["n_up"], n_dn=wl["n_dn"], precision=prec, out_every=wl["every"],
+               variant=args.variant)
     for _ in range(args.prof_repeat):
         rho = P.sample(7, wl["M"])
         X = P.evolve(rho, wl["steps"])
@@ -574,6 +575,7 @@ def main():
     ap.add_argument("--prof-repeat", type=int, default=2)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--gram", type=int, default=0)
+    ap.add_argument("--variant", type=int, default=0, help="stepper variant of the profile case (0 automatic)")
     args = ap.parse_args()
     if args.profile:
         run_profile_case(args)

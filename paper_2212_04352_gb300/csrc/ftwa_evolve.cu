@@ -536,12 +536,17 @@ __global__ void __launch_bounds__(kThreads, 1) rk4_stepper(const StepArgs<T> a)
 //  - Work items (runs of rows of one spin, one column block) are assigned to
 //    warps on the host (longest-processing-time first).
 // ---------------------------------------------------------------------------
+// Stored columns of row p in the banded layout: the upper triangle plus a
+// mirror band of bw entries below the diagonal, columns band_lo(p) .. N - 1.
+__host__ __device__ __forceinline__ int band_lo(int p, int bw) { return p > bw ? p - bw : 0; }
+
 template <typename T>
 struct BandArgs {
     const int32_t *nbr;
     const T *tnb;
     T U, dt, t_uniform;
     int N, bw, C, S, E, k_items, buf_bytes;
+    int qoff;                   // first column of block 0 (<= 0): blocks end at the last column
     int row_begin[kMaxCluster + 1];
     const uint32_t *items;      // [C][kWarps][k_items]: count | b << 6 | sr << 9 | slot << 18
     long long M, n_steps;
@@ -593,9 +598,9 @@ __device__ __forceinline__ void band_stage(unsigned char *smem, const BandArgs<T
         if (item == 0xFFFFFFFFu) break;
         const int count = item & 63, blk = (item >> 6) & 7, sr0 = (item >> 9) & 511, slot = item >> 18;
         const int s = sr0 >= N ? 1 : 0;
-        const int q = 32 * blk + lane;
+        const int q = a.qoff + 32 * blk + lane;
         const bool qa = q < N;
-        const int qc = qa ? q : N - 1;
+        const int qc = q < 0 ? 0 : (qa ? q : N - 1);
         // per-column registers for the whole item
         const int nq = s_nbr[qc];
         uint32_t koff[3];
@@ -738,10 +743,7 @@ __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
 
     const int rb0 = a.row_begin[rank], rb1 = a.row_begin[rank + 1];
     int eps = 0;                       // stored elements per slot of this rank
-    for (int sr = rb0; sr < rb1; ++sr) {
-        const int p = sr % N;
-        eps += N - (p > bw ? p - bw : 0);
-    }
+    for (int sr = rb0; sr < rb1; ++sr) eps += N - band_lo(sr % N, bw);
     const int eps_bytes = eps * SZ;
 
     if (threadIdx.x == 0) {
@@ -759,11 +761,8 @@ __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
         int owner = 0;
         while (owner + 1 < C && sr >= a.row_begin[owner + 1]) ++owner;
         int off = 0;
-        for (int x = a.row_begin[owner]; x < sr; ++x) {
-            const int px = x % N;
-            off += N - (px > bw ? px - bw : 0);
-        }
-        const int p = sr % N, lo = p > bw ? p - bw : 0;
+        for (int x = a.row_begin[owner]; x < sr; ++x) off += N - band_lo(x % N, bw);
+        const int p = sr % N, lo = band_lo(p, bw);
         const uint32_t start = bufA_s + (uint32_t)(off * SZ);   // element (p, lo)
         s_rowbase[sr] = (CLUSTER ? map_rank(start, owner) : start) - (uint32_t)(lo * SZ);
     }
@@ -776,11 +775,8 @@ __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
         d.deg = (nbp >> 24) & 0xFF;
         for (int n = 0; n < 3; ++n) d.base_k[n] = s_rowbase[s * N + ((nbp >> (8 * n)) & 0xFF)];
         int off = 0;
-        for (int x = rb0; x < sr && x < rb1; ++x) {
-            const int px = x % N;
-            off += N - (px > bw ? px - bw : 0);
-        }
-        const int lo = p > bw ? p - bw : 0;
+        for (int x = rb0; x < sr && x < rb1; ++x) off += N - band_lo(x % N, bw);
+        const int lo = band_lo(p, bw);
         d.base_local = bufA_s + (uint32_t)(off * SZ) - (uint32_t)(lo * SZ);
         d.pad0 = 0;
         d.pad1 = 0;
@@ -814,7 +810,7 @@ __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
         for (int slot = 0; slot < S; ++slot) {
             const long long m = b * S + slot;
             for (int sr = rb0 + warp; sr < rb1; sr += kWarps) {
-                const int s = sr / N, p = sr % N, lo = p > bw ? p - bw : 0;
+                const int s = sr / N, p = sr % N, lo = band_lo(p, bw);
                 const uint32_t base = s_row[sr].base_local + (uint32_t)(slot * eps_bytes);
                 for (int k = lo + lane; k < N; k += 32) {
                     V v;
@@ -850,7 +846,8 @@ __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
                 const uint32_t item = my_items[it];
                 if (item == 0xFFFFFFFFu) break;
                 const int count = item & 63, blk = (item >> 6) & 7, sr0 = (item >> 9) & 511, slot = item >> 18;
-                const int s = sr0 >= N ? 1 : 0, q = 32 * blk + lane;
+                const int s = sr0 >= N ? 1 : 0;
+                const int q = a.qoff + 32 * blk + lane;
                 const long long m = b * S + slot;
                 for (int r = 0; r < count; ++r, ++e) {
                     const int p = (sr0 + r) % N;
@@ -898,7 +895,8 @@ __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
                 const uint32_t item = my_items[it];
                 if (item == 0xFFFFFFFFu) break;
                 const int count = item & 63, blk = (item >> 6) & 7, sr0 = (item >> 9) & 511, slot = item >> 18;
-                const int s = sr0 >= N ? 1 : 0, q = 32 * blk + lane;
+                const int s = sr0 >= N ? 1 : 0;
+                const int q = a.qoff + 32 * blk + lane;
                 const long long m = b * S + slot;
                 for (int r = 0; r < count; ++r, ++e) {
                     const int p = (sr0 + r) % N;
@@ -909,10 +907,10 @@ __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
                         if (!(isfinite(y0.x) && isfinite(y0.y))) record_status(a.status, FTWA_ERR_NONFINITE);
                         a.rho[((m * 2 + s) * N + p) * (long long)N + q] = y0;
                         if (p != q) {
-                            V c;
-                            c.x = y0.x;
-                            c.y = -y0.y;
-                            a.rho[((m * 2 + s) * N + q) * (long long)N + p] = c;
+                            V cj;
+                            cj.x = y0.x;
+                            cj.y = -y0.y;
+                            a.rho[((m * 2 + s) * N + q) * (long long)N + p] = cj;
                         }
                     }
                 }
@@ -1109,30 +1107,36 @@ static int dispatch_t(Plan *p, StepperShape &sh, void *rho, int64_t M, int64_t n
 }
 
 // ---- banded stepper: shape and work items ------------------------------------
+// Stored elements of spin-row sr: columns band_lo(p) .. N - 1.
 static int band_row_len(int N, int bw, int sr)
 {
-    const int p = sr % N;
-    return N - (p > bw ? p - bw : 0);
+    return N - band_lo(sr % N, bw);
 }
+
+// Column blocks of 32 columns end at the last column, so that only the first
+// block is ragged and only the first rows reach it (blocks aligned at column 0
+// would leave the last block ragged for every row).
+static int band_nblk(int N) { return (N + 31) / 32; }
+static int band_qoff(int N) { return N - 32 * band_nblk(N); }
+// first column block holding an element q >= p of row p
+static int band_first_blk(int p, int qoff) { return (p - qoff) / 32; }
 
 // Work items of one rank: runs of <= R consecutive spin-rows of one spin with
 // at least one element in column block b, for every block and slot; assigned
 // to warps longest-first under the tensor-memory cap.
 static bool band_items(int N, int S, int rb0, int rb1, int e_cap, int R, std::vector<uint32_t> &out, int &E, int &K)
 {
-    const int nblk = (N + 31) / 32;
+    const int nblk = band_nblk(N), qoff = band_qoff(N);
     std::vector<std::pair<int, uint32_t>> items;   // (rows, packed)
-    long long total = 0;
     for (int slot = 0; slot < S; ++slot)
         for (int b = 0; b < nblk; ++b)
             for (int s = 0; s < 2; ++s) {
                 const int lo = std::max(rb0, s * N), hi = std::min(rb1, s * N + N);
-                // rows with p <= 32 b + 31
-                const int last = std::min(hi, s * N + std::min(N, 32 * b + 32));
+                // rows with p <= qoff + 32 (b + 1) - 1
+                const int last = std::min(hi, s * N + std::min(N, qoff + 32 * (b + 1)));
                 for (int sr = lo; sr < last;) {
                     const int cnt = std::min(R, last - sr);
                     items.push_back({cnt, (uint32_t)cnt | ((uint32_t)b << 6) | ((uint32_t)sr << 9) | ((uint32_t)slot << 18)});
-                    total += cnt;
                     sr += cnt;
                 }
             }
@@ -1151,7 +1155,6 @@ static bool band_items(int N, int S, int rb0, int rb1, int e_cap, int R, std::ve
     out.assign((size_t)kWarps * K, 0xFFFFFFFFu);
     for (int w = 0; w < kWarps; ++w)
         for (size_t i = 0; i < per[w].size(); ++i) out[(size_t)w * K + i] = per[w][i];
-    (void)total;
     return true;
 }
 
@@ -1172,21 +1175,23 @@ int choose_band_shape(Plan *p, int64_t M, BandShape *out)
     const int e_cap = kTmemColsPerWarp / (2 * WC);
     const int max_smem = 227 * 1024;
     const int sm = p->sm_count > 0 ? p->sm_count : 1;
-    const int nblk = (N + 31) / 32;
+    const int nblk = band_nblk(N), qoff = band_qoff(N);
+    auto slices = [&](int sr) { return nblk - band_first_blk(sr % N, qoff); };
     for (int C = 1; C <= kMaxCluster; C *= 2) {
         if (p->cluster_override && C != p->cluster_override) continue;
         BandShape sh;
         sh.cluster = C;
+        sh.qoff = qoff;
         // split spin-rows by their number of column-block slices
         double tot = 0;
-        for (int sr = 0; sr < 2 * N; ++sr) tot += nblk - (sr % N) / 32;
+        for (int sr = 0; sr < 2 * N; ++sr) tot += slices(sr);
         sh.row_begin[0] = 0;
         int sr = 0;
         double acc = 0;
         for (int r = 1; r < C; ++r) {
             const double target = tot * r / C;
-            while (sr < 2 * N && acc + 0.5 * (nblk - (sr % N) / 32) < target) {
-                acc += nblk - (sr % N) / 32;
+            while (sr < 2 * N && acc + 0.5 * slices(sr) < target) {
+                acc += slices(sr);
                 ++sr;
             }
             sh.row_begin[r] = sr;
@@ -1314,6 +1319,7 @@ static int band_launch(Plan *p, BandShape &sh, void *rho, int64_t M, int64_t n_s
     a.E = sh.E;
     a.k_items = sh.k_items;
     a.buf_bytes = sh.buf_bytes;
+    a.qoff = sh.qoff;
     for (int i = 0; i <= kMaxCluster; ++i) a.row_begin[i] = sh.row_begin[i];
     a.items = p->d_items;
     a.M = M;

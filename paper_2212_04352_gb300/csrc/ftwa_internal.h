@@ -34,6 +34,7 @@ struct StepperShape {
 // Launch shape of the banded stepper.
 struct BandShape {
     int cluster = 1, slots = 1, E = 0, k_items = 0, buf_bytes = 0, smem_bytes = 0, grid = 0;
+    int qoff = 0;    // first column of column block 0 (<= 0)
     int row_begin[kMaxCluster + 1] = {0};
     std::vector<uint32_t> items;   // [cluster][kWarps][k_items]
 };

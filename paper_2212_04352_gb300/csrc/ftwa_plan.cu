@@ -204,7 +204,7 @@ int ftwa_plan(const ftwa_lattice *lat, double U, double t, double filling, const
         }
     }
 
-    // neighbour tables: slots in bond order; empty slots point at the site
+    // neighbour tables: filled slots first; empty slots point at the site
     // itself with zero hopping
     p->nbr_host.assign(N, 0);
     p->nbr_bond.assign(3 * (size_t)N, -1);
@@ -223,6 +223,31 @@ int ftwa_plan(const ftwa_lattice *lat, double U, double t, double filling, const
         t64[4 * j + fill[j]] = p->t_bond[b];
         p->nbr_bond[3 * j + fill[j]] = b;
         fill[j]++;
+    }
+    // order each site's slots by distance |k - i| (then k): on lattices
+    // numbered along rows, slot 0 and 1 are then the in-row neighbours i -+ 1
+    // for most sites, so that a warp's gathers of one slot over consecutive
+    // columns touch consecutive addresses (fewer shared-memory bank conflicts)
+    for (int i = 0; i < N; ++i) {
+        int idx[3] = {0, 1, 2};
+        std::sort(idx, idx + fill[i], [&](int x, int y) {
+            const int kx = slot_k[3 * i + x], ky = slot_k[3 * i + y];
+            const int dx = std::abs(kx - i), dy = std::abs(ky - i);
+            return dx != dy ? dx < dy : kx < ky;
+        });
+        int k2[3], b2[3];
+        double t2[3];
+        for (int n = 0; n < 3; ++n) {
+            const int src = n < fill[i] ? idx[n] : n;
+            k2[n] = slot_k[3 * i + src];
+            b2[n] = p->nbr_bond[3 * i + src];
+            t2[n] = t64[4 * i + src];
+        }
+        for (int n = 0; n < 3; ++n) {
+            slot_k[3 * i + n] = k2[n];
+            p->nbr_bond[3 * i + n] = b2[n];
+            t64[4 * i + n] = t2[n];
+        }
     }
     for (int i = 0; i < N; ++i)
         p->nbr_host[i] = slot_k[3 * i] | (slot_k[3 * i + 1] << 8) | (slot_k[3 * i + 2] << 16) | (fill[i] << 24);

@@ -169,6 +169,30 @@ def test_evolve_fp32_short(ftwa, lat_name, variant):
         assert _rel(fin[m], fin_o[m]) <= 1e-4
 
 
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8])
+@pytest.mark.parametrize("lat_name", ["chain7", "brick35", "flake54"])
+def test_evolve_fp32_shapes(ftwa, lat_name, cluster, variant):
+    """FP32 steppers (1: banded, 2: packed triangle) on odd and even lattice
+    sizes (ragged first column block of the banded layout) and every cluster
+    split; ragged M."""
+    lat = {"chain7": W.chain(7), "brick35": W.brick_wall_flake(5, 7), "flake54": W.hexagonal_flake(3)}[lat_name]
+    nu, nd = W.neel_state(lat)
+    M, steps = 5, 100
+    rho0 = _oracle_states(lat, nu, nd, 21, M)
+    fin_o = np.stack([oracle.evolve(lat, 1.6, rho0[m], 0.01, steps)[0] for m in range(M)])
+    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=1, cluster=cluster, variant=variant) as P:
+        assert P.info()["cluster"] == cluster and P.info()["variant"] == variant
+        rho = torch.from_numpy(rho0.astype(np.complex64)).cuda()
+        P.evolve(rho, steps, snap=None)
+        assert P.status() == 0
+        fin = rho.cpu().numpy().astype(np.complex128)
+    for m in range(M):
+        assert _rel(fin[m], fin_o[m]) <= 1e-4, (m, _rel(fin[m], fin_o[m]))
+        for sp in range(2):
+            assert np.array_equal(fin[m, sp], fin[m, sp].conj().T)
+
+
 def test_hermitian_output_and_trace(ftwa):
     lat = W.hexagonal_flake(2)
     nu, nd = W.neel_state(lat)

@@ -20,6 +20,7 @@ from .lattices import (  # noqa: F401
     hexagon_chain,
     ring,
     dimer,
+    chain,
 )
 from .states import (  # noqa: F401
     neel_state,

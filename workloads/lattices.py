@@ -169,3 +169,8 @@ def ring(n: int, t: float = 1.0) -> Lattice:
 def dimer(t: float = 1.0) -> Lattice:
     """Two sites, one bond (the Hubbard dimer)."""
     return _finish("dimer", 2, [(0, 1)], [(0.0, 0.0), (1.0, 0.0)], sub=[0, 1], t=t)
+
+
+def chain(n: int, t: float = 1.0) -> Lattice:
+    """Open chain of n sites (bipartite for every n, so odd sizes are possible)."""
+    return _finish(f"chain_{n}", n, [(i, i + 1) for i in range(n - 1)], [(float(i), 0.0) for i in range(n)], t=t)

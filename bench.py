@@ -528,12 +528,13 @@ def run_profile_case(args):
 
 
 def run_profile_gram(args):
-    """A small Gram case for ncu: T = 4 times of M = 65536 synthetic FP32
-    snapshots of the 198-site workload's 396 site-spin occupations."""
+    """A small Gram case for ncu: T times (default 15, one batch of the
+    tensor-core Gram) of M = 65536 synthetic FP32 snapshots of the 198-site
+    workload's 396 site-spin occupations."""
     import torch
     import paper_2212_04352_gb300 as F
     import workloads as W
-    M, K, T = 65536, 396, 4
+    M, K, T = 65536, 396, args.gram_prof_times
     g = torch.Generator(device="cuda")
     g.manual_seed(5)
     X = torch.rand((T, M, K), generator=g, device="cuda", dtype=torch.float32) - 0.5
@@ -575,6 +576,7 @@ def main():
     ap.add_argument("--prof-repeat", type=int, default=2)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--gram", type=int, default=0)
+    ap.add_argument("--gram-prof-times", type=int, default=15)
     ap.add_argument("--variant", type=int, default=0, help="stepper variant of the profile case (0 automatic)")
     args = ap.parse_args()
     if args.profile:

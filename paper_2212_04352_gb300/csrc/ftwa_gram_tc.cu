@@ -8,17 +8,27 @@
 // hi_k hi_l + hi_k lo_l + lo_k hi_l (the lo*lo term, ~2^-16 relative, is
 // dropped), each a bf16 MMA with FP32 accumulation in tensor memory.
 //
-// One CTA per (time, 128x128 output tile of the upper triangle, sample
-// split).  The CTA streams 64-sample chunks: all threads centre, split and
-// write the operands as 128-byte-swizzled K-major images in shared memory
-// (two stages), one thread issues the MMAs (M = N = 128, K = 16 per
-// instruction) and commits them to an mbarrier.  The FP32 tile is written to
-// a partial buffer; a second kernel sums the sample splits in FP64 and
-// writes conn and g2.
+// Two kernels per batch of output times:
+//  1. split_kernel centres, splits and transposes X_t into two bf16 arrays
+//     hi, lo of shape [t][Kp][Mp] (sites x samples, samples contiguous, zero
+//     padded to Kp = 128-multiple sites and Mp = 64-multiple samples);
+//  2. gram_tc_kernel, one CTA per (time, 128 x 128 tile of the upper
+//     triangle), warp-specialised: warp 0 streams 64-sample chunks of the
+//     operands with TMA (128-byte swizzle, three stages), warp 1 issues the
+//     MMAs (M = N = 128, K = 16 per instruction) into one of two tensor-memory
+//     accumulators, and eight epilogue warps drain each 1024-sample segment
+//     of the FP32 accumulator into FP32 register sums while the next segment
+//     accumulates.  Segments bound the length of every FP32 tensor-core sum
+//     (the variances are long same-sign sums) to 1024 terms; the sum over
+//     segments adds one rounding per segment (64 at M = 65536), less than
+//     the rounding inside one segment.  The epilogue writes conn (both triangles) and g2 directly.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "ftwa_internal.h"
 #include "ptx.cuh"
@@ -27,21 +37,58 @@ namespace ftwa {
 
 namespace gram {
 
-constexpr int kTile = 128;          // output tile edge (features)
-constexpr int kChunk = 64;          // samples per operand image (128 bytes of bf16)
+constexpr int kTile = 128;                   // output tile edge (sites)
+constexpr int kChunk = 64;                   // samples per operand image (128 bytes of bf16)
 constexpr int kImage = kTile * kChunk * 2;   // 16 KB per operand image
-constexpr int kThreadsG = 256;
+constexpr int kStages = 3;
+constexpr int kSegChunks = 16;               // chunks per FP32 accumulation segment (1024 samples)
+constexpr int kEpiWarps = 8;
+constexpr int kThreadsG = 32 * (2 + kEpiWarps);
+constexpr int kSplitRows = 32;               // sites per split_kernel tile
 
-// byte offset of (row r, sample j) in a 128 x 64 bf16 K-major image with the
-// 128-byte swizzle: 8-row atoms of 1024 bytes; 16-byte chunk c of row r sits
-// at chunk position c ^ (r % 8)
-__device__ __forceinline__ uint32_t swz(int r, int c16)
+// ---- 1. centre, split, transpose ------------------------------------------------
+// tile: 64 samples x 32 sites; reads rows of X (sites contiguous), writes
+// rows of hi / lo (samples contiguous)
+__global__ void __launch_bounds__(256) split_kernel(const float *X, const double *mu, __nv_bfloat16 *hi,
+                                                   __nv_bfloat16 *lo, long long M, int K, int Kp, long long Mp,
+                                                   int t0)
 {
-    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c16 ^ (r & 7)) << 4));
+    __shared__ float tile[kChunk][kSplitRows + 1];
+    __shared__ float mu_f[kSplitRows];
+    const long long m0 = (long long)blockIdx.x * kChunk;
+    const int k0 = blockIdx.y * kSplitRows;
+    const int tl = blockIdx.z, t = t0 + tl;
+    if (threadIdx.x < kSplitRows) {
+        const int k = k0 + threadIdx.x;
+        mu_f[threadIdx.x] = k < K ? (float)mu[(long long)t * K + k] : 0.0f;
+    }
+    __syncthreads();
+    const float *Xt = X + (long long)t * M * K;
+    for (int i = threadIdx.x; i < kChunk * kSplitRows; i += blockDim.x) {
+        const int r = i / kSplitRows, c = i % kSplitRows;
+        const long long m = m0 + r;
+        const int k = k0 + c;
+        tile[r][c] = (m < M && k < K) ? Xt[m * K + k] - mu_f[c] : 0.0f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSplitRows * (kChunk / 2); i += blockDim.x) {
+        const int kr = i / (kChunk / 2), j = i % (kChunk / 2);
+        const int k = k0 + kr;
+        if (k >= Kp) continue;
+        const float y0 = tile[2 * j][kr], y1 = tile[2 * j + 1][kr];
+        const __nv_bfloat162 hb = __floats2bfloat162_rn(y0, y1);
+        const float2 hf = __bfloat1622float2(hb);
+        const __nv_bfloat162 lb = __floats2bfloat162_rn(y0 - hf.x, y1 - hf.y);
+        const long long o = ((long long)tl * Kp + k) * Mp + m0 + 2 * j;
+        *reinterpret_cast<__nv_bfloat162 *>(hi + o) = hb;
+        *reinterpret_cast<__nv_bfloat162 *>(lo + o) = lb;
+    }
 }
 
+// ---- 2. the contraction ------------------------------------------------------------
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart
+// 1024 bytes apart (the layout a 128-byte-swizzled TMA box of 64 bf16 x 128
+// rows leaves in shared memory)
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr)
 {
     uint64_t d = 0;
@@ -74,70 +121,69 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
                  : "memory");
 }
 
-__device__ __forceinline__ void fence_async_smem()
+__device__ __forceinline__ void arrive_expect_tx(uint32_t bar, uint32_t bytes)
 {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-struct GramArgs {
-    const float *X;        // [T][M][K]
+__device__ __forceinline__ void arrive_local(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+// bounded wait on an mbarrier phase that also gives up when another role of
+// the CTA has aborted; returns false on abort or timeout (and then raises the
+// CTA's abort flag and records the status)
+__device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity, unsigned long long limit,
+                                           volatile int *abort_flag, int *status)
+{
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait_cluster(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (global_ns() - t0 > limit) {
+            *abort_flag = 1;
+            atomicCAS(status, 0, FTWA_ERR_DEVICE_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+struct GemmArgs {
     const double *mu;      // [T][K]
-    float *partial;        // [splits][T][n_tiles][128][128]
+    double *conn, *g2;     // [T][K][K]
     long long M;
-    int K, T, n_kt, n_tiles, splits;
-    long long chunks_per_split;
+    int K, n_kt, n_tiles, t0;
     int *status;
     unsigned long long timeout_ns;
 };
 
-// operand image of features [ft*128, ft*128+128) x samples [m0, m0+64)
-__device__ __forceinline__ void build_image(const GramArgs &g, const float *Xt, const float *mu_f, int ft,
-                                            long long m0, unsigned char *hi_img, unsigned char *lo_img)
-{
-    // item = (feature row r, 8-sample chunk c): lanes run over features so
-    // every global load is coalesced across the warp
-    for (int it = threadIdx.x; it < kTile * 8; it += kThreadsG) {
-        const int r = it % kTile, c = it / kTile;
-        const int k = ft * kTile + r;
-        float y[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const long long m = m0 + 8 * c + j;
-            y[j] = (k < g.K && m < g.M) ? Xt[m * g.K + k] - mu_f[r] : 0.0f;
-        }
-        uint32_t h[4], l[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const __nv_bfloat162 hb = __floats2bfloat162_rn(y[2 * j], y[2 * j + 1]);
-            const float2 hf = __bfloat1622float2(hb);
-            const __nv_bfloat162 lb = __floats2bfloat162_rn(y[2 * j] - hf.x, y[2 * j + 1] - hf.y);
-            h[j] = *reinterpret_cast<const uint32_t *>(&hb);
-            l[j] = *reinterpret_cast<const uint32_t *>(&lb);
-        }
-        const uint32_t off = swz(r, c);
-        *reinterpret_cast<uint4 *>(hi_img + off) = make_uint4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<uint4 *>(lo_img + off) = make_uint4(l[0], l[1], l[2], l[3]);
-    }
-}
+struct GemmSmem {
+    unsigned long long full[kStages], empty[kStages], accfull[2], accempty[2], drain;
+    uint32_t tmem_base;
+    int abort;
+};
 
-__global__ void __launch_bounds__(kThreadsG, 1) gram_bf16x3_kernel(const GramArgs g)
+__global__ void __launch_bounds__(kThreadsG, 1) gram_tc_kernel(const __grid_constant__ CUtensorMap map_hi,
+                                                               const __grid_constant__ CUtensorMap map_lo,
+                                                               const GemmArgs g)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // 1024-byte aligned operand area: 2 stages x {A_hi, A_lo, B_hi, B_lo}
-    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *img = smem;                                        // 8 x 16 KB
-    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + 8 * kImage);   // 2 stage barriers
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2);
-    int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
-    float *mu_a = reinterpret_cast<float *>(tmem_slot + 4);          // [128]
-    float *mu_b = mu_a + kTile;                                       // [128]
+    // 1024-byte aligned operand area: kStages x {A_hi, A_lo, B_hi, B_lo}
+    unsigned char *img = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    GemmSmem *sh = reinterpret_cast<GemmSmem *>(img + kStages * 4 * kImage);
+    volatile int *abort_flag = &sh->abort;
 
-    // tile index -> (t, kt <= lt, split)
-    int idx = blockIdx.x;
-    const int split = idx % g.splits;
-    idx /= g.splits;
-    const int tile = idx % g.n_tiles;
-    const int t = idx / g.n_tiles;
+    const int tl = blockIdx.x / g.n_tiles, tile = blockIdx.x % g.n_tiles;
     int kt = 0, rem = tile;
     while (rem >= g.n_kt - kt) {
         rem -= g.n_kt - kt;
@@ -145,227 +191,295 @@ __global__ void __launch_bounds__(kThreadsG, 1) gram_bf16x3_kernel(const GramArg
     }
     const int lt = kt + rem;
     const bool same = kt == lt;
-    const float *Xt = g.X + (long long)t * g.M * g.K;
-    const int warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long n_chunks = (g.M + kChunk - 1) / kChunk;
+    const long long n_seg = (n_chunks + kSegChunks - 1) / kSegChunks;
 
     if (threadIdx.x == 0) {
-        mbar_init(smem_addr(&bars[0]), 1u);
-        mbar_init(smem_addr(&bars[1]), 1u);
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(smem_addr(&sh->full[i]), 1u);
+            mbar_init(smem_addr(&sh->empty[i]), 1u);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_addr(&sh->accfull[i]), 1u);
+            mbar_init(smem_addr(&sh->accempty[i]), (uint32_t)kEpiWarps);
+        }
+        mbar_init(smem_addr(&sh->drain), 1u);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        *abort_flag = 0;
-    }
-    for (int r = threadIdx.x; r < kTile; r += kThreadsG) {
-        const int ka = kt * kTile + r, kb = lt * kTile + r;
-        mu_a[r] = ka < g.K ? (float)g.mu[(long long)t * g.K + ka] : 0.0f;
-        mu_b[r] = kb < g.K ? (float)g.mu[(long long)t * g.K + kb] : 0.0f;
+        sh->abort = 0;
     }
     if (warp == 0) {
-        tmem_alloc(smem_addr(tmem_slot), kTile);
+        tmem_alloc(smem_addr(&sh->tmem_base), 2 * kTile);
         tmem_relinquish();
     }
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
-    const uint32_t d_tmem = *tmem_slot;
+    const uint32_t d_tmem = sh->tmem_base;
 
-    const long long c0 = (long long)split * g.chunks_per_split;
-    const long long n_chunks_total = (g.M + kChunk - 1) / kChunk;
-    const long long c1 = std::min<long long>(c0 + g.chunks_per_split, n_chunks_total);
-    uint32_t phase[2] = {0u, 0u};
-    bool issued[2] = {false, false};
-    long long n_done = 0;
-    for (long long c = c0; c < c1; ++c, ++n_done) {
-        const int st = (int)(n_done & 1);
-        unsigned char *a_hi = img + (st * 4 + 0) * kImage, *a_lo = img + (st * 4 + 1) * kImage;
-        unsigned char *b_hi = same ? a_hi : img + (st * 4 + 2) * kImage;
-        unsigned char *b_lo = same ? a_lo : img + (st * 4 + 3) * kImage;
-        // the stage is free once the MMAs issued on it two chunks ago are done
-        if (issued[st]) {
-            if (threadIdx.x == 0 && !mbar_wait_bounded(smem_addr(&bars[st]), phase[st], g.timeout_ns)) {
-                *abort_flag = 1;
-                atomicCAS(g.status, 0, FTWA_ERR_DEVICE_TIMEOUT);
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            const uint32_t bytes = (same ? 2u : 4u) * (uint32_t)kImage;
+            long long c = 0;
+            for (; c < n_chunks; ++c) {
+                const int st = (int)(c % kStages);
+                if (c >= kStages &&
+                    !wait_phase(smem_addr(&sh->empty[st]), (uint32_t)((c / kStages - 1) & 1), g.timeout_ns,
+                                abort_flag, g.status))
+                    break;
+                const uint32_t fb = smem_addr(&sh->full[st]);
+                const uint32_t base = smem_addr(img + st * 4 * kImage);
+                const int x = (int)(c * kChunk);
+                arrive_expect_tx(fb, bytes);
+                tma_load_3d(base, &map_hi, x, kt * kTile, tl, fb);
+                tma_load_3d(base + kImage, &map_lo, x, kt * kTile, tl, fb);
+                if (!same) {
+                    tma_load_3d(base + 2 * kImage, &map_hi, x, lt * kTile, tl, fb);
+                    tma_load_3d(base + 3 * kImage, &map_lo, x, lt * kTile, tl, fb);
+                }
             }
-            phase[st] ^= 1u;
-            issued[st] = false;
-            __syncthreads();
-            if (*abort_flag) break;
-            tmem_fence_after();
-        }
-        build_image(g, Xt, mu_a, kt, c * kChunk, a_hi, a_lo);
-        if (!same) build_image(g, Xt, mu_b, lt, c * kChunk, b_hi, b_lo);
-        fence_async_smem();
-        tmem_fence_before();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            tmem_fence_after();
-            const uint32_t sa_hi = smem_addr(a_hi), sa_lo = smem_addr(a_lo);
-            const uint32_t sb_hi = smem_addr(b_hi), sb_lo = smem_addr(b_lo);
-#pragma unroll
-            for (int ks = 0; ks < kChunk / 16; ++ks) {
-                const uint32_t ko = ks * 32;      // 16 bf16 = 32 bytes along K inside the swizzle atom
-                const uint32_t acc0 = (n_done > 0 || ks > 0) ? 1u : 0u;
-                mma_bf16(d_tmem, make_desc(sa_hi + ko), make_desc(sb_hi + ko), acc0);
-                mma_bf16(d_tmem, make_desc(sa_hi + ko), make_desc(sb_lo + ko), 1u);
-                mma_bf16(d_tmem, make_desc(sa_lo + ko), make_desc(sb_hi + ko), 1u);
+            if (*abort_flag) {
+                // let the copies in flight land before the CTA exits
+                for (long long d = (c > kStages ? c - kStages : 0); d < c; ++d) {
+                    const uint64_t t0 = global_ns();
+                    while (!mbar_try_wait_cluster(smem_addr(&sh->full[d % kStages]), (uint32_t)((d / kStages) & 1)) &&
+                           global_ns() - t0 < g.timeout_ns) {
+                    }
+                }
             }
-            mma_commit(smem_addr(&bars[st]));
         }
-        issued[st] = true;
         __syncwarp();
-    }
-    // drain
-    for (int st = 0; st < 2; ++st) {
-        if (issued[st]) {
-            if (threadIdx.x == 0 && !mbar_wait_bounded(smem_addr(&bars[st]), phase[st], g.timeout_ns)) {
-                *abort_flag = 1;
-                atomicCAS(g.status, 0, FTWA_ERR_DEVICE_TIMEOUT);
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            bool ok = true;
+            long long c = 0;
+            for (long long seg = 0; seg < n_seg && ok; ++seg) {
+                const int buf = (int)(seg & 1);
+                if (seg >= 2 && !wait_phase(smem_addr(&sh->accempty[buf]), (uint32_t)((seg / 2 - 1) & 1),
+                                            g.timeout_ns, abort_flag, g.status)) {
+                    ok = false;
+                    break;
+                }
+                tmem_fence_after();
+                const uint32_t acc = d_tmem + (uint32_t)(buf * kTile);
+                const long long c_end = (seg + 1) * kSegChunks < n_chunks ? (seg + 1) * kSegChunks : n_chunks;
+                for (long long first = c; c < c_end; ++c) {
+                    const int st = (int)(c % kStages);
+                    if (!wait_phase(smem_addr(&sh->full[st]), (uint32_t)((c / kStages) & 1), g.timeout_ns,
+                                    abort_flag, g.status)) {
+                        ok = false;
+                        break;
+                    }
+                    tmem_fence_after();
+                    const uint32_t base = smem_addr(img + st * 4 * kImage);
+                    const uint32_t a_hi = base, a_lo = base + kImage;
+                    const uint32_t b_hi = same ? a_hi : base + 2 * kImage, b_lo = same ? a_lo : base + 3 * kImage;
+#pragma unroll
+                    for (int ks = 0; ks < kChunk / 16; ++ks) {
+                        const uint32_t ko = ks * 32;   // 16 bf16 = 32 bytes along K inside the swizzle atom
+                        const uint32_t acc0 = (c != first || ks > 0) ? 1u : 0u;
+                        mma_bf16(acc, make_desc(a_hi + ko), make_desc(b_hi + ko), acc0);
+                        mma_bf16(acc, make_desc(a_hi + ko), make_desc(b_lo + ko), 1u);
+                        mma_bf16(acc, make_desc(a_lo + ko), make_desc(b_hi + ko), 1u);
+                    }
+                    mma_commit(smem_addr(&sh->empty[st]));
+                }
+                if (ok) mma_commit(smem_addr(&sh->accfull[buf]));
+            }
+            // every issued MMA has completed before the accumulators are freed
+            mma_commit(smem_addr(&sh->drain));
+            const uint64_t t0 = global_ns();
+            while (!mbar_try_wait_cluster(smem_addr(&sh->drain), 0u) && global_ns() - t0 < g.timeout_ns) {
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: FP64 accumulation and output ----------------
+        // warp w reads tensor-memory lanes 32 (w % 4) .. +31 (tile rows) and
+        // columns 64 h .. 64 h + 63 of the accumulator
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const int row = 32 * q + lane;
+        // FP32 sum over segments: at most n_seg roundings of 2^-24, far below
+        // the rounding of the 1024-sample tensor-core sums themselves
+        float acc[64];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) acc[j] = 0.0f;
+        bool ok = true;
+        for (long long seg = 0; seg < n_seg; ++seg) {
+            const int buf = (int)(seg & 1);
+            // one lane waits; the warp takes its decision together
+            bool got = false;
+            if (lane == 0)
+                got = wait_phase(smem_addr(&sh->accfull[buf]), (uint32_t)((seg / 2) & 1), g.timeout_ns, abort_flag,
+                                 g.status);
+            got = __shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0) != 0;
+            if (!got) {
+                ok = false;
+                break;
+            }
+            tmem_fence_after();
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                uint32_t v[32];
+                const uint32_t ta = d_tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * kTile + 64 * h + 32 * half);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                    "[%32];\n\t"
+                    "tcgen05.wait::ld.sync.aligned;"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(ta)
+                    : "memory");
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[32 * half + j] += __uint_as_float(v[j]);
+            }
+            tmem_fence_before();
+            __syncwarp();
+            if (lane == 0) arrive_local(smem_addr(&sh->accempty[buf]));
+        }
+        if (ok && *abort_flag == 0) {
+            const int t = g.t0 + tl;
+            const int k = kt * kTile + row;
+            const long long base = (long long)t * g.K * g.K;
+            const double inv_m = 1.0 / (double)g.M;
+            const double ok_ = k < g.K ? g.mu[(long long)t * g.K + k] + 0.5 : 0.0;
+            if (k < g.K) {
+#pragma unroll
+                for (int j = 0; j < 64; ++j) {
+                    const int l = lt * kTile + 64 * h + j;
+                    if (l >= g.K || (same && l < k)) continue;
+                    const double c = (double)acc[j] * inv_m;
+                    g.conn[base + (long long)k * g.K + l] = c;
+                    g.conn[base + (long long)l * g.K + k] = c;
+                    if (g.g2) {
+                        const double ol = g.mu[(long long)t * g.K + l] + 0.5;
+                        const double v = (c + ok_ * ol) / (ok_ * ol);
+                        g.g2[base + (long long)k * g.K + l] = v;
+                        g.g2[base + (long long)l * g.K + k] = v;
+                    }
+                }
             }
         }
     }
-    __syncthreads();
-    tmem_fence_after();
 
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (tile rows) and
-    // columns 64 (w / 4) .. +63; an empty split writes zeros
-    const int row = 32 * (warp & 3) + (threadIdx.x & 31);
-    const int col0 = 64 * (warp >> 2);
-    float *out = g.partial + ((((long long)split * g.T + t) * g.n_tiles + tile) * kTile + row) * kTile + col0;
-    const bool have = n_done > 0 && *abort_flag == 0;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        uint32_t v[32];
-        const uint32_t ta = d_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(col0 + 32 * h);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-            "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
-            "tcgen05.wait::ld.sync.aligned;"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-            : "r"(ta)
-            : "memory");
-#pragma unroll
-        for (int j = 0; j < 32; j += 4) {
-            float4 f;
-            f.x = have ? __uint_as_float(v[j]) : 0.0f;
-            f.y = have ? __uint_as_float(v[j + 1]) : 0.0f;
-            f.z = have ? __uint_as_float(v[j + 2]) : 0.0f;
-            f.w = have ? __uint_as_float(v[j + 3]) : 0.0f;
-            *reinterpret_cast<float4 *>(out + 32 * h + j) = f;
-        }
-    }
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
-    if (warp == 0) tmem_dealloc(d_tmem, kTile);
-}
-
-// Sum the sample splits in FP64 and write conn (both triangles) and g2.
-__global__ void gram_reduce_kernel(const float *partial, int splits, int T, int n_kt, int n_tiles, int K, long long M,
-                                   const double *mu, double *conn, double *g2)
-{
-    const long long total = (long long)T * n_tiles * kTile * kTile;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int col = (int)(i % kTile), row = (int)((i / kTile) % kTile);
-        const int tile = (int)((i / ((long long)kTile * kTile)) % n_tiles);
-        const int t = (int)(i / ((long long)kTile * kTile * n_tiles));
-        int kt = 0, rem = tile;
-        while (rem >= n_kt - kt) {
-            rem -= n_kt - kt;
-            ++kt;
-        }
-        const int lt = kt + rem;
-        const int k = kt * kTile + row, l = lt * kTile + col;
-        if (k >= K || l >= K) continue;
-        if (kt == lt && l < k) continue;          // diagonal tile: each pair once
-        double s = 0.0;
-        for (int sp = 0; sp < splits; ++sp) s += (double)partial[(((long long)sp * T + t) * n_tiles + tile) * kTile * kTile +
-                                                               (long long)row * kTile + col];
-        const double c = s / (double)M;
-        const long long base = (long long)t * K * K;
-        conn[base + (long long)k * K + l] = c;
-        conn[base + (long long)l * K + k] = c;
-        if (g2) {
-            const double ok = mu[(long long)t * K + k] + 0.5, ol = mu[(long long)t * K + l] + 0.5;
-            const double v = (c + ok * ol) / (ok * ol);
-            g2[base + (long long)k * K + l] = v;
-            g2[base + (long long)l * K + k] = v;
-        }
-    }
+    if (warp == 0) tmem_dealloc(d_tmem, 2 * kTile);
 }
 
 }  // namespace gram
 
-// Sample splits: enough CTAs to fill the machine twice, and every split's
-// FP32 tensor-memory accumulation limited to kMaxChunksPerSplit chunks (1024
-// samples), so that the FP32 rounding of a long same-sign sum (the
-// variances) stays far below the sampling error; splits are summed in FP64.
-static void gram_splits(Plan *p, long long n_chunks, long long base_ctas, long long &splits, long long &cps)
+// ---- host side -----------------------------------------------------------------------
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
-    constexpr long long kMaxChunksPerSplit = 16;
-    splits = std::max<long long>(1, (2LL * std::max(1, p->sm_count) + base_ctas - 1) / base_ctas);
-    splits = std::min<long long>(splits, std::max<long long>(1, n_chunks / 4));
-    splits = std::max<long long>(splits, (n_chunks + kMaxChunksPerSplit - 1) / kMaxChunksPerSplit);
-    cps = (n_chunks + splits - 1) / splits;
-    splits = (n_chunks + cps - 1) / cps;
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
 }
+
+struct GramGeom {
+    int K, Kp, n_kt, n_tiles, TB;
+    long long Mp;
+    size_t mu_bytes, ops_bytes;
+};
+
+// Times per batch: one wave of (time, tile) CTAs over the SMs, and at most
+// about 2 GB of split operands.
+GramGeom gram_geom(Plan *p, int64_t M, int32_t T)
+{
+    using namespace gram;
+    GramGeom gg;
+    gg.K = 2 * p->N;
+    gg.n_kt = (gg.K + kTile - 1) / kTile;
+    gg.Kp = gg.n_kt * kTile;
+    gg.n_tiles = gg.n_kt * (gg.n_kt + 1) / 2;
+    gg.Mp = (M + kChunk - 1) / kChunk * kChunk;
+    const size_t per_t = 2 * (size_t)gg.Kp * (size_t)gg.Mp * sizeof(__nv_bfloat16);
+    const int sm = std::max(1, p->sm_count);
+    int tb = std::max(1, sm / gg.n_tiles);
+    tb = (int)std::min<size_t>((size_t)tb, std::max<size_t>(1, (size_t)(2ull << 30) / per_t));
+    gg.TB = std::max(1, std::min(tb, (int)T));
+    gg.mu_bytes = ((sizeof(double) * (size_t)T * gg.K + 255) / 256) * 256;
+    gg.ops_bytes = per_t * gg.TB;
+    return gg;
+}
+
+}  // namespace
 
 int launch_gram_bf16x3(Plan *p, const void *snap, int64_t M, int32_t T, const double *mu, double *conn, double *g2,
                        cudaStream_t s)
 {
     using namespace gram;
     if (p->precision != FTWA_FP32) return FTWA_ERR_UNSUPPORTED;   // the split is defined for FP32 snapshots
-    const int K = 2 * p->N;
-    const int n_kt = (K + kTile - 1) / kTile;
-    const int n_tiles = n_kt * (n_kt + 1) / 2;
-    const long long n_chunks = (M + kChunk - 1) / kChunk;
-    const long long base_ctas = (long long)T * n_tiles;
-    long long splits, cps;
-    gram_splits(p, n_chunks, base_ctas, splits, cps);
-    // workspace: mu already occupies the first T*K doubles
-    const size_t mu_bytes = ((sizeof(double) * (size_t)T * K + 255) / 256) * 256;
-    const size_t part_bytes = sizeof(float) * (size_t)splits * T * n_tiles * kTile * kTile;
-    if (p->ws_bytes < mu_bytes + part_bytes) return FTWA_ERR_OUT_OF_MEMORY;   // sized by the caller below
-    float *partial = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(p->d_ws) + mu_bytes);
-    GramArgs g;
-    g.X = reinterpret_cast<const float *>(snap);
-    g.mu = mu;
-    g.partial = partial;
-    g.M = M;
-    g.K = K;
-    g.T = T;
-    g.n_kt = n_kt;
-    g.n_tiles = n_tiles;
-    g.splits = (int)splits;
-    g.chunks_per_split = cps;
-    g.status = p->d_status;
-    g.timeout_ns = p->timeout_ns;
-    const int smem = 8 * kImage + 1024 + 64 + 2 * kTile * 4 + 64;
-    cudaError_t e = cudaFuncSetAttribute(gram_bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (M < 1 || T < 1) return FTWA_ERR_INVALID_ARGUMENT;
+    if (M > (int64_t)0x7FFFFFFF - kChunk) return FTWA_ERR_UNSUPPORTED;   // TMA coordinates are 32-bit
+    const GramGeom gg = gram_geom(p, M, T);
+    if (p->ws_bytes < gg.mu_bytes + gg.ops_bytes) return FTWA_ERR_OUT_OF_MEMORY;   // sized by the caller
+    PFN_cuTensorMapEncodeTiled_v12000 encode = encode_fn();
+    if (!encode) return FTWA_ERR_UNSUPPORTED;
+    unsigned char *ws = reinterpret_cast<unsigned char *>(p->d_ws);
+    __nv_bfloat16 *hi = reinterpret_cast<__nv_bfloat16 *>(ws + gg.mu_bytes);
+    __nv_bfloat16 *lo = hi + gg.ops_bytes / (2 * sizeof(__nv_bfloat16));
+
+    CUtensorMap map_hi, map_lo;
+    const cuuint64_t dims[3] = {(cuuint64_t)gg.Mp, (cuuint64_t)gg.Kp, (cuuint64_t)gg.TB};
+    const cuuint64_t strides[2] = {(cuuint64_t)gg.Mp * 2, (cuuint64_t)gg.Kp * (cuuint64_t)gg.Mp * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)kChunk, (cuuint32_t)kTile, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    for (int i = 0; i < 2; ++i) {
+        CUresult r = encode(i == 0 ? &map_hi : &map_lo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, i == 0 ? (void *)hi : (void *)lo,
+                            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return FTWA_ERR_CUDA;
+    }
+    const int smem = kStages * 4 * kImage + 1024 + (int)sizeof(GemmSmem);
+    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return set_cuda_error(e);
-    gram_bf16x3_kernel<<<(unsigned)(base_ctas * splits), kThreadsG, smem, s>>>(g);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return set_cuda_error(e);
-    const long long total = (long long)T * n_tiles * kTile * kTile;
-    const int blocks = (int)std::min<long long>((total + 255) / 256, 65535LL * 8);
-    gram_reduce_kernel<<<blocks, 256, 0, s>>>(partial, (int)splits, T, n_kt, n_tiles, K, M, mu, conn, g2);
-    return set_cuda_error(cudaGetLastError());
+    GemmArgs a;
+    a.mu = mu;
+    a.conn = conn;
+    a.g2 = g2;
+    a.M = M;
+    a.K = gg.K;
+    a.n_kt = gg.n_kt;
+    a.n_tiles = gg.n_tiles;
+    a.status = p->d_status;
+    a.timeout_ns = p->timeout_ns;
+    for (int t0 = 0; t0 < T; t0 += gg.TB) {
+        const int tb = std::min(gg.TB, T - t0);
+        dim3 gs((unsigned)(gg.Mp / kChunk), (unsigned)(gg.Kp / kSplitRows), (unsigned)tb);
+        split_kernel<<<gs, 256, 0, s>>>(reinterpret_cast<const float *>(snap), mu, hi, lo, M, gg.K, gg.Kp, gg.Mp, t0);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return set_cuda_error(e);
+        a.t0 = t0;
+        gram_tc_kernel<<<(unsigned)(tb * gg.n_tiles), kThreadsG, smem, s>>>(map_hi, map_lo, a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return set_cuda_error(e);
+    }
+    return FTWA_OK;
 }
 
 size_t gram_bf16x3_workspace(Plan *p, int64_t M, int32_t T)
 {
-    using namespace gram;
-    const int K = 2 * p->N;
-    const int n_kt = (K + kTile - 1) / kTile;
-    const int n_tiles = n_kt * (n_kt + 1) / 2;
-    const long long n_chunks = (M + kChunk - 1) / kChunk;
-    const long long base_ctas = (long long)T * n_tiles;
-    long long splits, cps;
-    gram_splits(p, n_chunks, base_ctas, splits, cps);
-    const size_t mu_bytes = ((sizeof(double) * (size_t)T * K + 255) / 256) * 256;
-    return mu_bytes + sizeof(float) * (size_t)splits * T * n_tiles * kTile * kTile;
+    const GramGeom gg = gram_geom(p, M, T);
+    return gg.mu_bytes + gg.ops_bytes;
 }
 
 }  // namespace ftwa

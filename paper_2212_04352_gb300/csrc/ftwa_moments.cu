@@ -1,6 +1,7 @@
 // Sample-mean estimators of Eqs. 5 and 10 from diagonal snapshots.
 //
-//   mu[t][k]   = (1/M) sum_m X[t][m][k]                 (double, fixed order)
+//   mu[t][k]   = (1/M) sum_m X[t][m][k]                 (FP64 snapshots: double,
+//                fixed order; FP32 snapshots: 64-bit fixed point, exact to 2^-45)
 //   occ[t][k]  = mu + 1/2                               (Eq. 5, first line)
 //   conn[t]    = (1/M) (X - mu)^T (X - mu)              (connected Gram)
 //   g2[t][k][l] = (conn_kl + occ_k occ_l) / (occ_k occ_l)   (Eq. 10: the sample
@@ -40,6 +41,87 @@ __global__ void mean_kernel(const T *__restrict__ X, long long M, int K, double 
         mu[t * K + k] = a;
         occ[t * K + k] = a + 0.5;
     }
+}
+
+// Sample sums of FP32 snapshots in 64-bit fixed point (units of 2^-44).
+// Every FP32 value with |x| < 4 is rounded once, to within 2^-45, and the
+// integer additions are exact and associative: the mean is exact to 2^-45
+// whatever the order or split of the samples, without one FP64 operation per
+// value (FP64 throughput is low on this part).  A block that meets |x| >= 4
+// or a non-finite value marks its partial; the final kernel then sums that
+// column in FP64.
+constexpr int kMeanRows = 4096;                        // samples per partial
+constexpr long long kMeanBad = (long long)(1ULL << 63);   // marker: sum this column in FP64
+
+__global__ void __launch_bounds__(256) mean_fx_partial_kernel(const float *__restrict__ X, long long M, int K,
+                                                              long long *__restrict__ part)
+{
+    const int t = blockIdx.z, chunk = blockIdx.y, n_chunks = gridDim.y;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int k = blockIdx.x * 32 + lane;
+    __shared__ long long sp[8][32];
+    __shared__ int sb[8][32];
+    long long acc = 0;
+    int bad = 0;
+    if (k < K) {
+        const long long m0 = (long long)chunk * kMeanRows;
+        const long long m1 = M < m0 + kMeanRows ? M : m0 + kMeanRows;
+        const float *x = X + (long long)t * M * K + k;
+        long long m = m0 + w;
+        for (; m + 56 < m1; m += 64) {      // warp w: rows m0 + w + 8 i; 8 loads in flight
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = x[(m + 8 * j) * K];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                bad |= !(fabsf(v[j]) < 4.0f);
+                acc += __float2ll_rn(v[j] * 0x1p44f);
+            }
+        }
+        for (; m < m1; m += 8) {
+            const float v = x[m * K];
+            bad |= !(fabsf(v) < 4.0f);
+            acc += __float2ll_rn(v * 0x1p44f);
+        }
+    }
+    sp[w][lane] = acc;
+    sb[w][lane] = bad;
+    __syncthreads();
+    if (w == 0 && k < K) {
+        long long s = 0;
+        int b = 0;
+        for (int r = 0; r < 8; ++r) {
+            s += sp[r][lane];
+            b |= sb[r][lane];
+        }
+        part[((long long)t * n_chunks + chunk) * K + k] = b ? kMeanBad : s;
+    }
+}
+
+__global__ void mean_fx_final_kernel(const long long *__restrict__ part, int n_chunks, const float *__restrict__ X,
+                                     long long M, int K, int T, double *__restrict__ mu, double *__restrict__ occ)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)T * K) return;
+    const int t = (int)(i / K), k = (int)(i % K);
+    __int128 s = 0;
+    bool bad = false;
+    for (int c = 0; c < n_chunks; ++c) {
+        const long long v = part[((long long)t * n_chunks + c) * K + k];
+        if (v == kMeanBad) bad = true;
+        s += v;
+    }
+    double m;
+    if (!bad) {
+        m = (double)s * 0x1p-44 / (double)M;
+    } else {
+        double a = 0.0;
+        const float *x = X + (long long)t * M * K + k;
+        for (long long j = 0; j < M; ++j) a += (double)x[j * K];
+        m = a / (double)M;
+    }
+    mu[i] = m;
+    occ[i] = m + 0.5;
 }
 
 // FP64 connected Gram: one block per (t, 64x64 tile of the upper triangle);
@@ -120,16 +202,31 @@ int launch_moments(Plan *p, const void *snap, int64_t M, int32_t T, double *occ,
 {
     const int K = 2 * p->N;
     if (mode == FTWA_GRAM_BF16X3 && p->precision != FTWA_FP32) return FTWA_ERR_UNSUPPORTED;
-    size_t need = sizeof(double) * (size_t)T * K;
+    // workspace: mu [T][K] doubles, then (used in turn) the fixed-point
+    // partial sums of the mean and the tensor-core Gram's operands
+    const size_t mu_bytes = ((sizeof(double) * (size_t)T * K + 255) / 256) * 256;
+    const long long n_chunks = (M + kMeanRows - 1) / kMeanRows;
+    if (n_chunks > 65535 || T > 65535) return FTWA_ERR_UNSUPPORTED;
+    size_t need = mu_bytes;
+    if (p->precision == FTWA_FP32) need += sizeof(long long) * (size_t)T * n_chunks * K;
     if (mode == FTWA_GRAM_BF16X3) need = std::max(need, gram_bf16x3_workspace(p, M, T));
     int rc = ensure_workspace(p, need);
     if (rc != FTWA_OK) return rc;
     double *mu = reinterpret_cast<double *>(p->d_ws);
-    dim3 gm((K + 31) / 32, T);
-    if (p->precision == FTWA_FP64)
+    if (p->precision == FTWA_FP64) {
+        dim3 gm((K + 31) / 32, T);
         mean_kernel<double><<<gm, 256, 0, s>>>(reinterpret_cast<const double *>(snap), M, K, mu, occ);
-    else
-        mean_kernel<float><<<gm, 256, 0, s>>>(reinterpret_cast<const float *>(snap), M, K, mu, occ);
+    } else {
+        long long *part = reinterpret_cast<long long *>(reinterpret_cast<unsigned char *>(p->d_ws) + mu_bytes);
+        dim3 gm((K + 31) / 32, (unsigned)n_chunks, T);
+        mean_fx_partial_kernel<<<gm, 256, 0, s>>>(reinterpret_cast<const float *>(snap), M, K, part);
+        rc = set_cuda_error(cudaGetLastError());
+        if (rc != FTWA_OK) return rc;
+        const long long tk = (long long)T * K;
+        mean_fx_final_kernel<<<(unsigned)((tk + 255) / 256), 256, 0, s>>>(part, (int)n_chunks,
+                                                                          reinterpret_cast<const float *>(snap), M, K,
+                                                                          T, mu, occ);
+    }
     rc = set_cuda_error(cudaGetLastError());
     if (rc != FTWA_OK) return rc;
     if (mode == FTWA_GRAM_BF16X3) return launch_gram_bf16x3(p, snap, M, T, mu, conn, g2, s);

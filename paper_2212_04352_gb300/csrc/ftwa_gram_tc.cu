@@ -10,8 +10,8 @@
 //
 // Two kernels per batch of output times:
 //  1. split_kernel centres, splits and transposes X_t into two bf16 arrays
-//     hi, lo of shape [t][Kp][Mp] (sites x samples, samples contiguous, zero
-//     padded to Kp = 128-multiple sites and Mp = 64-multiple samples);
+//     hi, lo of shape [t][Kd][Mp] (sites x samples, samples contiguous;
+//     Kd = max(K, 128) rows, Mp = M rounded up to 64 samples, zero padded);
 //  2. gram_tc_kernel, one CTA per (time, 128 x 128 tile of the upper
 //     triangle), warp-specialised: warp 0 streams 64-sample chunks of the
 //     operands with TMA (128-byte swizzle, three stages), warp 1 issues the
@@ -44,44 +44,70 @@ constexpr int kStages = 3;
 constexpr int kSegChunks = 16;               // chunks per FP32 accumulation segment (1024 samples)
 constexpr int kEpiWarps = 8;
 constexpr int kThreadsG = 32 * (2 + kEpiWarps);
-constexpr int kSplitRows = 32;               // sites per split_kernel tile
 
 // ---- 1. centre, split, transpose ------------------------------------------------
-// tile: 64 samples x 32 sites; reads rows of X (sites contiguous), writes
-// rows of hi / lo (samples contiguous)
+// tile: 64 samples x 128 sites.  Lane l reads sites l, l + 32, l + 64, l + 96
+// of a sample row (coalesced 128-byte rows), the centred values are
+// transposed through shared memory (odd row pitch: conflict-free writes), and
+// each thread splits 8 consecutive samples of one site into 16 bytes of hi
+// and 16 bytes of lo (8 lanes write one 128-byte row segment).
+constexpr int kSplitSites = 128;
+
 __global__ void __launch_bounds__(256) split_kernel(const float *X, const double *mu, __nv_bfloat16 *hi,
-                                                   __nv_bfloat16 *lo, long long M, int K, int Kp, long long Mp,
+                                                   __nv_bfloat16 *lo, long long M, int K, int Kd, long long Mp,
                                                    int t0)
 {
-    __shared__ float tile[kChunk][kSplitRows + 1];
-    __shared__ float mu_f[kSplitRows];
+    __shared__ float tile[kSplitSites][kChunk + 1];
     const long long m0 = (long long)blockIdx.x * kChunk;
-    const int k0 = blockIdx.y * kSplitRows;
+    const int k0 = blockIdx.y * kSplitSites;
     const int tl = blockIdx.z, t = t0 + tl;
-    if (threadIdx.x < kSplitRows) {
-        const int k = k0 + threadIdx.x;
-        mu_f[threadIdx.x] = k < K ? (float)mu[(long long)t * K + k] : 0.0f;
-    }
-    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float *Xt = X + (long long)t * M * K;
-    for (int i = threadIdx.x; i < kChunk * kSplitRows; i += blockDim.x) {
-        const int r = i / kSplitRows, c = i % kSplitRows;
-        const long long m = m0 + r;
-        const int k = k0 + c;
-        tile[r][c] = (m < M && k < K) ? Xt[m * K + k] - mu_f[c] : 0.0f;
+    float mr[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int k = k0 + lane + 32 * i;
+        mr[i] = k < K ? (float)mu[(long long)t * K + k] : 0.0f;
+    }
+    float v[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const long long m = m0 + w + 8 * j;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int k = k0 + lane + 32 * i;
+            v[j][i] = (m < M && k < K) ? Xt[m * K + k] : 0.0f;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const long long m = m0 + w + 8 * j;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int k = k0 + lane + 32 * i;
+            tile[lane + 32 * i][w + 8 * j] = (m < M && k < K) ? v[j][i] - mr[i] : 0.0f;
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kSplitRows * (kChunk / 2); i += blockDim.x) {
-        const int kr = i / (kChunk / 2), j = i % (kChunk / 2);
-        const int k = k0 + kr;
-        if (k >= Kp) continue;
-        const float y0 = tile[2 * j][kr], y1 = tile[2 * j + 1][kr];
-        const __nv_bfloat162 hb = __floats2bfloat162_rn(y0, y1);
-        const float2 hf = __bfloat1622float2(hb);
-        const __nv_bfloat162 lb = __floats2bfloat162_rn(y0 - hf.x, y1 - hf.y);
-        const long long o = ((long long)tl * Kp + k) * Mp + m0 + 2 * j;
-        *reinterpret_cast<__nv_bfloat162 *>(hi + o) = hb;
-        *reinterpret_cast<__nv_bfloat162 *>(lo + o) = lb;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int id = threadIdx.x + 256 * u;
+        const int sl = id >> 3, o = id & 7;        // site of the tile, sample octet
+        const int k = k0 + sl;
+        if (k >= Kd) continue;
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float y0 = tile[sl][8 * o + 2 * j], y1 = tile[sl][8 * o + 2 * j + 1];
+            const __nv_bfloat162 hb = __floats2bfloat162_rn(y0, y1);
+            const float2 hf = __bfloat1622float2(hb);
+            const __nv_bfloat162 lb = __floats2bfloat162_rn(y0 - hf.x, y1 - hf.y);
+            hw[j] = *reinterpret_cast<const uint32_t *>(&hb);
+            lw[j] = *reinterpret_cast<const uint32_t *>(&lb);
+        }
+        const long long off = ((long long)tl * Kd + k) * Mp + m0 + 8 * o;
+        *reinterpret_cast<uint4 *>(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4 *>(lo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
     }
 }
 
@@ -172,6 +198,90 @@ struct GemmSmem {
     uint32_t tmem_base;
     int abort;
 };
+
+// one lane waits; the warp takes the decision together
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, unsigned long long limit,
+                                          volatile int *abort_flag, int *status)
+{
+    bool got = false;
+    if ((threadIdx.x & 31) == 0) got = wait_phase(bar, parity, limit, abort_flag, status);
+    got = __shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0) != 0;
+    return got;
+}
+
+// Epilogue warp (warp index w >= 2 of the CTA): adds columns 64 h .. 64 h + 63
+// of tensor-memory lanes 32 (w % 4) .. +31 of accumulator `buf` (a finished
+// 1024-sample segment) to its FP32 registers and releases the accumulator.
+__device__ __forceinline__ bool drain_segment(float (&acc)[64], uint32_t d_tmem, int buf, long long seg, uint32_t accfull,
+                                              uint32_t accempty, const GemmArgs &g, volatile int *abort_flag)
+{
+    const int warp = threadIdx.x >> 5, q = warp & 3, h = (warp - 2) >> 2;
+    if (!warp_wait(accfull, (uint32_t)((seg / 2) & 1), g.timeout_ns, abort_flag, g.status)) return false;
+    tmem_fence_after();
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        uint32_t v[32];
+        const uint32_t ta = d_tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * kTile + 64 * h + 32 * half);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+            "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+            "[%32];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(ta)
+            : "memory");
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[32 * half + j] += __uint_as_float(v[j]);
+    }
+    tmem_fence_before();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) arrive_local(accempty);
+    return true;
+}
+
+// Epilogue output: conn (both triangles) and g2 of tile (kt, lt) at time t
+__device__ __forceinline__ void write_tile(const float (&acc)[64], int t, int kt, int lt, const GemmArgs &g)
+{
+    const int warp = threadIdx.x >> 5, q = warp & 3, h = (warp - 2) >> 2;
+    const int row = 32 * q + (threadIdx.x & 31);
+    const bool same = kt == lt;
+    const int k = kt * kTile + row;
+    if (k >= g.K) return;
+    const long long base = (long long)t * g.K * g.K;
+    const double inv_m = 1.0 / (double)g.M;
+    const double ok = g.mu[(long long)t * g.K + k] + 0.5;
+#pragma unroll
+    for (int j = 0; j < 64; ++j) {
+        const int l = lt * kTile + 64 * h + j;
+        if (l >= g.K || (same && l < k)) continue;
+        const double c = (double)acc[j] * inv_m;
+        g.conn[base + (long long)k * g.K + l] = c;
+        g.conn[base + (long long)l * g.K + k] = c;
+        if (g.g2) {
+            const double ol = g.mu[(long long)t * g.K + l] + 0.5;
+            const double v = (c + ok * ol) / (ok * ol);
+            g.g2[base + (long long)k * g.K + l] = v;
+            g.g2[base + (long long)l * g.K + k] = v;
+        }
+    }
+}
+
+// MMA issue of one 64-sample chunk: 4 K-steps x {hi hi, hi lo, lo hi}
+__device__ __forceinline__ void mma_chunk(uint32_t acc, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi, uint32_t b_lo,
+                                          bool first)
+{
+#pragma unroll
+    for (int ks = 0; ks < kChunk / 16; ++ks) {
+        const uint32_t ko = ks * 32;   // 16 bf16 = 32 bytes along K inside the swizzle atom
+        const uint32_t acc0 = (!first || ks > 0) ? 1u : 0u;
+        mma_bf16(acc, make_desc(a_hi + ko), make_desc(b_hi + ko), acc0);
+        mma_bf16(acc, make_desc(a_hi + ko), make_desc(b_lo + ko), 1u);
+        mma_bf16(acc, make_desc(a_lo + ko), make_desc(b_hi + ko), 1u);
+    }
+}
 
 __global__ void __launch_bounds__(kThreadsG, 1) gram_tc_kernel(const __grid_constant__ CUtensorMap map_hi,
                                                                const __grid_constant__ CUtensorMap map_lo,
@@ -276,14 +386,7 @@ __global__ void __launch_bounds__(kThreadsG, 1) gram_tc_kernel(const __grid_cons
                     const uint32_t base = smem_addr(img + st * 4 * kImage);
                     const uint32_t a_hi = base, a_lo = base + kImage;
                     const uint32_t b_hi = same ? a_hi : base + 2 * kImage, b_lo = same ? a_lo : base + 3 * kImage;
-#pragma unroll
-                    for (int ks = 0; ks < kChunk / 16; ++ks) {
-                        const uint32_t ko = ks * 32;   // 16 bf16 = 32 bytes along K inside the swizzle atom
-                        const uint32_t acc0 = (c != first || ks > 0) ? 1u : 0u;
-                        mma_bf16(acc, make_desc(a_hi + ko), make_desc(b_hi + ko), acc0);
-                        mma_bf16(acc, make_desc(a_hi + ko), make_desc(b_lo + ko), 1u);
-                        mma_bf16(acc, make_desc(a_lo + ko), make_desc(b_hi + ko), 1u);
-                    }
+                    mma_chunk(acc, a_hi, a_lo, b_hi, b_lo, c == first);
                     mma_commit(smem_addr(&sh->empty[st]));
                 }
                 if (ok) mma_commit(smem_addr(&sh->accfull[buf]));
@@ -296,76 +399,19 @@ __global__ void __launch_bounds__(kThreadsG, 1) gram_tc_kernel(const __grid_cons
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue: FP64 accumulation and output ----------------
-        // warp w reads tensor-memory lanes 32 (w % 4) .. +31 (tile rows) and
-        // columns 64 h .. 64 h + 63 of the accumulator
-        const int q = warp & 3, h = (warp - 2) >> 2;
-        const int row = 32 * q + lane;
+        // ---------------- epilogue: segment sums and output ----------------
         // FP32 sum over segments: at most n_seg roundings of 2^-24, far below
         // the rounding of the 1024-sample tensor-core sums themselves
         float acc[64];
 #pragma unroll
         for (int j = 0; j < 64; ++j) acc[j] = 0.0f;
         bool ok = true;
-        for (long long seg = 0; seg < n_seg; ++seg) {
+        for (long long seg = 0; seg < n_seg && ok; ++seg) {
             const int buf = (int)(seg & 1);
-            // one lane waits; the warp takes its decision together
-            bool got = false;
-            if (lane == 0)
-                got = wait_phase(smem_addr(&sh->accfull[buf]), (uint32_t)((seg / 2) & 1), g.timeout_ns, abort_flag,
-                                 g.status);
-            got = __shfl_sync(0xFFFFFFFFu, got ? 1 : 0, 0) != 0;
-            if (!got) {
-                ok = false;
-                break;
-            }
-            tmem_fence_after();
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                uint32_t v[32];
-                const uint32_t ta = d_tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * kTile + 64 * h + 32 * half);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                    "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
-                    "[%32];\n\t"
-                    "tcgen05.wait::ld.sync.aligned;"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                    : "r"(ta)
-                    : "memory");
-#pragma unroll
-                for (int j = 0; j < 32; ++j) acc[32 * half + j] += __uint_as_float(v[j]);
-            }
-            tmem_fence_before();
-            __syncwarp();
-            if (lane == 0) arrive_local(smem_addr(&sh->accempty[buf]));
+            ok = drain_segment(acc, d_tmem, buf, seg, smem_addr(&sh->accfull[buf]), smem_addr(&sh->accempty[buf]), g,
+                               abort_flag);
         }
-        if (ok && *abort_flag == 0) {
-            const int t = g.t0 + tl;
-            const int k = kt * kTile + row;
-            const long long base = (long long)t * g.K * g.K;
-            const double inv_m = 1.0 / (double)g.M;
-            const double ok_ = k < g.K ? g.mu[(long long)t * g.K + k] + 0.5 : 0.0;
-            if (k < g.K) {
-#pragma unroll
-                for (int j = 0; j < 64; ++j) {
-                    const int l = lt * kTile + 64 * h + j;
-                    if (l >= g.K || (same && l < k)) continue;
-                    const double c = (double)acc[j] * inv_m;
-                    g.conn[base + (long long)k * g.K + l] = c;
-                    g.conn[base + (long long)l * g.K + k] = c;
-                    if (g.g2) {
-                        const double ol = g.mu[(long long)t * g.K + l] + 0.5;
-                        const double v = (c + ok_ * ol) / (ok_ * ol);
-                        g.g2[base + (long long)k * g.K + l] = v;
-                        g.g2[base + (long long)l * g.K + k] = v;
-                    }
-                }
-            }
-        }
+        if (ok && *abort_flag == 0) write_tile(acc, g.t0 + tl, kt, lt, g);
     }
 
     tmem_fence_before();
@@ -395,7 +441,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 }
 
 struct GramGeom {
-    int K, Kp, n_kt, n_tiles, TB;
+    int K, Kd, n_kt, n_tiles, TB;   // Kd = max(K, 128) stored site rows
     long long Mp;
     size_t mu_bytes, ops_bytes;
 };
@@ -408,10 +454,10 @@ GramGeom gram_geom(Plan *p, int64_t M, int32_t T)
     GramGeom gg;
     gg.K = 2 * p->N;
     gg.n_kt = (gg.K + kTile - 1) / kTile;
-    gg.Kp = gg.n_kt * kTile;
+    gg.Kd = std::max(gg.K, kTile);
     gg.n_tiles = gg.n_kt * (gg.n_kt + 1) / 2;
     gg.Mp = (M + kChunk - 1) / kChunk * kChunk;
-    const size_t per_t = 2 * (size_t)gg.Kp * (size_t)gg.Mp * sizeof(__nv_bfloat16);
+    const size_t per_t = 2 * (size_t)gg.Kd * (size_t)gg.Mp * sizeof(__nv_bfloat16);
     const int sm = std::max(1, p->sm_count);
     int tb = std::max(1, sm / gg.n_tiles);
     tb = (int)std::min<size_t>((size_t)tb, std::max<size_t>(1, (size_t)(2ull << 30) / per_t));
@@ -430,28 +476,9 @@ int launch_gram_bf16x3(Plan *p, const void *snap, int64_t M, int32_t T, const do
     if (p->precision != FTWA_FP32) return FTWA_ERR_UNSUPPORTED;   // the split is defined for FP32 snapshots
     if (M < 1 || T < 1) return FTWA_ERR_INVALID_ARGUMENT;
     if (M > (int64_t)0x7FFFFFFF - kChunk) return FTWA_ERR_UNSUPPORTED;   // TMA coordinates are 32-bit
-    const GramGeom gg = gram_geom(p, M, T);
-    if (p->ws_bytes < gg.mu_bytes + gg.ops_bytes) return FTWA_ERR_OUT_OF_MEMORY;   // sized by the caller
     PFN_cuTensorMapEncodeTiled_v12000 encode = encode_fn();
     if (!encode) return FTWA_ERR_UNSUPPORTED;
-    unsigned char *ws = reinterpret_cast<unsigned char *>(p->d_ws);
-    __nv_bfloat16 *hi = reinterpret_cast<__nv_bfloat16 *>(ws + gg.mu_bytes);
-    __nv_bfloat16 *lo = hi + gg.ops_bytes / (2 * sizeof(__nv_bfloat16));
-
-    CUtensorMap map_hi, map_lo;
-    const cuuint64_t dims[3] = {(cuuint64_t)gg.Mp, (cuuint64_t)gg.Kp, (cuuint64_t)gg.TB};
-    const cuuint64_t strides[2] = {(cuuint64_t)gg.Mp * 2, (cuuint64_t)gg.Kp * (cuuint64_t)gg.Mp * 2};
-    const cuuint32_t box[3] = {(cuuint32_t)kChunk, (cuuint32_t)kTile, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    for (int i = 0; i < 2; ++i) {
-        CUresult r = encode(i == 0 ? &map_hi : &map_lo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, i == 0 ? (void *)hi : (void *)lo,
-                            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return FTWA_ERR_CUDA;
-    }
-    const int smem = kStages * 4 * kImage + 1024 + (int)sizeof(GemmSmem);
-    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return set_cuda_error(e);
+    const GramGeom gg = gram_geom(p, M, T);
     GemmArgs a;
     a.mu = mu;
     a.conn = conn;
@@ -462,10 +489,31 @@ int launch_gram_bf16x3(Plan *p, const void *snap, int64_t M, int32_t T, const do
     a.n_tiles = gg.n_tiles;
     a.status = p->d_status;
     a.timeout_ns = p->timeout_ns;
+    const cuuint32_t estr[3] = {1, 1, 1};
+    cudaError_t e;
+
+    if (p->ws_bytes < gg.mu_bytes + gg.ops_bytes) return FTWA_ERR_OUT_OF_MEMORY;   // sized by the caller
+    unsigned char *ws = reinterpret_cast<unsigned char *>(p->d_ws);
+    __nv_bfloat16 *hi = reinterpret_cast<__nv_bfloat16 *>(ws + gg.mu_bytes);
+    __nv_bfloat16 *lo = hi + gg.ops_bytes / (2 * sizeof(__nv_bfloat16));
+    CUtensorMap map_hi, map_lo;
+    // rows k >= Kd of the last tile's boxes read as zeros (TMA out-of-bounds fill)
+    const cuuint64_t dims[3] = {(cuuint64_t)gg.Mp, (cuuint64_t)gg.Kd, (cuuint64_t)gg.TB};
+    const cuuint64_t strides[2] = {(cuuint64_t)gg.Mp * 2, (cuuint64_t)gg.Kd * (cuuint64_t)gg.Mp * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)kChunk, (cuuint32_t)kTile, 1};
+    for (int i = 0; i < 2; ++i) {
+        CUresult r = encode(i == 0 ? &map_hi : &map_lo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, i == 0 ? (void *)hi : (void *)lo,
+                            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return FTWA_ERR_CUDA;
+    }
+    const int smem = kStages * 4 * kImage + 1024 + (int)sizeof(GemmSmem);
+    e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return set_cuda_error(e);
     for (int t0 = 0; t0 < T; t0 += gg.TB) {
         const int tb = std::min(gg.TB, T - t0);
-        dim3 gs((unsigned)(gg.Mp / kChunk), (unsigned)(gg.Kp / kSplitRows), (unsigned)tb);
-        split_kernel<<<gs, 256, 0, s>>>(reinterpret_cast<const float *>(snap), mu, hi, lo, M, gg.K, gg.Kp, gg.Mp, t0);
+        dim3 gs((unsigned)(gg.Mp / kChunk), (unsigned)((gg.Kd + kSplitSites - 1) / kSplitSites), (unsigned)tb);
+        split_kernel<<<gs, 256, 0, s>>>(reinterpret_cast<const float *>(snap), mu, hi, lo, M, gg.K, gg.Kd, gg.Mp, t0);
         e = cudaGetLastError();
         if (e != cudaSuccess) return set_cuda_error(e);
         a.t0 = t0;
@@ -476,9 +524,10 @@ int launch_gram_bf16x3(Plan *p, const void *snap, int64_t M, int32_t T, const do
     return FTWA_OK;
 }
 
-size_t gram_bf16x3_workspace(Plan *p, int64_t M, int32_t T)
+size_t gram_bf16x3_workspace(Plan *p, const void *snap, int64_t M, int32_t T)
 {
     const GramGeom gg = gram_geom(p, M, T);
+    (void)snap;
     return gg.mu_bytes + gg.ops_bytes;
 }
 

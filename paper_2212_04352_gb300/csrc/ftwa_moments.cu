@@ -1,7 +1,7 @@
 // Sample-mean estimators of Eqs. 5 and 10 from diagonal snapshots.
 //
 //   mu[t][k]   = (1/M) sum_m X[t][m][k]                 (FP64 snapshots: double,
-//                fixed order; FP32 snapshots: 64-bit fixed point, exact to 2^-45)
+//                fixed order; FP32 snapshots: 64-bit fixed point, exact to 2^-44)
 //   occ[t][k]  = mu + 1/2                               (Eq. 5, first line)
 //   conn[t]    = (1/M) (X - mu)^T (X - mu)              (connected Gram)
 //   g2[t][k][l] = (conn_kl + occ_k occ_l) / (occ_k occ_l)   (Eq. 10: the sample
@@ -44,15 +44,33 @@ __global__ void mean_kernel(const T *__restrict__ X, long long M, int K, double 
 }
 
 // Sample sums of FP32 snapshots in 64-bit fixed point (units of 2^-44).
-// Every FP32 value with |x| < 4 is rounded once, to within 2^-45, and the
-// integer additions are exact and associative: the mean is exact to 2^-45
-// whatever the order or split of the samples, without one FP64 operation per
-// value (FP64 throughput is low on this part).  A block that meets |x| >= 4
-// or a non-finite value marks its partial; the final kernel then sums that
-// column in FP64.
+// Every FP32 value with |x| < 4 is rounded once, to within 2^-44, and the
+// integer additions are exact and associative: the mean is exact to 2^-44
+// whatever the order or split of the samples, without one FP64 operation (or
+// 64-bit conversion, which runs at FP64 rate on this part) per value.  The
+// rounding uses FP32 additions of "magic" constants 1.5 * 2^(23 - s): the
+// sum's ulp is 2^-s, so its bit pattern minus the constant's is round(x 2^s):
+//   a1 = round(x 2^20)               (x + 12, in [8, 16))
+//   r1 = x - a1 2^-20                (exact, |r1| <= 2^-21)
+//   a2 = round(r1 2^43)              (r1 + 1.5 2^-20, in [2^-20, 2^-19])
+//   x 2^44 ~ a1 2^24 + 2 a2.
+// A block that meets |x| >= 4 or a non-finite value marks its partial; the
+// final kernel then sums that column in FP64.
 constexpr int kMeanRows = 4096;                        // samples per partial
 constexpr long long kMeanBad = (long long)(1ULL << 63);   // marker: sum this column in FP64
 
+__device__ __forceinline__ void fx_split(float x, int &a1, int &a2)
+{
+    const float c1 = 12.0f, c2 = 0x1.8p-20f;
+    const float t1 = x + c1;
+    a1 = __float_as_int(t1) - __float_as_int(c1);
+    const float r1 = x - (t1 - c1);
+    const float t2 = r1 + c2;
+    a2 = __float_as_int(t2) - __float_as_int(c2);
+}
+
+// one block per (32 columns, 4096-sample chunk, time); warp w takes rows
+// w, w + 8, ...; eight rows per step in flight, summed in 32 bits per step
 __global__ void __launch_bounds__(256) mean_fx_partial_kernel(const float *__restrict__ X, long long M, int K,
                                                               long long *__restrict__ part)
 {
@@ -61,40 +79,49 @@ __global__ void __launch_bounds__(256) mean_fx_partial_kernel(const float *__res
     const int k = blockIdx.x * 32 + lane;
     __shared__ long long sp[8][32];
     __shared__ int sb[8][32];
-    long long acc = 0;
+    long long s1 = 0, s2 = 0;
     int bad = 0;
     if (k < K) {
         const long long m0 = (long long)chunk * kMeanRows;
         const long long m1 = M < m0 + kMeanRows ? M : m0 + kMeanRows;
         const float *x = X + (long long)t * M * K + k;
         long long m = m0 + w;
-        for (; m + 56 < m1; m += 64) {      // warp w: rows m0 + w + 8 i; 8 loads in flight
+        for (; m + 56 < m1; m += 64) {
             float v[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) v[j] = x[(m + 8 * j) * K];
+            int b1 = 0, b2 = 0;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 bad |= !(fabsf(v[j]) < 4.0f);
-                acc += __float2ll_rn(v[j] * 0x1p44f);
+                int a1, a2;
+                fx_split(v[j], a1, a2);
+                b1 += a1;
+                b2 += a2;
             }
+            s1 += b1;
+            s2 += b2;
         }
         for (; m < m1; m += 8) {
             const float v = x[m * K];
             bad |= !(fabsf(v) < 4.0f);
-            acc += __float2ll_rn(v * 0x1p44f);
+            int a1, a2;
+            fx_split(v, a1, a2);
+            s1 += a1;
+            s2 += a2;
         }
     }
-    sp[w][lane] = acc;
+    sp[w][lane] = s1 * (1LL << 24) + 2 * s2;
     sb[w][lane] = bad;
     __syncthreads();
     if (w == 0 && k < K) {
-        long long s = 0;
+        long long s_ = 0;
         int b = 0;
         for (int r = 0; r < 8; ++r) {
-            s += sp[r][lane];
+            s_ += sp[r][lane];
             b |= sb[r][lane];
         }
-        part[((long long)t * n_chunks + chunk) * K + k] = b ? kMeanBad : s;
+        part[((long long)t * n_chunks + chunk) * K + k] = b ? kMeanBad : s_;
     }
 }
 
@@ -183,7 +210,7 @@ __global__ void gram_fp64_kernel(const T *__restrict__ X, long long M, int K, co
 
 int launch_gram_bf16x3(Plan *p, const void *snap, int64_t M, int32_t T, const double *mu, double *conn,
                        double *g2, cudaStream_t s);
-size_t gram_bf16x3_workspace(Plan *p, int64_t M, int32_t T);
+size_t gram_bf16x3_workspace(Plan *p, const void *snap, int64_t M, int32_t T);
 
 static int ensure_workspace(Plan *p, size_t bytes)
 {
@@ -209,7 +236,7 @@ int launch_moments(Plan *p, const void *snap, int64_t M, int32_t T, double *occ,
     if (n_chunks > 65535 || T > 65535) return FTWA_ERR_UNSUPPORTED;
     size_t need = mu_bytes;
     if (p->precision == FTWA_FP32) need += sizeof(long long) * (size_t)T * n_chunks * K;
-    if (mode == FTWA_GRAM_BF16X3) need = std::max(need, gram_bf16x3_workspace(p, M, T));
+    if (mode == FTWA_GRAM_BF16X3) need = std::max(need, gram_bf16x3_workspace(p, snap, M, T));
     int rc = ensure_workspace(p, need);
     if (rc != FTWA_OK) return rc;
     double *mu = reinterpret_cast<double *>(p->d_ws);

@@ -290,15 +290,16 @@ def test_full_path_config1_against_oracle(ftwa):
 # ------------------------------------------------------------------ tensor-core Gram
 @pytest.mark.parametrize("lat_name,M,steps", [("periodic8", 1000, 50), ("hexflake54", 777, 30),
                                               ("hexflake96", 2000, 20), ("brick198", 1500, 20),
-                                              ("brick198", 300, 250)])
+                                              ("brick198", 300, 250), ("brick35", 900, 30)])
 def test_gram_bf16x3_matches_fp64(ftwa, lat_name, M, steps):
     """BF16x3 tensor-core Gram against the FP64 Gram of the same FP32
     snapshots.  Each product y_k y_l loses at most the lo*lo term (2^-16
     relative), so |C_bf16 - C_fp64| <= 3e-5 sqrt(C_kk C_ll) (+ FP32
     accumulation); ragged M, 1 to 10 output tiles, several batches of
-    output times (26 times of the 198-site case)."""
+    output times (26 times of the 198-site case), odd K (35 sites)."""
     lat = {"periodic8": W.periodic_honeycomb, "hexflake54": lambda: W.hexagonal_flake(3),
-           "hexflake96": lambda: W.hexagonal_flake(4), "brick198": W.brick_wall_flake}[lat_name]()
+           "hexflake96": lambda: W.hexagonal_flake(4), "brick198": W.brick_wall_flake,
+           "brick35": lambda: W.brick_wall_flake(5, 7)}[lat_name]()
     nu, nd = W.neel_state(lat)
     with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=1, out_every=10) as P:
         rho = P.sample(3, M)

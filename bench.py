@@ -36,6 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "fTWA sample-RK4-steps/s at 198 sites, FP32 vs FP64 GPU at stated error; adjoint time"
 UNIT = "sample-RK4-steps/s"
 FLOP_PER_ELEMENT_STEP = 152          # 4 stages x (2x(3+3) hopping FMAs + U term + i) + RK4 combine
+SMEM_BYTES_PER_ELEMENT_STEP = 256    # 4 stages x (7 complex FP32 reads + 1 write) of the stage state
 
 
 def workload(M=16384, steps=1000, every=10, U=1.6):
@@ -128,7 +129,7 @@ def max_over_ranks(x, ws):
 
 def traffic_record(kernel_src):
     """ncu DRAM bytes per launch recorded for this kernel source (or None)."""
-    path = os.path.join(ROOT, "profiles", "rk4_stepper_fp32_198_traffic.txt")
+    path = os.path.join(ROOT, "profiles", "band_stepper_fp32_198_traffic.txt")
     if not os.path.exists(path):
         return None
     kv = {}
@@ -485,9 +486,17 @@ def run_gpu(args):
     flops = FLOP_PER_ELEMENT_STEP * N * (N + 1) * M * steps
     achieved = flops / (evolve_ms / 1000.0) / 1e12
     traffic = traffic_record(os.path.join(ROOT, "paper_2212_04352_gb300", "csrc", "ftwa_evolve.cu"))
+    # the shared-memory bound: 7 complex reads + 1 write per element and
+    # stage (64 B in FP32) at 128 B per clock and SM
+    smem_bytes = SMEM_BYTES_PER_ELEMENT_STEP * N * (N + 1) * M * steps
+    smem_peak = sm_count * 128 * sm_mhz * 1e6 / 1e12                # TB/s
+    smem_achieved = smem_bytes / (evolve_ms / 1000.0) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-            "traffic": traffic, "kernel": "rk4_stepper<float>",
-            "peak_source": f"FP32 FMA: {sm_count} SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (max SM clock, MEASURED_PEAKS.json)"}
+            "traffic": traffic, "kernel": "band_stepper<float>",
+            "peak_source": f"FP32 FMA: {sm_count} SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (max SM clock, MEASURED_PEAKS.json)",
+            "smem": {"achieved": smem_achieved, "peak": smem_peak, "unit": "TB/s", "frac": smem_achieved / smem_peak,
+                     "bytes_per_element_step": SMEM_BYTES_PER_ELEMENT_STEP,
+                     "peak_source": f"{sm_count} SMs x 128 B/clock x {sm_mhz:.0f} MHz"}}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -42,13 +42,20 @@ template <typename T> struct C2T;
 template <> struct C2T<float> { using type = float2; };
 template <> struct C2T<double> { using type = double2; };
 
-constexpr int kThreadsA = 512;
+// Four samples per SM at a time (256 threads each): the per-sample work is a
+// sequence of dependent passes whose neighbour gathers read L2; independent
+// samples hide its latency.  (Staging each evaluation's input in shared
+// memory, one sample per SM, measured slower: 2.0 s against 1.7 s for 608
+// FP32 samples of the 96-site flake.)
+constexpr int kThreadsA = 256;
+constexpr int kCtasPerSm = 4;
 
 template <typename T>
 struct AdjArgs {
     int N, B, NE;                 // sites, bonds, packed elements (both spins)
     const int32_t *nbr;           // [N] packed slots
     const int32_t *nbr_bond;      // [N][3] bond of each slot (-1 if none)
+    const int32_t *bonds;         // [B][2] bond endpoints
     const T *tnb;                 // [N][4]
     const double *nocc;           // [2][N] initial occupations
     T U, dt;
@@ -109,6 +116,7 @@ struct Smem {
     uint32_t *elem;     // [NE]: a | b << 8 | s << 16
     int32_t *nbr;       // [N]
     int32_t *bond;      // [N][3]
+    int32_t *bxy;       // [B][2]
     double *cdiag;      // [2][N] diagonal coupling accumulator
     double *gt;         // [B]
     double *gn;         // [2][N]
@@ -149,44 +157,46 @@ __device__ void f_eval(const AdjArgs<T> &a, const Smem &sm, const typename C2T<T
     }
 }
 
-// w = VJP_f(Y)[v]; accumulates dL/dU (register), dL/dt_b and the diagonal
-// coupling (shared memory).  The coupling is added to w after a barrier.
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// w = VJP_f(Y)[v]; accumulates dL/dU (register) and dL/dt_b (shared memory).
+//  - elementwise: w = -f_D(v) with D from Y, and the U gradient;
+//  - the U term's coupling to the other spin's diagonal,
+//      c_k = -2U sum_j Im(conj(v_kj) Y_kj)   (full row k), one warp per row;
+//  - the hopping gradient of bond b = (x, y): with Hermitian v and Y,
+//      <v, d f / d t_b> = -2 Im[(v Y)_xy + (v Y)_yx]   (per spin),
+//    dot products over the full rows/columns, one warp per bond.
+// Every shared-memory sum has one writer: no atomics.
 template <typename T>
 __device__ void vjp(const AdjArgs<T> &a, const Smem &sm, const typename C2T<T>::type *Y,
                     const typename C2T<T>::type *v, typename C2T<T>::type *w, double &gU)
 {
     using V = typename C2T<T>::type;
     const int N = a.N;
-    for (int e = threadIdx.x; e < 2 * N; e += blockDim.x) sm.cdiag[e] = 0.0;
-    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
     for (int e = threadIdx.x; e < a.NE; e += blockDim.x) {
         const uint32_t d = sm.elem[e];
         const int i = d & 0xFF, j = (d >> 8) & 0xFF, s = d >> 16;
         const int nj = sm.nbr[j], ni = sm.nbr[i];
-        const double wgt = i == j ? 1.0 : 2.0;
         const V vo = v[e], yo = Y[e];
         T hr = T(0), hi = T(0);
-        // row part: neighbours k of j, bond (j, k)
+        // row part: neighbours k of j
         for (int n = 0; n < ((nj >> 24) & 0xFF); ++n) {
-            const int k = (nj >> (8 * n)) & 0xFF;
+            const V vk = getc(v, N, s, i, (nj >> (8 * n)) & 0xFF);
             const T t = a.tnb[4 * j + n];
-            const V vk = getc(v, N, s, i, k), yk = getc(Y, N, s, i, k);
             hr = fma(t, vk.x, hr);
             hi = fma(t, vk.y, hi);
-            // -Im(conj(v_ij) Y_ik)
-            const double im = (double)vo.x * yk.y - (double)vo.y * yk.x;
-            atomicAdd(&sm.gt[sm.bond[3 * j + n]], -wgt * im);
         }
-        // column part: neighbours k of i, bond (i, k)
+        // column part: neighbours k of i
         for (int n = 0; n < ((ni >> 24) & 0xFF); ++n) {
-            const int k = (ni >> (8 * n)) & 0xFF;
+            const V vk = getc(v, N, s, (ni >> (8 * n)) & 0xFF, j);
             const T t = a.tnb[4 * i + n];
-            const V vk = getc(v, N, s, k, j), yk = getc(Y, N, s, k, j);
             hr = fma(-t, vk.x, hr);
             hi = fma(-t, vk.y, hi);
-            // +Im(conj(v_ij) Y_kj)
-            const double im = (double)vo.x * yk.y - (double)vo.y * yk.x;
-            atomicAdd(&sm.gt[sm.bond[3 * i + n]], wgt * im);
         }
         const T di = Y[pidx(N, 1 - s, i, i)].x, dj = Y[pidx(N, 1 - s, j, j)].x;
         const T g = a.U * (di - dj);
@@ -198,12 +208,33 @@ __device__ void vjp(const AdjArgs<T> &a, const Smem &sm, const typename C2T<T>::
         o.y = (i == j) ? T(0) : -hr;
         w[e] = o;
         if (i != j) {
-            // P = Im(conj(v_ij) Y_ij)
-            const double P = (double)vo.x * yo.y - (double)vo.y * yo.x;
-            gU += wgt * (double)(di - dj) * (-P);
-            atomicAdd(&sm.cdiag[s * N + i], -2.0 * (double)a.U * P);
-            atomicAdd(&sm.cdiag[s * N + j], 2.0 * (double)a.U * P);
+            // weight 2: the stored (i, j) stands for (i, j) and (j, i)
+            const double P = (double)vo.x * yo.y - (double)vo.y * yo.x;   // Im(conj(v_ij) Y_ij)
+            gU += 2.0 * (double)(di - dj) * (-P);
         }
+    }
+    for (int r = warp; r < 2 * N; r += n_warps) {
+        const int s = r / N, k = r % N;
+        double acc = 0.0;
+        for (int j = lane; j < N; j += 32) {
+            const V vk = getc(v, N, s, k, j), yk = getc(Y, N, s, k, j);
+            acc += (double)vk.x * yk.y - (double)vk.y * yk.x;
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) sm.cdiag[r] = -2.0 * (double)a.U * acc;
+    }
+    for (int b = warp; b < a.B; b += n_warps) {
+        const int x = sm.bxy[2 * b], y = sm.bxy[2 * b + 1];
+        double acc = 0.0;
+        for (int s = 0; s < 2; ++s)
+            for (int i = lane; i < N; i += 32) {
+                // Im(v_xi Y_iy) + Im(v_yi Y_ix)
+                const V v1 = getc(v, N, s, x, i), y1 = getc(Y, N, s, i, y);
+                const V v2 = getc(v, N, s, y, i), y2 = getc(Y, N, s, i, x);
+                acc += (double)v1.x * y1.y + (double)v1.y * y1.x + (double)v2.x * y2.y + (double)v2.y * y2.x;
+            }
+        acc = warp_sum(acc);
+        if (lane == 0) sm.gt[b] += -2.0 * acc;
     }
     __syncthreads();
     // coupling to the other spin's diagonal
@@ -270,7 +301,7 @@ __device__ void rk4(const AdjArgs<T> &a, const Smem &sm, const typename C2T<T>::
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreadsA, 1) adjoint_kernel(const AdjArgs<T> a)
+__global__ void __launch_bounds__(kThreadsA, kCtasPerSm) adjoint_kernel(const AdjArgs<T> a)
 {
     using V = typename C2T<T>::type;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -287,13 +318,19 @@ __global__ void __launch_bounds__(kThreadsA, 1) adjoint_kernel(const AdjArgs<T> 
     p += sizeof(int32_t) * N;
     sm.bond = reinterpret_cast<int32_t *>(p);
     p += sizeof(int32_t) * 3 * N;
+    sm.bxy = reinterpret_cast<int32_t *>(p);
+    p += sizeof(int32_t) * 2 * std::max(a.B, 1);
     sm.elem = reinterpret_cast<uint32_t *>(p);
 
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         sm.nbr[i] = a.nbr[i];
         for (int n = 0; n < 3; ++n) sm.bond[3 * i + n] = a.nbr_bond[3 * i + n];
     }
-    for (int i = threadIdx.x; i < a.B; i += blockDim.x) sm.gt[i] = 0.0;
+    for (int i = threadIdx.x; i < a.B; i += blockDim.x) {
+        sm.gt[i] = 0.0;
+        sm.bxy[2 * i] = a.bonds[2 * i];
+        sm.bxy[2 * i + 1] = a.bonds[2 * i + 1];
+    }
     for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) sm.gn[i] = 0.0;
     for (int s = 0; s < 2; ++s)
         for (int i = 0; i < N; ++i)
@@ -471,7 +508,9 @@ static int launch_adjoint_t(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, 
     const int NE = N * (N + 1);
     const int n_seg = (int)(n_steps / ckpt_every);
     const long long stride = (long long)(n_seg + ckpt_every + 1 + 12) * NE;
-    const int grid = (int)std::min<long long>(M, std::max(1, p->sm_count));
+    const int smem_tables = (int)(sizeof(double) * (4 * N + std::max(p->B, 1)) + sizeof(int32_t) * 4 * N +
+                                  sizeof(int32_t) * 2 * std::max(p->B, 1) + sizeof(uint32_t) * NE + 64);
+    const int grid = (int)std::min<long long>(M, (long long)kCtasPerSm * std::max(1, p->sm_count));
     const size_t bytes = sizeof(V) * (size_t)stride * grid;
     if (p->adj_ws_bytes < bytes) {
         cudaFree(p->d_adj_ws);
@@ -491,6 +530,7 @@ static int launch_adjoint_t(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, 
     a.NE = NE;
     a.nbr = p->d_nbr;
     a.nbr_bond = p->d_nbr_bond;
+    a.bonds = p->d_bonds;
     a.tnb = std::is_same<T, double>::value ? reinterpret_cast<const T *>(p->d_t64)
                                            : reinterpret_cast<const T *>(p->d_t32);
     a.nocc = p->d_n;
@@ -508,8 +548,7 @@ static int launch_adjoint_t(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, 
     a.ws = reinterpret_cast<V *>(p->d_adj_ws);
     a.ws_stride = stride;
     a.status = p->d_status;
-    const int smem = (int)(sizeof(double) * (4 * N + std::max(p->B, 1)) + sizeof(int32_t) * 4 * N +
-                           sizeof(uint32_t) * NE + 64);
+    const int smem = smem_tables;
     if (smem > 227 * 1024) return FTWA_ERR_UNSUPPORTED;
     cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return set_cuda_error(e);

@@ -85,3 +85,38 @@ def test_adjoint_checkpoint_invariance(ftwa):
     for o in out[1:]:
         for a, b in zip(o, out[0]):
             np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-14)
+
+
+def test_adjoint_96_sites_fp64_spot_check(ftwa):
+    """96-site flake (the adjoint workload's lattice) in FP64: dL/dU, three
+    bond gradients and two occupation gradients against central differences
+    of the oracle."""
+    lat = W.hexagonal_flake(4)
+    n0u, n0d = W.neel_state(lat)
+    nu, nd = W.softened(n0u), W.softened(n0d)
+    U, seed, M, steps, every, ckpt = 1.6, 7, 2, 20, 10, 10
+    rng = np.random.default_rng(1)
+    target = 0.5 + 0.1 * rng.standard_normal((steps // every + 1, 2 * lat.n_sites))
+    tb = np.array(lat.t_bond, dtype=np.float64)
+    L0, occ = _loss(lat, U, nu, nd, seed, M, steps, every, target, tb)
+    g = torch.from_numpy(2.0 * (occ - target)).cuda()
+    with ftwa.Plan(lat, U, n_up=nu, n_dn=nd, precision=0, out_every=every) as P:
+        gU, gt, gn = P.adjoint(seed, M, steps, ckpt, g)
+        assert P.status() == 0
+    gU, gt, gn = gU.item(), gt.cpu().numpy(), gn.cpu().numpy()
+    h = 1e-5
+    def fd(fn):
+        return (fn(h) - fn(-h)) / (2 * h)
+    checks = [(gU, fd(lambda d: _loss(lat, U + d, nu, nd, seed, M, steps, every, target, tb)[0]))]
+    for b in (0, 57, lat.n_bonds - 1):
+        checks.append((gt[b], fd(lambda d, b=b: _loss(lat, U, nu, nd, seed, M, steps, every, target,
+                                                      tb + d * (np.arange(lat.n_bonds) == b))[0])))
+    for s, i in ((0, 3), (1, 90)):
+        def Ln(d, s=s, i=i):
+            a, b = nu.copy(), nd.copy()
+            (a if s == 0 else b)[i] += d
+            return _loss(lat, U, a, b, seed, M, steps, every, target, tb)[0]
+        checks.append((gn[s, i], fd(Ln)))
+    scale = max(abs(f) for _, f in checks)
+    for got, want in checks:
+        assert abs(got - want) <= 1e-6 * scale, (got, want)

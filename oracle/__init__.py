@@ -109,6 +109,16 @@ def sample(N, n_up, n_dn, seed, m):
     return out
 
 
+def sample_general(N, lam, V, seed, m):
+    """One initial sample of a general state n_s = V_s diag(lam_s) V_s^dagger
+    (App. A covariance, Eq. 7 in the diagonalising basis): rho~ drawn by Eq. 7
+    with the eigen-occupations lam (same counters as :func:`sample`), then
+    rho_s = V_s rho~_s V_s^dagger.  lam [2, N], V [2, N, N]; shape [2, N, N]."""
+    rt = sample(N, lam[0], lam[1], seed, m)
+    V = np.asarray(V, dtype=np.complex128)
+    return np.stack([V[s] @ rt[s] @ V[s].conj().T for s in range(2)])
+
+
 def rhs(lat, U, rho, t_bond=None):
     """Right-hand side of Eq. 6 for a state [2, N, N]."""
     lib = _load()

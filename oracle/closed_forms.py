@@ -91,3 +91,22 @@ def rho11_taylor(eps, j1, xi1, U):
     eta1 = math.sqrt(2) * np.real(xi1)
     eta2 = math.sqrt(2) * np.imag(xi1)
     return 0.5 - np.sum(j1 * eta2) * eps - np.sum(j1 ** 2) * eps ** 2 + U / 2 * np.sum(j1 * eta1) * eps ** 2
+
+
+def general_state_covariance(lam, V, idx):
+    """cov(rho*_ab, rho_mn) of the Gaussian Wigner density of a one-body state
+    n = V diag(lam) V^dagger (one spin), App. A:
+        1/2 (nt_ma n_bn + nt_bn n_ma),   nt = 1 - n,
+    minus the part carried by the eigen-diagonal, sum_k conj(V_ak) V_bk V_mk
+    conj(V_nk) lam_k (1 - lam_k), which Eq. 7 (applied in the diagonalising
+    basis) leaves without noise.  idx: list of (a, b, m, n)."""
+    lam = np.asarray(lam, dtype=np.float64)
+    V = np.asarray(V, dtype=np.complex128)
+    n = (V * lam[None, :]) @ V.conj().T
+    nt = np.eye(len(lam)) - n
+    out = []
+    for a, b, m, k in idx:
+        full = 0.5 * (nt[m, a] * n[b, k] + nt[b, k] * n[m, a])
+        diag = np.sum(V[a].conj() * V[b] * V[m] * V[k].conj() * lam * (1 - lam))
+        out.append(full - diag)
+    return np.array(out)

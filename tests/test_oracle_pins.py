@@ -284,3 +284,40 @@ def test_fd_gradient_converges():
     g1 = oracle.fd_gradient(lat, 1.6, nu, nd, 3, 8, 0.01, 40, 20, tgt, [("U",), ("t", 0)], h=1e-3)
     g2 = oracle.fd_gradient(lat, 1.6, nu, nd, 3, 8, 0.01, 40, 20, tgt, [("U",), ("t", 0)], h=5e-4)
     assert np.all(np.abs(g1 - g2) <= 1e-5 * np.maximum(1, np.abs(g2)))
+
+
+# ---- general (non-diagonal) initial states ---------------------------------------
+def test_general_sampler_identity_basis_is_eq7():
+    """With V = 1 the general sampler is the diagonal sampler of Eq. 7."""
+    lat = W.hexagon_chain(2)
+    nu, nd = W.softened(W.neel_state(lat)[0]), W.softened(W.neel_state(lat)[1])
+    V = np.stack([np.eye(lat.n_sites), np.eye(lat.n_sites)]).astype(np.complex128)
+    for m in range(3):
+        a = oracle.sample_general(lat.n_sites, np.stack([nu, nd]), V, 11, m)
+        b = oracle.sample(lat.n_sites, nu, nd, 11, m)
+        assert np.array_equal(a, b)
+
+
+def test_general_sampler_moments_match_app_a_covariance():
+    """Statistics of the general sampler (random complex basis, fractional
+    eigen-occupations, 40000 samples): the mean is n - 1/2 and
+    cov(rho*_ab, rho_mn) is the covariance of App. A minus the eigen-diagonal
+    part that Eq. 7 leaves noiseless (|z| < 5); the trace and Hermiticity
+    hold per sample."""
+    N, K = 4, 40000
+    lam, V = W.random_basis(N, 3, [0.1, 0.6, 0.9, 0.3], [0.2, 0.5, 0.7, 1.0])
+    X = np.stack([oracle.sample_general(N, lam, V, 7, m) for m in range(K)])
+    for s in range(2):
+        assert np.abs(np.trace(X[:, s], axis1=1, axis2=2) - (lam[s].sum() - N / 2)).max() < 1e-12
+        assert np.abs(X[:, s] - np.conj(np.transpose(X[:, s], (0, 2, 1)))).max() < 1e-14
+        n = (V[s] * lam[s][None, :]) @ V[s].conj().T
+        mean = X[:, s].mean(axis=0)
+        se = np.maximum(X[:, s].std(axis=0) / np.sqrt(K), 1e-12)
+        assert (np.abs(mean - (n - 0.5 * np.eye(N))) / se).max() < 5
+        idx = [(0, 1, 0, 1), (0, 1, 2, 3), (1, 1, 2, 2), (0, 2, 0, 2), (3, 0, 1, 2), (2, 2, 2, 2), (0, 0, 1, 1)]
+        want = cf.general_state_covariance(lam[s], V[s], idx)
+        D = X[:, s] - mean
+        for (a, b, m, k), w in zip(idx, want):
+            prod = np.conj(D[:, a, b]) * D[:, m, k]
+            sd = np.sqrt(np.var(prod.real) + np.var(prod.imag)) / np.sqrt(K)
+            assert abs(prod.mean() - w) < 5 * sd + 1e-12

@@ -26,4 +26,6 @@ from .states import (  # noqa: F401
     neel_state,
     charge_imbalanced_state,
     softened,
+    thermal_basis,
+    random_basis,
 )

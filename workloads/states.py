@@ -71,3 +71,33 @@ def softened(n, eps: float = 0.05):
     """Map Fock occupations {0, 1} to {eps, 1 - eps} (smooth sampler map)."""
     n = np.asarray(n, dtype=np.float64)
     return eps + (1.0 - 2.0 * eps) * n
+
+
+# ---- general (non-diagonal) initial states, given in a diagonalising basis ----
+# A one-body state n_s = V_s diag(lam_s) V_s^dagger per spin is described by
+# (lam [2, N], V [2, N, N], columns of V_s = eigenvectors).  These helpers only
+# build such inputs (eigen-decompositions with numpy's LAPACK routines).
+
+def thermal_basis(lat: Lattice, beta: float, mu: float = 0.0):
+    """Grand-canonical thermal state of the hopping Hamiltonian h = -J of
+    Eq. 1 (U = 0) at inverse temperature beta and chemical potential mu,
+    both spins: lam_k = 1 / (exp(beta (eps_k - mu)) + 1), V = eigenvectors."""
+    J = np.zeros((lat.n_sites, lat.n_sites))
+    for (i, j), t in zip(lat.bonds, lat.t_bond):
+        J[i, j] = J[j, i] = t
+    eps, V = np.linalg.eigh(-J)
+    lam = 1.0 / (np.exp(np.clip(beta * (eps - mu), -700, 700)) + 1.0)
+    return np.stack([lam, lam]), np.stack([V, V]).astype(np.complex128)
+
+
+def random_basis(n_sites: int, seed: int, lam_up, lam_dn):
+    """Seeded Haar-like random unitary bases (QR of a complex Gaussian matrix,
+    phases fixed by the diagonal of R) with the given eigen-occupations."""
+    rng = np.random.default_rng(seed)
+    Vs = []
+    for _ in range(2):
+        z = rng.standard_normal((n_sites, n_sites)) + 1j * rng.standard_normal((n_sites, n_sites))
+        q, r = np.linalg.qr(z)
+        d = np.diag(r)
+        Vs.append(q * (d / np.abs(d))[None, :])
+    return np.stack([np.asarray(lam_up, dtype=np.float64), np.asarray(lam_dn, dtype=np.float64)]), np.stack(Vs)

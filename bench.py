@@ -252,6 +252,43 @@ def bench_adjoint(F, args):
     return out
 
 
+def bench_general(F, args):
+    """General initial state (Sec. 8(f) first extension): the 198-site flake in
+    the thermal state of its hopping Hamiltonian (beta = 2, mu = 0.3), FP32,
+    M samples: ftwa_sample = Eq. 7 in the eigenbasis + rho = V rho~ V^dagger
+    (two complex N^3 products per sample and spin on the CUDA cores)."""
+    import torch
+    import workloads as W
+    M = args.general_samples
+    lat = W.brick_wall_flake(11, 18)
+    nu, nd = W.neel_state(lat)
+    lam, V = W.thermal_basis(lat, beta=2.0, mu=0.3)
+    P = F.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=F.FTWA_FP32)
+    P.set_initial_basis(lam, V)
+    rho = P.new_state(M)
+    P.sample(1, M, out=rho)
+    torch.cuda.synchronize()
+    a, b = _events()
+    a.record()
+    P.sample(2, M, out=rho)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    if P.status() != 0:
+        raise RuntimeError("general sampling device status")
+    N = lat.n_sites
+    flops = 2 * 8.0 * N ** 3 * 2 * M
+    pk = peaks()
+    sm_count = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    fp32_peak = sm_count * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    P.close()
+    del rho
+    torch.cuda.empty_cache()
+    return {"workload": f"198-site flake, thermal state of -J (beta=2, mu=0.3), FP32, M={M}",
+            "ms": ms, "samples_per_s": M / (ms / 1000), "rotation_tflops": flops / (ms / 1000) / 1e12,
+            "rotation_frac_of_fp32_peak": flops / (ms / 1000) / 1e12 / fp32_peak}
+
+
 def bench_batched(F, args):
     """Config 3: honeycomb flakes of 24, 54, 96, 150 and 198 sites x U/t in
     {0.5, 1.0, 1.6, 2.5}, M samples each, FP32 state, one CUDA-graph launch
@@ -477,6 +514,8 @@ def run_gpu(args):
         extra["batched"] = bench_batched(F, args)
     if not args.no_gram:
         extra["gram"] = bench_gram(F, args)
+    if not args.no_general:
+        extra["general_state"] = bench_general(F, args)
 
     # ---- roofline of the dominant kernel (the RK4 stepper) -----------------------
     pk = peaks()
@@ -574,6 +613,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-gram", action="store_true")
+    ap.add_argument("--no-general", action="store_true")
+    ap.add_argument("--general-samples", type=int, default=4096)
     ap.add_argument("--adjoint-samples", type=int, default=4096)
     ap.add_argument("--batch-samples", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=100)

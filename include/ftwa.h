@@ -149,6 +149,22 @@ int ftwa_get_info(const ftwa_plan_t *plan, ftwa_plan_info *info);
 int ftwa_sample(ftwa_plan_t *plan, uint64_t seed, int64_t first_sample, int64_t M,
                 void *rho_dev, void *stream);
 
+/* General (non-diagonal) initial state, App. A (the covariance of the
+ * Gaussian Wigner density) with Eq. 7 applied in a diagonalising basis: the
+ * one-body density matrix of spin s is n_s = V_s diag(lambda_s) V_s^dagger
+ * with n_s,ij = <c^dagger_i c_j>.  Host arrays: lambda[2][N] eigen-occupations
+ * in [0, 1]; v_re, v_im [2][N][N] row-major, column k of V_s the eigenvector
+ * of lambda_s,k (v_im may be NULL for a real basis).  After this call
+ * ftwa_sample draws rho~ by Eq. 7 with lambda (same Philox counters) and
+ * writes rho = V rho~ V^dagger (mean n - 1/2); the rotation runs on the
+ * device in the plan's precision and keeps a workspace of at most 256 MB.
+ * lambda == NULL returns the plan to its diagonal initial state.  The plan
+ * copies the arrays.  ftwa_adjoint is not available while a basis is set.
+ * Errors: FTWA_ERR_INVALID_ARGUMENT (null plan or v_re, lambda outside
+ * [0, 1], non-finite entries, V not unitary to 1e-10), FTWA_ERR_CUDA,
+ * FTWA_ERR_OUT_OF_MEMORY. */
+int ftwa_set_initial_basis(ftwa_plan_t *plan, const double *lambda, const double *v_re, const double *v_im);
+
 /* Raw Philox4x32-10 words for counters (m_lo, m_hi, spin, p0 + q),
  * q = 0 .. count-1, key (seed_lo, seed_hi): out_dev[q][4] uint32.  Exposes
  * the integer stage of ftwa_sample for bit-exact checks. */
@@ -205,7 +221,8 @@ int ftwa_moments(ftwa_plan_t *plan, const void *snap_dev, int64_t M, int32_t n_t
  * out_every.  The plan keeps a per-CTA workspace (checkpoints, one replayed
  * segment, stage states; grown on demand).  Errors:
  * FTWA_ERR_INVALID_ARGUMENT, FTWA_ERR_UNSUPPORTED (lattice too large for
- * the per-sample tables), FTWA_ERR_OUT_OF_MEMORY, FTWA_ERR_CUDA. */
+ * the per-sample tables, or a general initial basis is set),
+ * FTWA_ERR_OUT_OF_MEMORY, FTWA_ERR_CUDA. */
 int ftwa_adjoint(ftwa_plan_t *plan, uint64_t seed, int64_t M, int64_t n_steps, int32_t ckpt_every,
                  const double *dL_docc_dev, double *grad_U_dev, double *grad_t_dev,
                  double *grad_n0_dev, void *stream);

@@ -112,6 +112,22 @@ class Plan:
               "ftwa_sample")
         return rho
 
+    def set_initial_basis(self, lam, V):
+        """General initial state n_s = V_s diag(lam_s) V_s^dagger (lam [2, N] in
+        [0, 1], V [2, N, N] unitary, columns = eigenvectors); None, None returns
+        to the diagonal state of the plan's occupations."""
+        import numpy as np
+        if lam is None:
+            check(load().ftwa_set_initial_basis(self._h, None, None, None), "ftwa_set_initial_basis")
+            return
+        lam = np.ascontiguousarray(lam, dtype=np.float64).reshape(2, self.N)
+        V = np.asarray(V).reshape(2, self.N, self.N)
+        vr = np.ascontiguousarray(V.real, dtype=np.float64)
+        vi = np.ascontiguousarray(V.imag, dtype=np.float64) if np.iscomplexobj(V) else None
+        check(load().ftwa_set_initial_basis(self._h, ctypes.c_void_p(lam.ctypes.data), ctypes.c_void_p(vr.ctypes.data),
+                                            None if vi is None else ctypes.c_void_p(vi.ctypes.data)),
+              "ftwa_set_initial_basis")
+
     def evolve(self, rho, n_steps, snap=True, stream=None):
         """Advance rho in place; returns snapshots [n_out, M, 2N] (or None)."""
         import torch

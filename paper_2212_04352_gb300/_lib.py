@@ -23,7 +23,8 @@ FTWA_MAX_SITES = 256
 FTWA_MOMENTS_NOALLOC_MAX_TK = 131072
 
 # every symbol include/ftwa.h declares
-EXPORTS = ("ftwa_plan", "ftwa_destroy", "ftwa_get_info", "ftwa_sample", "ftwa_philox", "ftwa_evolve",
+EXPORTS = ("ftwa_plan", "ftwa_destroy", "ftwa_get_info", "ftwa_sample", "ftwa_set_initial_basis", "ftwa_philox",
+           "ftwa_evolve",
            "ftwa_moments", "ftwa_moments_noalloc", "ftwa_adjoint", "ftwa_autotune", "ftwa_batch_create",
            "ftwa_batch_launch", "ftwa_batch_destroy", "ftwa_status", "ftwa_debug_force_timeout", "ftwa_error_string",
            "ftwa_version")
@@ -75,6 +76,7 @@ def load(path: str = LIB_PATH):
     lib.ftwa_destroy.restype = None
     lib.ftwa_get_info.argtypes = [P, ctypes.POINTER(PlanInfo)]
     lib.ftwa_sample.argtypes = [P, u64, i64, i64, P, P]
+    lib.ftwa_set_initial_basis.argtypes = [P, P, P, P]
     lib.ftwa_philox.argtypes = [u64, i64, i32, i64, i64, P, P]
     lib.ftwa_evolve.argtypes = [P, P, i64, i64, P, P]
     lib.ftwa_moments.argtypes = [P, P, i64, i32, P, P, P, i32, P]

@@ -559,6 +559,9 @@ static int launch_adjoint_t(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, 
 int launch_adjoint(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, int32_t ckpt_every, const double *dL,
                    double *gU, double *gt, double *gn, cudaStream_t s)
 {
+    // the samples of a general initial state depend on the eigenbasis, whose
+    // derivatives the adjoint does not carry
+    if (p->general_basis) return FTWA_ERR_UNSUPPORTED;
     if (p->precision == FTWA_FP64) return launch_adjoint_t<double>(p, seed, M, n_steps, ckpt_every, dL, gU, gt, gn, s);
     return launch_adjoint_t<float>(p, seed, M, n_steps, ckpt_every, dL, gU, gt, gn, s);
 }

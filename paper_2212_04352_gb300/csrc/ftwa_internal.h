@@ -74,12 +74,22 @@ struct Plan {
     int variant_override = 0;         // 0 auto, 1 banded only, 2 general only
     size_t ws_bytes = 0;
     StepperShape shape;               // chosen for the full machine
+    // general (non-diagonal) initial state n = V diag(lambda) V^dagger per spin
+    bool general_basis = false;
+    double *d_lam = nullptr;          // [2][N] eigen-occupations lambda
+    void *d_V = nullptr;              // [2][N][N] complex eigenvectors (columns), plan precision
+    void *d_rot_ws = nullptr;         // rotation workspace (chunk of samples)
+    size_t rot_ws_bytes = 0;
 };
 
 int set_cuda_error(cudaError_t e);
 
 // per-translation-unit launchers
 int launch_sample(Plan *p, uint64_t seed, int64_t first, int64_t M, void *rho, cudaStream_t s);
+int launch_sample_diag(Plan *p, const double *occ, uint64_t seed, int64_t first, int64_t M, void *rho,
+                       cudaStream_t s);
+int launch_rotate(Plan *p, void *rho, int64_t M, cudaStream_t s);
+void free_basis(Plan *p);
 int launch_philox(uint64_t seed, int64_t m, int32_t spin, int64_t p0, int64_t count, uint32_t *out,
                   cudaStream_t s);
 int launch_evolve(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s);

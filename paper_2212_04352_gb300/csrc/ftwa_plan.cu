@@ -31,6 +31,7 @@ static void free_tables(Plan *p)
     cudaFree(p->d_ws);
     cudaFree(p->d_items);
     cudaFree(p->d_adj_ws);
+    free_basis(p);
     p->d_adj_ws = nullptr;
     p->adj_ws_bytes = 0;
     p->d_items = nullptr;

@@ -109,17 +109,29 @@ static int grid_for(long long total)
     return (int)(g < 1 ? 1 : (g > 65535LL * 8 ? 65535LL * 8 : g));
 }
 
-int launch_sample(Plan *p, uint64_t seed, int64_t first, int64_t M, void *rho, cudaStream_t s)
+int launch_sample_diag(Plan *p, const double *occ, uint64_t seed, int64_t first, int64_t M, void *rho,
+                       cudaStream_t s)
 {
     if (M == 0) return FTWA_OK;
     const long long total = M * 2LL * p->N * p->N;
     if (p->precision == FTWA_FP64)
-        sample_kernel<double, double2><<<grid_for(total), 256, 0, s>>>(p->d_n, p->N, seed, first, M,
+        sample_kernel<double, double2><<<grid_for(total), 256, 0, s>>>(occ, p->N, seed, first, M,
                                                                       reinterpret_cast<double2 *>(rho));
     else
-        sample_kernel<float, float2><<<grid_for(total), 256, 0, s>>>(p->d_n, p->N, seed, first, M,
+        sample_kernel<float, float2><<<grid_for(total), 256, 0, s>>>(occ, p->N, seed, first, M,
                                                                     reinterpret_cast<float2 *>(rho));
     return set_cuda_error(cudaGetLastError());
+}
+
+// Diagonal initial state: Eq. 7 with the site occupations.  General state
+// n = V diag(lambda) V^dagger: Eq. 7 with the eigen-occupations lambda in the
+// diagonalising basis, then rho = V rho~ V^dagger (ftwa_basis.cu).
+int launch_sample(Plan *p, uint64_t seed, int64_t first, int64_t M, void *rho, cudaStream_t s)
+{
+    if (!p->general_basis) return launch_sample_diag(p, p->d_n, seed, first, M, rho, s);
+    const int rc = launch_sample_diag(p, p->d_lam, seed, first, M, rho, s);
+    if (rc != FTWA_OK) return rc;
+    return launch_rotate(p, rho, M, s);
 }
 
 int launch_philox(uint64_t seed, int64_t m, int32_t spin, int64_t p0, int64_t count, uint32_t *out, cudaStream_t s)

@@ -202,6 +202,34 @@ static void rhs(const adjacency *a, double U, const cplx *rho, cplx *f)
     }
 }
 
+/* Time-dependent on-site potential (the time-dependent Hamiltonians of
+ * Sec. III, written as h_ii(t) += v_i,s(t)): v_i,s(t) = amp[s][i] f(t) with
+ * the pulse f(t) = exp(-(t - t0)^2 / (2 sigma^2)) cos(omega (t - t0) + phase)
+ * (sigma <= 0: no envelope).  It adds i (v_i,s - v_j,s) rho_ij,s to Eq. 6,
+ * the same form as the U term. */
+typedef struct {
+    const double *amp;   /* [2][N] or NULL */
+    double t0, sigma, omega, phase;
+} drive;
+
+static double drive_f(const drive *d, double t)
+{
+    const double env = d->sigma > 0.0 ? exp(-(t - d->t0) * (t - d->t0) / (2.0 * d->sigma * d->sigma)) : 1.0;
+    return env * cos(d->omega * (t - d->t0) + d->phase);
+}
+
+static void add_drive(int N, const drive *d, double t, const cplx *rho, cplx *f)
+{
+    if (!d || !d->amp) return;
+    const double ft = drive_f(d, t);
+    for (int s = 0; s < 2; ++s)
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j < N; ++j) {
+                const size_t e = ((size_t)s * N + i) * N + j;
+                f[e] += I * ft * (d->amp[s * N + i] - d->amp[s * N + j]) * rho[e];
+            }
+}
+
 void orc_rhs(int32_t N, int32_t B, const int32_t *bonds, const double *t_bond, double U,
              const double *rho, double *f)
 {
@@ -210,25 +238,31 @@ void orc_rhs(int32_t N, int32_t B, const int32_t *bonds, const double *t_bond, d
     free_adjacency(&a);
 }
 
-/* Classical fourth-order Runge-Kutta step of Eq. 6, both spins together. */
-static void rk4_step(const adjacency *a, double U, double dt, cplx *y, cplx *k, cplx *ys, cplx *acc)
+/* Classical fourth-order Runge-Kutta step of Eq. 6, both spins together,
+ * from time t (stage times t, t + dt/2, t + dt/2, t + dt for the drive). */
+static void rk4_step(const adjacency *a, double U, double dt, cplx *y, cplx *k, cplx *ys, cplx *acc,
+                     const drive *d, double t)
 {
     const size_t n = 2 * (size_t)a->N * a->N;
-    rhs(a, U, y, k);                                         /* k1 = f(y) */
+    rhs(a, U, y, k);                                         /* k1 = f(t, y) */
+    add_drive(a->N, d, t, y, k);
     for (size_t e = 0; e < n; ++e) { acc[e] = k[e]; ys[e] = y[e] + 0.5 * dt * k[e]; }
-    rhs(a, U, ys, k);                                        /* k2 = f(y + dt/2 k1) */
+    rhs(a, U, ys, k);                                        /* k2 = f(t + dt/2, y + dt/2 k1) */
+    add_drive(a->N, d, t + 0.5 * dt, ys, k);
     for (size_t e = 0; e < n; ++e) { acc[e] += 2.0 * k[e]; ys[e] = y[e] + 0.5 * dt * k[e]; }
-    rhs(a, U, ys, k);                                        /* k3 = f(y + dt/2 k2) */
+    rhs(a, U, ys, k);                                        /* k3 = f(t + dt/2, y + dt/2 k2) */
+    add_drive(a->N, d, t + 0.5 * dt, ys, k);
     for (size_t e = 0; e < n; ++e) { acc[e] += 2.0 * k[e]; ys[e] = y[e] + dt * k[e]; }
-    rhs(a, U, ys, k);                                        /* k4 = f(y + dt k3) */
+    rhs(a, U, ys, k);                                        /* k4 = f(t + dt, y + dt k3) */
+    add_drive(a->N, d, t + dt, ys, k);
     for (size_t e = 0; e < n; ++e) y[e] += dt / 6.0 * (acc[e] + k[e]);
 }
 
-/* Integrate one trajectory for n_steps steps.  snap (optional) receives
- * Re rho_ii,s at steps 0, out_every, 2 out_every, ... as [n_out][2N]
- * (s-major: index s*N + i). */
+/* Integrate one trajectory for n_steps steps from time t_start.  snap
+ * (optional) receives Re rho_ii,s at steps 0, out_every, 2 out_every, ... as
+ * [n_out][2N] (s-major: index s*N + i). */
 static void evolve_one(const adjacency *a, double U, double dt, int64_t n_steps, int64_t out_every,
-                       cplx *y, double *snap, int64_t snap_stride)
+                       cplx *y, double *snap, int64_t snap_stride, const drive *d, double t_start)
 {
     const int N = a->N;
     const size_t n = 2 * (size_t)N * N;
@@ -241,7 +275,7 @@ static void evolve_one(const adjacency *a, double U, double dt, int64_t n_steps,
                     snap[row * snap_stride + s * N + i] = creal(y[((size_t)s * N + i) * N + i]);
             row++;
         }
-        if (step < n_steps) rk4_step(a, U, dt, y, k, ys, acc);
+        if (step < n_steps) rk4_step(a, U, dt, y, k, ys, acc, d, t_start + (double)step * dt);
     }
     free(k); free(ys); free(acc);
 }
@@ -250,7 +284,18 @@ void orc_evolve(int32_t N, int32_t B, const int32_t *bonds, const double *t_bond
                 int64_t n_steps, int64_t out_every, double *rho, double *snap)
 {
     adjacency a = build_adjacency(N, B, bonds, t_bond);
-    evolve_one(&a, U, dt, n_steps, out_every, (cplx *)rho, snap, 2 * N);
+    evolve_one(&a, U, dt, n_steps, out_every, (cplx *)rho, snap, 2 * N, NULL, 0.0);
+    free_adjacency(&a);
+}
+
+/* orc_evolve with the time-dependent on-site drive, from time t_start. */
+void orc_evolve_drive(int32_t N, int32_t B, const int32_t *bonds, const double *t_bond, double U, double dt,
+                      int64_t n_steps, int64_t out_every, double *rho, double *snap, const double *amp,
+                      double t_start, double t0, double sigma, double omega, double phase)
+{
+    adjacency a = build_adjacency(N, B, bonds, t_bond);
+    drive d = {amp, t0, sigma, omega, phase};
+    evolve_one(&a, U, dt, n_steps, out_every, (cplx *)rho, snap, 2 * N, &d, t_start);
     free_adjacency(&a);
 }
 
@@ -275,7 +320,7 @@ int orc_run(int32_t N, int32_t B, const int32_t *bonds, const double *t_bond, do
         cplx *y = malloc(sizeof(cplx) * n);
         double *sn = snap ? malloc(sizeof(double) * (size_t)n_out * 2 * N) : NULL;
         orc_sample(N, n_up, n_dn, seed, m0 + mm, (double *)y);
-        evolve_one(&a, U, dt, n_steps, out_every, y, sn, 2 * N);
+        evolve_one(&a, U, dt, n_steps, out_every, y, sn, 2 * N, NULL, 0.0);
         if (sn) {
             for (int64_t r = 0; r < n_out; ++r)
                 memcpy(snap + ((size_t)r * M + mm) * 2 * N, sn + (size_t)r * 2 * N, sizeof(double) * 2 * N);

@@ -321,3 +321,50 @@ def test_general_sampler_moments_match_app_a_covariance():
             prod = np.conj(D[:, a, b]) * D[:, m, k]
             sd = np.sqrt(np.var(prod.real) + np.var(prod.imag)) / np.sqrt(K)
             assert abs(prod.mean() - w) < 5 * sd + 1e-12
+
+
+# ---- time-dependent on-site drive ----------------------------------------------
+def _drive_case():
+    lat = W.hexagon_chain(2)
+    N = lat.n_sites
+    rng = np.random.default_rng(4)
+    amp = rng.uniform(-1.0, 1.0, (2, N))
+    drive = dict(amp=amp, t0=1.2, sigma=0.5, omega=3.0, phase=0.4)
+    nu, nd = W.softened(W.neel_state(lat)[0]), W.softened(W.neel_state(lat)[1])
+    return lat, drive, oracle.sample(N, nu, nd, 5, 0)
+
+
+def test_drive_phases_closed_form():
+    """J = 0, U = 0: d rho_ij/dt = i (v_i - v_j) rho_ij, so
+    rho_ij(t) = rho_ij(0) exp(i (a_i - a_j) F(t)), F the integral of the pulse
+    (by quadrature); RK4 converges to it at fourth order in dt."""
+    from scipy.integrate import quad
+    lat, drive, r0 = _drive_case()
+    tb = np.zeros(lat.n_bonds)
+    T = 2.4
+    F = quad(lambda t: np.exp(-(t - drive["t0"]) ** 2 / (2 * drive["sigma"] ** 2))
+             * np.cos(drive["omega"] * (t - drive["t0"]) + drive["phase"]), 0.3, 0.3 + T, epsabs=1e-14)[0]
+    amp = drive["amp"]
+    want = np.stack([r0[s] * np.exp(1j * (amp[s][:, None] - amp[s][None, :]) * F) for s in range(2)])
+    errs = []
+    for dt in (0.02, 0.01):
+        got, _ = oracle.evolve(lat, 0.0, r0, dt, int(round(T / dt)), t_bond=tb, drive=drive, t_start=0.3)
+        errs.append(np.abs(got - want).max())
+    assert errs[1] < 1e-8
+    assert 10 < errs[0] / errs[1] < 24          # fourth order: ratio 16
+
+
+def test_drive_neutral_cases():
+    """Zero amplitudes, or equal amplitudes on every site, leave the
+    trajectory unchanged (the drive enters only through v_i - v_j); a later
+    start time equals an earlier pulse centre."""
+    lat, drive, r0 = _drive_case()
+    base, _ = oracle.evolve(lat, 1.6, r0, 0.01, 150)
+    z = dict(drive, amp=np.zeros_like(drive["amp"]))
+    assert np.array_equal(oracle.evolve(lat, 1.6, r0, 0.01, 150, drive=z)[0], base)
+    u = dict(drive, amp=np.full_like(drive["amp"], 0.7))
+    assert np.array_equal(oracle.evolve(lat, 1.6, r0, 0.01, 150, drive=u)[0], base)
+    a, _ = oracle.evolve(lat, 1.6, r0, 0.01, 150, drive=drive, t_start=0.5)
+    b, _ = oracle.evolve(lat, 1.6, r0, 0.01, 150, drive=dict(drive, t0=drive["t0"] - 0.5), t_start=0.0)
+    assert np.abs(a - b).max() < 1e-12
+    assert np.abs(a - base).max() > 1e-3          # and the drive does act

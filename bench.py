@@ -289,6 +289,40 @@ def bench_general(F, args):
             "rotation_frac_of_fp32_peak": flops / (ms / 1000) / 1e12 / fp32_peak}
 
 
+def bench_drive(F, args):
+    """Time-dependent on-site drive (Sec. 8(f) second extension): the 198-site
+    workload in FP32 with a Gaussian-envelope pulse on every site, against
+    the same integration without the drive (M samples, n steps)."""
+    import numpy as np
+    import torch
+    M, steps = args.drive_samples, args.drive_steps
+    wl = workload(M=M, steps=steps)
+    rng = np.random.default_rng(8)
+    amp = rng.uniform(-1.0, 1.0, (2, wl["lat"].n_sites))
+    out = {"workload": f"198-site flake, FP32, M={M}, {steps} RK4 steps, pulse t0=0.5 sigma=0.3 omega=5 on all sites"}
+    for name in ("undriven", "driven"):
+        P = F.Plan(wl["lat"], wl["U"], n_up=wl["n_up"], n_dn=wl["n_dn"], precision=F.FTWA_FP32)
+        if name == "driven":
+            P.set_drive(amp, 0.5, 0.3, 5.0, 0.0)
+        rho = P.sample(1, M)
+        P.evolve(rho, 5, snap=None)
+        torch.cuda.synchronize()
+        a, b = _events()
+        a.record()
+        P.evolve(rho, steps, snap=None, t_start=0.0)
+        b.record()
+        torch.cuda.synchronize()
+        if P.status() != 0:
+            raise RuntimeError("drive device status")
+        out[name] = M * steps / (a.elapsed_time(b) / 1000.0)
+        P.close()
+        del rho
+    out["unit"] = "sample-RK4-steps/s"
+    out["driven_over_undriven"] = out["driven"] / out["undriven"]
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_batched(F, args):
     """Config 3: honeycomb flakes of 24, 54, 96, 150 and 198 sites x U/t in
     {0.5, 1.0, 1.6, 2.5}, M samples each, FP32 state, one CUDA-graph launch
@@ -516,6 +550,8 @@ def run_gpu(args):
         extra["gram"] = bench_gram(F, args)
     if not args.no_general:
         extra["general_state"] = bench_general(F, args)
+    if not args.no_drive:
+        extra["drive"] = bench_drive(F, args)
 
     # ---- roofline of the dominant kernel (the RK4 stepper) -----------------------
     pk = peaks()
@@ -614,6 +650,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-gram", action="store_true")
     ap.add_argument("--no-general", action="store_true")
+    ap.add_argument("--no-drive", action="store_true")
+    ap.add_argument("--drive-samples", type=int, default=4096)
+    ap.add_argument("--drive-steps", type=int, default=200)
     ap.add_argument("--general-samples", type=int, default=4096)
     ap.add_argument("--adjoint-samples", type=int, default=4096)
     ap.add_argument("--batch-samples", type=int, default=4096)

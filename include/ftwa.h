@@ -184,6 +184,27 @@ int ftwa_philox(uint64_t seed, int64_t m, int32_t spin, int64_t p0, int64_t coun
 int ftwa_evolve(ftwa_plan_t *plan, void *rho_dev, int64_t M, int64_t n_steps,
                 void *snap_dev, void *stream);
 
+/* Time-dependent on-site drive (the time-dependent Hamiltonians that Sec. III
+ * admits; e.g. a pulsed site potential): h_ii,s(t) += v_i,s(t) with
+ * v_i,s(t) = amp[s][i] f(t), f(t) = exp(-(t - t0)^2 / (2 sigma^2))
+ * cos(omega (t - t0) + phase) (sigma <= 0: no envelope).  Eq. 6 gains
+ * i (v_i,s - v_j,s) rho_ij,s, evaluated at the RK4 stage times.  amp: host
+ * [2][N] (copied); amp == NULL removes the drive.  While a drive is set,
+ * ftwa_evolve / ftwa_evolve_at run the banded stepper (FTWA_ERR_UNSUPPORTED if
+ * its shape does not fit), and ftwa_adjoint and ftwa_batch_create return
+ * FTWA_ERR_UNSUPPORTED.  Errors: FTWA_ERR_INVALID_ARGUMENT (null plan,
+ * non-finite values), FTWA_ERR_CUDA, FTWA_ERR_OUT_OF_MEMORY. */
+int ftwa_set_drive(ftwa_plan_t *plan, const double *amp, double t0, double sigma, double omega, double phase);
+
+/* ftwa_evolve from time t_start (the time of the state in rho_dev; only the
+ * drive depends on it): stage times t_start + (step + c) dt, c = 0, 1/2,
+ * 1/2, 1.  ftwa_evolve is ftwa_evolve_at with t_start = 0.  With a drive the
+ * plan keeps a device table of 4 n_steps pulse values (grown on demand).
+ * Errors: as ftwa_evolve, and FTWA_ERR_INVALID_ARGUMENT for a non-finite
+ * t_start. */
+int ftwa_evolve_at(ftwa_plan_t *plan, void *rho_dev, int64_t M, int64_t n_steps, double t_start, void *snap_dev,
+                   void *stream);
+
 /* Eqs. 5 and 10 (fTWA_moments, g2_fTWA) from snapshots snap_dev
  * ([n_times][M][2N], plan precision), accumulated in double:
  *   occ_dev[t][k]     = <n_k>(t) = mean_m X[t][m][k] + 1/2,   k = s*N + i

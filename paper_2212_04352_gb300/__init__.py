@@ -128,8 +128,21 @@ class Plan:
                                             None if vi is None else ctypes.c_void_p(vi.ctypes.data)),
               "ftwa_set_initial_basis")
 
-    def evolve(self, rho, n_steps, snap=True, stream=None):
-        """Advance rho in place; returns snapshots [n_out, M, 2N] (or None)."""
+    def set_drive(self, amp, t0=0.0, sigma=0.0, omega=0.0, phase=0.0):
+        """Time-dependent on-site drive v_i,s(t) = amp[s][i] f(t) with
+        f(t) = exp(-(t - t0)^2 / (2 sigma^2)) cos(omega (t - t0) + phase);
+        amp None removes it."""
+        import numpy as np
+        if amp is None:
+            check(load().ftwa_set_drive(self._h, None, 0.0, 0.0, 0.0, 0.0), "ftwa_set_drive")
+            return
+        a = np.ascontiguousarray(amp, dtype=np.float64).reshape(2, self.N)
+        check(load().ftwa_set_drive(self._h, ctypes.c_void_p(a.ctypes.data), float(t0), float(sigma), float(omega),
+                                    float(phase)), "ftwa_set_drive")
+
+    def evolve(self, rho, n_steps, snap=True, stream=None, t_start=None):
+        """Advance rho in place (from time t_start, default 0); returns
+        snapshots [n_out, M, 2N] (or None)."""
         import torch
         M = rho.shape[0]
         X = None
@@ -137,8 +150,12 @@ class Plan:
             X = torch.empty((self.n_out(n_steps), M, 2 * self.N), dtype=self.real_dtype, device=rho.device)
         elif snap is not None and snap is not False:
             X = snap
-        check(load().ftwa_evolve(self._h, _ptr(rho), int(M), int(n_steps), _ptr(X), _stream(stream)),
-              "ftwa_evolve")
+        if t_start is None:
+            check(load().ftwa_evolve(self._h, _ptr(rho), int(M), int(n_steps), _ptr(X), _stream(stream)),
+                  "ftwa_evolve")
+        else:
+            check(load().ftwa_evolve_at(self._h, _ptr(rho), int(M), int(n_steps), float(t_start), _ptr(X),
+                                        _stream(stream)), "ftwa_evolve_at")
         return X
 
     def moments(self, X, gram_mode=FTWA_GRAM_FP64, g2=True, stream=None):

@@ -549,6 +549,8 @@ struct BandArgs {
     int qoff;                   // first column of block 0 (<= 0): blocks end at the last column
     int row_begin[kMaxCluster + 1];
     const uint32_t *items;      // [C][kWarps][k_items]: count | b << 6 | sr << 9 | slot << 18
+    const T *amp;               // [2][N] drive amplitudes (DRIVE)
+    const T *ftab;              // [n_steps][4] pulse value at the RK4 stage times (DRIVE)
     long long M, n_steps;
     int out_every;
     typename C2<T>::type *rho;
@@ -571,12 +573,13 @@ __device__ __forceinline__ void cfma(double t, double2 v, double2 &acc)
     acc.y = fma(t, v.y, acc.y);
 }
 
-template <int STAGE, typename T, bool CLUSTER, bool UNIFORM_T>
+template <int STAGE, typename T, bool CLUSTER, bool UNIFORM_T, bool DRIVE>
 __device__ __forceinline__ void band_stage(unsigned char *smem, const BandArgs<T> &a, const BandRow *s_row,
                                            const uint32_t *s_rowbase,
                                            const uint32_t *my_items, const int32_t *s_nbr, const T *s_t, T *s_diag,
                                            uint32_t diag_s, int lane, uint32_t t_state, int eps_bytes,
-                                           int diag_stride, long long b, bool snap_now, long long snap_row)
+                                           int diag_stride, long long b, bool snap_now, long long snap_row,
+                                           const T *s_amp, T fs)
 {
     using V = typename C2<T>::type;
     constexpr int SZ = sizeof(V);
@@ -615,6 +618,7 @@ __device__ __forceinline__ void band_stage(unsigned char *smem, const BandArgs<T
         const uint32_t mirror = s_rowbase[s * N + qc] + soff + boff_nxt;
         const T *dgo = dg + slot * twoN + (1 - s) * N;       // other spin's diagonal
         const T dq = dgo[qc];
+        const T aq = DRIVE ? s_amp[s * N + qc] : T(0);        // drive amplitude of column q
         // rows are processed two at a time: independent work for the same warp
         for (int r = 0; r < count; r += 2, e += 2) {
             const bool two = r + 1 < count;
@@ -652,7 +656,10 @@ __device__ __forceinline__ void band_stage(unsigned char *smem, const BandArgs<T
                     cfma(-t, CLUSTER ? ldc2(ad, T()) : lds2(ad, T()), h);
                 }
                 // + U (Re rho_pp,sbar - Re rho_qq,sbar) rho_pq
-                cfma(a.U * (dgo[p] - dq), own, h);
+                // (+ (v_p(t) - v_q(t)) rho_pq, the time-dependent on-site drive)
+                T coef = a.U * (dgo[p] - dq);
+                if constexpr (DRIVE) coef = fma(fs, s_amp[s * N + p] - aq, coef);
+                cfma(coef, own, h);
                 // k = i h; the diagonal of Eq. 6 is real (its imaginary part is
                 // rounding residue and is dropped)
                 V kk;
@@ -710,7 +717,7 @@ __device__ __forceinline__ void band_stage(unsigned char *smem, const BandArgs<T
     }
 }
 
-template <typename T, bool CLUSTER, bool UNIFORM_T>
+template <typename T, bool CLUSTER, bool UNIFORM_T, bool DRIVE>
 __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
 {
     using V = typename C2<T>::type;
@@ -737,6 +744,11 @@ __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
     ptr += 16 * ((4 * twoN + 15) / 16);
     T *s_diag = reinterpret_cast<T *>(ptr);
     ptr += 16 * ((sizeof(T) * 2 * S * twoN + 15) / 16);
+    T *s_amp = nullptr;
+    if constexpr (DRIVE) {
+        s_amp = reinterpret_cast<T *>(ptr);
+        ptr += 16 * ((sizeof(T) * twoN + 15) / 16);
+    }
     const uint32_t bufA_s = smem_addr(ptr);
     const uint32_t diag_s = smem_addr(s_diag);
     const int diag_stride = S * twoN;
@@ -756,6 +768,8 @@ __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
         s_nbr[i] = a.nbr[i];
         for (int n = 0; n < 4; ++n) s_t[4 * i + n] = a.tnb[4 * i + n];
     }
+    if constexpr (DRIVE)
+        for (int i = threadIdx.x; i < twoN; i += blockDim.x) s_amp[i] = a.amp[i];
     // row bases: element (p, k) of spin-row sr (slot 0, buffer A) at base + k * SZ
     for (int sr = threadIdx.x; sr < twoN; sr += blockDim.x) {
         int owner = 0;
@@ -869,20 +883,27 @@ __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
         for (long long step = 0; step < a.n_steps && h->abort == 0; ++step) {
             const bool snap_now = a.snap && ((step + 1) % a.out_every == 0);
             const long long snap_row = (step + 1) / a.out_every;
-            band_stage<0, T, CLUSTER, UNIFORM_T>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag, diag_s, lane,
-                                                 t_state, eps_bytes, diag_stride, b, snap_now, snap_row);
+            T fd[4] = {T(0), T(0), T(0), T(0)};
+            if constexpr (DRIVE)
+                for (int k = 0; k < 4; ++k) fd[k] = a.ftab[4 * step + k];
+            band_stage<0, T, CLUSTER, UNIFORM_T, DRIVE>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag,
+                                                        diag_s, lane, t_state, eps_bytes, diag_stride, b, snap_now,
+                                                        snap_row, s_amp, fd[0]);
             tmem_wait_st();
             if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
-            band_stage<1, T, CLUSTER, UNIFORM_T>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag, diag_s, lane,
-                                                 t_state, eps_bytes, diag_stride, b, snap_now, snap_row);
+            band_stage<1, T, CLUSTER, UNIFORM_T, DRIVE>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag,
+                                                        diag_s, lane, t_state, eps_bytes, diag_stride, b, snap_now,
+                                                        snap_row, s_amp, fd[1]);
             tmem_wait_st();
             if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
-            band_stage<2, T, CLUSTER, UNIFORM_T>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag, diag_s, lane,
-                                                 t_state, eps_bytes, diag_stride, b, snap_now, snap_row);
+            band_stage<2, T, CLUSTER, UNIFORM_T, DRIVE>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag,
+                                                        diag_s, lane, t_state, eps_bytes, diag_stride, b, snap_now,
+                                                        snap_row, s_amp, fd[2]);
             tmem_wait_st();
             if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
-            band_stage<3, T, CLUSTER, UNIFORM_T>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag, diag_s, lane,
-                                                 t_state, eps_bytes, diag_stride, b, snap_now, snap_row);
+            band_stage<3, T, CLUSTER, UNIFORM_T, DRIVE>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag,
+                                                        diag_s, lane, t_state, eps_bytes, diag_stride, b, snap_now,
+                                                        snap_row, s_amp, fd[3]);
             tmem_wait_st();
             if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
         }
@@ -1158,11 +1179,12 @@ static bool band_items(int N, int S, int rb0, int rb1, int e_cap, int R, std::ve
     return true;
 }
 
-static int band_smem(int N, int S, int real_bytes, int buf_bytes)
+static int band_smem(int N, int S, int real_bytes, int buf_bytes, bool drive)
 {
     auto r16 = [](int x) { return 16 * ((x + 15) / 16); };
     int b = 64 + (int)sizeof(BandRow) * 2 * N + r16(4 * N) + r16(real_bytes * 4 * N) + r16(4 * 2 * N);
     b += r16(real_bytes * 2 * S * 2 * N);
+    if (drive) b += r16(real_bytes * 2 * N);
     return b + 2 * buf_bytes;
 }
 
@@ -1210,7 +1232,7 @@ int choose_band_shape(Plan *p, int64_t M, BandShape *out)
         int bestE = 0, bestK = 0;
         for (int S = 1; S <= want; ++S) {
             const int buf = ((S * eps_max * SZ + 15) / 16) * 16;
-            if (band_smem(N, S, real_bytes, buf) > max_smem) break;
+            if (band_smem(N, S, real_bytes, buf, p->drive) > max_smem) break;
             std::vector<std::vector<uint32_t>> its(C);
             int E = 0, K = 0;
             bool ok = true;
@@ -1246,7 +1268,7 @@ int choose_band_shape(Plan *p, int64_t M, BandShape *out)
                     sh.items[((size_t)r * kWarps + w) * bestK + i] = best_items[r][(size_t)w * Kr + i];
         }
         sh.buf_bytes = ((best * eps_max * SZ + 15) / 16) * 16;
-        sh.smem_bytes = std::max(kMinSmem, band_smem(N, best, real_bytes, sh.buf_bytes));
+        sh.smem_bytes = std::max(kMinSmem, band_smem(N, best, real_bytes, sh.buf_bytes, p->drive));
         const long long batches = (M + best - 1) / best;
         sh.grid = (int)std::min<long long>(std::max<long long>(batches, 1), std::max(1, sm / C)) * C;
         *out = sh;
@@ -1255,10 +1277,10 @@ int choose_band_shape(Plan *p, int64_t M, BandShape *out)
     return FTWA_ERR_UNSUPPORTED;
 }
 
-template <typename T, bool CLUSTER, bool UNIFORM_T>
+template <typename T, bool CLUSTER, bool UNIFORM_T, bool DRIVE>
 static int band_launch(Plan *p, BandShape &sh, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s)
 {
-    auto kern = band_stepper<T, CLUSTER, UNIFORM_T>;
+    auto kern = band_stepper<T, CLUSTER, UNIFORM_T, DRIVE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem_bytes);
     if (e != cudaSuccess) return set_cuda_error(e);
     cudaLaunchConfig_t cfg{};
@@ -1320,6 +1342,11 @@ static int band_launch(Plan *p, BandShape &sh, void *rho, int64_t M, int64_t n_s
     a.k_items = sh.k_items;
     a.buf_bytes = sh.buf_bytes;
     a.qoff = sh.qoff;
+    a.amp = nullptr;
+    if (DRIVE)
+        a.amp = std::is_same<T, double>::value ? reinterpret_cast<const T *>(p->d_amp64)
+                                               : reinterpret_cast<const T *>(p->d_amp32);
+    a.ftab = DRIVE ? reinterpret_cast<const T *>(p->d_ftab) : nullptr;
     for (int i = 0; i <= kMaxCluster; ++i) a.row_begin[i] = sh.row_begin[i];
     a.items = p->d_items;
     a.M = M;
@@ -1334,18 +1361,77 @@ static int band_launch(Plan *p, BandShape &sh, void *rho, int64_t M, int64_t n_s
     return set_cuda_error(e);
 }
 
+template <typename T, bool DRIVE>
+static int band_dispatch_d(Plan *p, BandShape &sh, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s)
+{
+    if (sh.cluster > 1)
+        return p->uniform_t ? band_launch<T, true, true, DRIVE>(p, sh, rho, M, n_steps, snap, s)
+                            : band_launch<T, true, false, DRIVE>(p, sh, rho, M, n_steps, snap, s);
+    return p->uniform_t ? band_launch<T, false, true, DRIVE>(p, sh, rho, M, n_steps, snap, s)
+                        : band_launch<T, false, false, DRIVE>(p, sh, rho, M, n_steps, snap, s);
+}
+
 template <typename T>
 static int band_dispatch(Plan *p, BandShape &sh, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s)
 {
-    if (sh.cluster > 1)
-        return p->uniform_t ? band_launch<T, true, true>(p, sh, rho, M, n_steps, snap, s)
-                            : band_launch<T, true, false>(p, sh, rho, M, n_steps, snap, s);
-    return p->uniform_t ? band_launch<T, false, true>(p, sh, rho, M, n_steps, snap, s)
-                        : band_launch<T, false, false>(p, sh, rho, M, n_steps, snap, s);
+    return p->drive ? band_dispatch_d<T, true>(p, sh, rho, M, n_steps, snap, s)
+                    : band_dispatch_d<T, false>(p, sh, rho, M, n_steps, snap, s);
 }
 
-int launch_evolve(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s)
+// pulse values f(t) of the on-site drive at the four RK4 stage times of every
+// step, t = t_start + (step + c) dt, c = 0, 1/2, 1/2, 1 (in double)
+template <typename T>
+__global__ void drive_table_kernel(T *ftab, long long n_steps, double t_start, double dt, double t0, double sigma,
+                                   double omega, double phase)
 {
+    const double c[4] = {0.0, 0.5, 0.5, 1.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 4 * n_steps;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double t = t_start + ((double)(i / 4) + c[i % 4]) * dt;
+        const double env = sigma > 0.0 ? exp(-(t - t0) * (t - t0) / (2.0 * sigma * sigma)) : 1.0;
+        ftab[i] = (T)(env * cos(omega * (t - t0) + phase));
+    }
+}
+
+static int prepare_drive(Plan *p, int64_t n_steps, double t_start, cudaStream_t s)
+{
+    const size_t bytes = (size_t)(p->precision == FTWA_FP64 ? 8 : 4) * 4 * (size_t)std::max<int64_t>(n_steps, 1);
+    if (p->ftab_bytes < bytes) {
+        cudaFree(p->d_ftab);
+        p->d_ftab = nullptr;
+        p->ftab_bytes = 0;
+        cudaError_t e = cudaMalloc(&p->d_ftab, bytes);
+        if (e != cudaSuccess) return set_cuda_error(e);
+        p->ftab_bytes = bytes;
+    }
+    if (n_steps == 0) return FTWA_OK;
+    const long long n = 4 * n_steps;
+    const int grid = (int)std::min<long long>((n + 255) / 256, 4096);
+    if (p->precision == FTWA_FP64)
+        drive_table_kernel<double><<<grid, 256, 0, s>>>(reinterpret_cast<double *>(p->d_ftab), n_steps, t_start,
+                                                       p->dt, p->drive_t0, p->drive_sigma, p->drive_omega,
+                                                       p->drive_phase);
+    else
+        drive_table_kernel<float><<<grid, 256, 0, s>>>(reinterpret_cast<float *>(p->d_ftab), n_steps, t_start,
+                                                      p->dt, p->drive_t0, p->drive_sigma, p->drive_omega,
+                                                      p->drive_phase);
+    return set_cuda_error(cudaGetLastError());
+}
+
+int launch_evolve(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s, double t_start)
+{
+    if (p->drive) {
+        // the time-dependent drive runs on the banded stepper (both precisions)
+        BandShape bs;
+        int rc = choose_band_shape(p, M, &bs);
+        if (rc != FTWA_OK) return rc;
+        if (M > 0 && !p->dry_run) {
+            rc = prepare_drive(p, n_steps, t_start, s);
+            if (rc != FTWA_OK) return rc;
+        }
+        return p->precision == FTWA_FP64 ? band_dispatch<double>(p, bs, rho, M, n_steps, snap, s)
+                                         : band_dispatch<float>(p, bs, rho, M, n_steps, snap, s);
+    }
     // automatic choice: the banded stepper for FP32; for FP64 (DFMA-bound on
     // this part) the packed-triangle stepper, which does fewer flops per element
     const bool try_band = p->variant_override == 1 || (p->variant_override == 0 && p->precision == FTWA_FP32);

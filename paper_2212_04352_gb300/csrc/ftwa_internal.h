@@ -80,6 +80,13 @@ struct Plan {
     void *d_V = nullptr;              // [2][N][N] complex eigenvectors (columns), plan precision
     void *d_rot_ws = nullptr;         // rotation workspace (chunk of samples)
     size_t rot_ws_bytes = 0;
+    // time-dependent on-site drive v_i,s(t) = amp[s][i] f(t)
+    bool drive = false;
+    double drive_t0 = 0, drive_sigma = 0, drive_omega = 0, drive_phase = 0;
+    double *d_amp64 = nullptr;        // [2][N]
+    float *d_amp32 = nullptr;         // [2][N]
+    void *d_ftab = nullptr;           // [n_steps][4] pulse values of the last evolve call
+    size_t ftab_bytes = 0;
 };
 
 int set_cuda_error(cudaError_t e);
@@ -92,7 +99,9 @@ int launch_rotate(Plan *p, void *rho, int64_t M, cudaStream_t s);
 void free_basis(Plan *p);
 int launch_philox(uint64_t seed, int64_t m, int32_t spin, int64_t p0, int64_t count, uint32_t *out,
                   cudaStream_t s);
-int launch_evolve(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s);
+int launch_evolve(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s,
+                 double t_start = 0.0);
+void free_drive(Plan *p);
 int choose_stepper_shape(Plan *p, int64_t M, StepperShape *out);
 int choose_band_shape(Plan *p, int64_t M, BandShape *out);
 int launch_moments(Plan *p, const void *snap, int64_t M, int32_t T, double *occ, double *conn, double *g2,

@@ -7,6 +7,7 @@
 #include <new>
 #include <set>
 #include <utility>
+#include <vector>
 
 #include "ftwa_internal.h"
 
@@ -17,6 +18,18 @@ int set_cuda_error(cudaError_t e)
     if (e == cudaSuccess) return FTWA_OK;
     if (e == cudaErrorMemoryAllocation) return FTWA_ERR_OUT_OF_MEMORY;
     return FTWA_ERR_CUDA;
+}
+
+void free_drive(Plan *p)
+{
+    cudaFree(p->d_amp64);
+    cudaFree(p->d_amp32);
+    cudaFree(p->d_ftab);
+    p->d_amp64 = nullptr;
+    p->d_amp32 = nullptr;
+    p->d_ftab = nullptr;
+    p->ftab_bytes = 0;
+    p->drive = false;
 }
 
 static void free_tables(Plan *p)
@@ -32,6 +45,7 @@ static void free_tables(Plan *p)
     cudaFree(p->d_items);
     cudaFree(p->d_adj_ws);
     free_basis(p);
+    free_drive(p);
     p->d_adj_ws = nullptr;
     p->adj_ws_bytes = 0;
     p->d_items = nullptr;
@@ -352,6 +366,44 @@ int ftwa_evolve(ftwa_plan_t *p, void *rho_dev, int64_t M, int64_t n_steps, void 
 {
     if (!p || M < 0 || n_steps < 0 || (M > 0 && !rho_dev)) return FTWA_ERR_INVALID_ARGUMENT;
     return launch_evolve(p, rho_dev, M, n_steps, snap_dev, static_cast<cudaStream_t>(stream));
+}
+
+int ftwa_evolve_at(ftwa_plan_t *p, void *rho_dev, int64_t M, int64_t n_steps, double t_start, void *snap_dev,
+                   void *stream)
+{
+    if (!p || M < 0 || n_steps < 0 || (M > 0 && !rho_dev) || !std::isfinite(t_start))
+        return FTWA_ERR_INVALID_ARGUMENT;
+    return launch_evolve(p, rho_dev, M, n_steps, snap_dev, static_cast<cudaStream_t>(stream), t_start);
+}
+
+int ftwa_set_drive(ftwa_plan_t *p, const double *amp, double t0, double sigma, double omega, double phase)
+{
+    if (!p) return FTWA_ERR_INVALID_ARGUMENT;
+    if (!amp) {
+        free_drive(p);
+        return FTWA_OK;
+    }
+    if (!std::isfinite(t0) || !std::isfinite(sigma) || !std::isfinite(omega) || !std::isfinite(phase))
+        return FTWA_ERR_INVALID_ARGUMENT;
+    const int n = 2 * p->N;
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(amp[i])) return FTWA_ERR_INVALID_ARGUMENT;
+    free_drive(p);
+    std::vector<float> a32(amp, amp + n);
+    cudaError_t e = cudaMalloc(&p->d_amp64, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_amp64, amp, sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_amp32, sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_amp32, a32.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_drive(p);
+        return set_cuda_error(e);
+    }
+    p->drive_t0 = t0;
+    p->drive_sigma = sigma;
+    p->drive_omega = omega;
+    p->drive_phase = phase;
+    p->drive = true;
+    return FTWA_OK;
 }
 
 int ftwa_moments(ftwa_plan_t *p, const void *snap_dev, int64_t M, int32_t n_times, double *occ_dev, double *conn_dev,

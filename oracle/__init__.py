@@ -55,6 +55,7 @@ def _load():
             lib.orc_sample.argtypes = [i32, P, P, u64, i64, P]
             lib.orc_rhs.argtypes = [i32, i32, P, P, f64, P, P]
             lib.orc_evolve.argtypes = [i32, i32, P, P, f64, f64, i64, i64, P, P]
+            lib.orc_evolve_longrange.argtypes = [i32, i32, P, P, P, f64, i64, i64, P, P]
             lib.orc_evolve_drive.argtypes = [i32, i32, P, P, f64, f64, i64, i64, P, P, P, f64, f64, f64, f64, f64]
             lib.orc_run.argtypes = [i32, i32, P, P, f64, P, P, u64, i64, i64, f64, i64, i64, P, P, i32]
             lib.orc_run.restype = ctypes.c_int
@@ -130,19 +131,26 @@ def rhs(lat, U, rho, t_bond=None):
     return out
 
 
-def evolve(lat, U, rho0, dt, n_steps, out_every=0, t_bond=None, drive=None, t_start=0.0):
+def evolve(lat, U, rho0, dt, n_steps, out_every=0, t_bond=None, drive=None, t_start=0.0, u=None):
     """RK4-integrate one state; returns (rho(T), snapshots [n_out, 2N] or None).
 
     drive: optional time-dependent on-site potential v_i,s(t) = amp[s][i] f(t),
     f(t) = exp(-(t - t0)^2 / (2 sigma^2)) cos(omega (t - t0) + phase), given as
-    dict(amp=[2, N], t0=, sigma=, omega=, phase=); t_start is the time of rho0."""
+    dict(amp=[2, N], t0=, sigma=, omega=, phase=); t_start is the time of rho0.
+    u: optional symmetric interaction matrix [N, N] of Eq. 1 (replaces U)."""
     lib = _load()
     b, t = _lat_arrays(lat, t_bond)
     r = np.array(rho0, dtype=np.complex128, order="C", copy=True)
     snap = None
     if out_every > 0:
         snap = np.zeros((n_steps // out_every + 1, 2 * lat.n_sites))
-    if drive is None:
+    if u is not None:
+        if drive is not None:
+            raise ValueError("the oracle integrates a drive or a long-range u, not both")
+        um = np.ascontiguousarray(u, dtype=np.float64).reshape(lat.n_sites, lat.n_sites)
+        lib.orc_evolve_longrange(lat.n_sites, lat.n_bonds, _p(b), _p(t), _p(um), dt, n_steps, out_every, _p(r),
+                                 _p(snap))
+    elif drive is None:
         lib.orc_evolve(lat.n_sites, lat.n_bonds, _p(b), _p(t), U, dt, n_steps, out_every, _p(r), _p(snap))
     else:
         amp = np.ascontiguousarray(drive["amp"], dtype=np.float64).reshape(2, lat.n_sites)

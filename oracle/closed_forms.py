@@ -110,3 +110,14 @@ def general_state_covariance(lam, V, idx):
         diag = np.sum(V[a].conj() * V[b] * V[m] * V[k].conj() * lam * (1 - lam))
         out.append(full - diag)
     return np.array(out)
+
+
+def energy_longrange(lat, u, rho):
+    """Classical energy of Eq. A10 with the full interaction sum of Eq. 1,
+    H_W = -sum_ij,s j_ij rho_ij,s + sum_ij u_ij (rho_ii,up + 1/2)(rho_jj,dn + 1/2),
+    for a symmetric u; conserved by the flow of Eq. 6 with that u."""
+    J = hopping_matrix(lat)
+    e = -sum(np.sum(J * rho[s]) for s in range(2))
+    du = np.real(np.diag(rho[0])) + 0.5
+    dd = np.real(np.diag(rho[1])) + 0.5
+    return float(np.real(e) + du @ np.asarray(u) @ dd)

@@ -230,6 +230,62 @@ static void add_drive(int N, const drive *d, double t, const cplx *rho, cplx *f)
             }
 }
 
+/* Eq. 6 with a general (symmetric) interaction matrix u_ij of Eq. 1:
+ *   d/dt rho_ij,s = i sum_k ( j_jk rho_ik,s - j_ki rho_kj,s
+ *                            + (u_ki - u_kj)(rho_kk,sbar + 1/2) rho_ij,s ),
+ * the interaction sum taken literally over k. */
+static void rhs_longrange(const adjacency *a, const double *u, const cplx *rho, cplx *f)
+{
+    const int N = a->N;
+    for (int s = 0; s < 2; ++s) {
+        const cplx *r = rho + (size_t)s * N * N;
+        const cplx *rb = rho + (size_t)(1 - s) * N * N;
+        cplx *o = f + (size_t)s * N * N;
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j < N; ++j) {
+                cplx acc = 0.0;
+                for (int e = a->start[j]; e < a->start[j + 1]; ++e)
+                    acc += a->hop[e] * r[(size_t)i * N + a->nbr[e]];
+                for (int e = a->start[i]; e < a->start[i + 1]; ++e)
+                    acc -= a->hop[e] * r[(size_t)a->nbr[e] * N + j];
+                cplx w = 0.0;
+                for (int k = 0; k < N; ++k)
+                    w += (u[(size_t)k * N + i] - u[(size_t)k * N + j]) * (rb[(size_t)k * N + k] + 0.5);
+                acc += w * r[(size_t)i * N + j];
+                o[(size_t)i * N + j] = I * acc;
+            }
+    }
+}
+
+/* RK4 integration of one state under rhs_longrange (snapshots as orc_evolve). */
+void orc_evolve_longrange(int32_t N, int32_t B, const int32_t *bonds, const double *t_bond, const double *u,
+                          double dt, int64_t n_steps, int64_t out_every, double *rho_in, double *snap)
+{
+    adjacency a = build_adjacency(N, B, bonds, t_bond);
+    const size_t n = 2 * (size_t)N * N;
+    cplx *y = (cplx *)rho_in;
+    cplx *k = malloc(sizeof(cplx) * n), *ys = malloc(sizeof(cplx) * n), *acc = malloc(sizeof(cplx) * n);
+    int64_t row = 0;
+    for (int64_t step = 0; step <= n_steps; ++step) {
+        if (snap && out_every > 0 && step % out_every == 0) {
+            for (int s = 0; s < 2; ++s)
+                for (int i = 0; i < N; ++i) snap[row * 2 * N + s * N + i] = creal(y[((size_t)s * N + i) * N + i]);
+            row++;
+        }
+        if (step == n_steps) break;
+        rhs_longrange(&a, u, y, k);
+        for (size_t e = 0; e < n; ++e) { acc[e] = k[e]; ys[e] = y[e] + 0.5 * dt * k[e]; }
+        rhs_longrange(&a, u, ys, k);
+        for (size_t e = 0; e < n; ++e) { acc[e] += 2.0 * k[e]; ys[e] = y[e] + 0.5 * dt * k[e]; }
+        rhs_longrange(&a, u, ys, k);
+        for (size_t e = 0; e < n; ++e) { acc[e] += 2.0 * k[e]; ys[e] = y[e] + dt * k[e]; }
+        rhs_longrange(&a, u, ys, k);
+        for (size_t e = 0; e < n; ++e) y[e] += dt / 6.0 * (acc[e] + k[e]);
+    }
+    free(k); free(ys); free(acc);
+    free_adjacency(&a);
+}
+
 void orc_rhs(int32_t N, int32_t B, const int32_t *bonds, const double *t_bond, double U,
              const double *rho, double *f)
 {

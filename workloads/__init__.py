@@ -21,6 +21,7 @@ from .lattices import (  # noqa: F401
     ring,
     dimer,
     chain,
+    coulomb_interaction,
 )
 from .states import (  # noqa: F401
     neel_state,

@@ -174,3 +174,13 @@ def dimer(t: float = 1.0) -> Lattice:
 def chain(n: int, t: float = 1.0) -> Lattice:
     """Open chain of n sites (bipartite for every n, so odd sizes are possible)."""
     return _finish(f"chain_{n}", n, [(i, i + 1) for i in range(n - 1)], [(float(i), 0.0) for i in range(n)], t=t)
+
+
+def coulomb_interaction(lat: Lattice, U: float, V: float) -> np.ndarray:
+    """Symmetric interaction matrix u_ij of Eq. 1 with a long-range tail:
+    u_ii = U and u_ij = V / |r_i - r_j| (distances in the lattice's coordinate
+    units) for i != j."""
+    d = np.linalg.norm(lat.coords[:, None, :] - lat.coords[None, :, :], axis=-1)
+    u = np.where(d > 0, V / np.where(d > 0, d, 1.0), 0.0)
+    np.fill_diagonal(u, U)
+    return u

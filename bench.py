@@ -290,20 +290,25 @@ def bench_general(F, args):
 
 
 def bench_drive(F, args):
-    """Time-dependent on-site drive (Sec. 8(f) second extension): the 198-site
-    workload in FP32 with a Gaussian-envelope pulse on every site, against
-    the same integration without the drive (M samples, n steps)."""
+    """Tabulated diagonal field (Sec. 8(f) second and third extensions): the
+    198-site workload in FP32 with a Gaussian-envelope pulse on every site,
+    and with a long-range interaction u_ij over all pairs, against the plain
+    on-site integration (M samples, n steps)."""
     import numpy as np
     import torch
     M, steps = args.drive_samples, args.drive_steps
     wl = workload(M=M, steps=steps)
     rng = np.random.default_rng(8)
     amp = rng.uniform(-1.0, 1.0, (2, wl["lat"].n_sites))
-    out = {"workload": f"198-site flake, FP32, M={M}, {steps} RK4 steps, pulse t0=0.5 sigma=0.3 omega=5 on all sites"}
-    for name in ("undriven", "driven"):
+    import workloads as W
+    out = {"workload": f"198-site flake, FP32, M={M}, {steps} RK4 steps; driven: pulse t0=0.5 sigma=0.3 "
+                       f"omega=5 on all sites; longrange: u_ii = U, u_ij = 0.4 / r_ij (all pairs)"}
+    for name in ("undriven", "driven", "longrange"):
         P = F.Plan(wl["lat"], wl["U"], n_up=wl["n_up"], n_dn=wl["n_dn"], precision=F.FTWA_FP32)
         if name == "driven":
             P.set_drive(amp, 0.5, 0.3, 5.0, 0.0)
+        if name == "longrange":
+            P.set_interaction(W.coulomb_interaction(wl["lat"], wl["U"], 0.4))
         rho = P.sample(1, M)
         P.evolve(rho, 5, snap=None)
         torch.cuda.synchronize()
@@ -319,6 +324,7 @@ def bench_drive(F, args):
         del rho
     out["unit"] = "sample-RK4-steps/s"
     out["driven_over_undriven"] = out["driven"] / out["undriven"]
+    out["longrange_over_onsite"] = out["longrange"] / out["undriven"]
     torch.cuda.empty_cache()
     return out
 

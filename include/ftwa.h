@@ -196,6 +196,17 @@ int ftwa_evolve(ftwa_plan_t *plan, void *rho_dev, int64_t M, int64_t n_steps,
  * non-finite values), FTWA_ERR_CUDA, FTWA_ERR_OUT_OF_MEMORY. */
 int ftwa_set_drive(ftwa_plan_t *plan, const double *amp, double t0, double sigma, double omega, double phase);
 
+/* Long-range interaction (Eq. 1 with a general u_ij; Eq. 6 with its sum over
+ * k): u is a host [N][N] symmetric matrix (copied; u_ii is the on-site term
+ * and replaces the plan's U).  Eq. 6 then uses the diagonal field
+ * h_ii,s = sum_k u_ik (rho_kk,sbar + 1/2), a dense mat-vec per stage computed
+ * on the device.  u == NULL returns to the on-site U.  While set,
+ * ftwa_evolve runs the banded stepper (FTWA_ERR_UNSUPPORTED if its shape
+ * does not fit) and ftwa_adjoint / ftwa_batch_create return
+ * FTWA_ERR_UNSUPPORTED.  Errors: FTWA_ERR_INVALID_ARGUMENT (null plan,
+ * non-finite or non-symmetric u), FTWA_ERR_CUDA, FTWA_ERR_OUT_OF_MEMORY. */
+int ftwa_set_interaction(ftwa_plan_t *plan, const double *u);
+
 /* ftwa_evolve from time t_start (the time of the state in rho_dev; only the
  * drive depends on it): stage times t_start + (step + c) dt, c = 0, 1/2,
  * 1/2, 1.  ftwa_evolve is ftwa_evolve_at with t_start = 0.  With a drive the

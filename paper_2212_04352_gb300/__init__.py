@@ -140,6 +140,16 @@ class Plan:
         check(load().ftwa_set_drive(self._h, ctypes.c_void_p(a.ctypes.data), float(t0), float(sigma), float(omega),
                                     float(phase)), "ftwa_set_drive")
 
+    def set_interaction(self, u):
+        """Long-range interaction u [N, N] (symmetric, u_ii = on-site term) of
+        Eq. 1 in place of U; None returns to the on-site U."""
+        import numpy as np
+        if u is None:
+            check(load().ftwa_set_interaction(self._h, None), "ftwa_set_interaction")
+            return
+        a = np.ascontiguousarray(u, dtype=np.float64).reshape(self.N, self.N)
+        check(load().ftwa_set_interaction(self._h, ctypes.c_void_p(a.ctypes.data)), "ftwa_set_interaction")
+
     def evolve(self, rho, n_steps, snap=True, stream=None, t_start=None):
         """Advance rho in place (from time t_start, default 0); returns
         snapshots [n_out, M, 2N] (or None)."""

@@ -549,8 +549,11 @@ struct BandArgs {
     int qoff;                   // first column of block 0 (<= 0): blocks end at the last column
     int row_begin[kMaxCluster + 1];
     const uint32_t *items;      // [C][kWarps][k_items]: count | b << 6 | sr << 9 | slot << 18
-    const T *amp;               // [2][N] drive amplitudes (DRIVE)
-    const T *ftab;              // [n_steps][4] pulse value at the RK4 stage times (DRIVE)
+    // FIELD: the diagonal field h_pp,s of every stage is tabulated in shared
+    // memory (on-site U or a long-range u, plus the time-dependent drive)
+    const T *amp;               // [2][N] drive amplitudes, or null
+    const T *ftab;              // [n_steps][4] pulse value at the RK4 stage times, or null
+    const T *u;                 // [N][N] symmetric interaction of Eq. 1, or null (on-site U)
     long long M, n_steps;
     int out_every;
     typename C2<T>::type *rho;
@@ -573,13 +576,13 @@ __device__ __forceinline__ void cfma(double t, double2 v, double2 &acc)
     acc.y = fma(t, v.y, acc.y);
 }
 
-template <int STAGE, typename T, bool CLUSTER, bool UNIFORM_T, bool DRIVE>
+template <int STAGE, typename T, bool CLUSTER, bool UNIFORM_T, bool FIELD>
 __device__ __forceinline__ void band_stage(unsigned char *smem, const BandArgs<T> &a, const BandRow *s_row,
                                            const uint32_t *s_rowbase,
                                            const uint32_t *my_items, const int32_t *s_nbr, const T *s_t, T *s_diag,
                                            uint32_t diag_s, int lane, uint32_t t_state, int eps_bytes,
                                            int diag_stride, long long b, bool snap_now, long long snap_row,
-                                           const T *s_amp, T fs)
+                                           const T *s_field)
 {
     using V = typename C2<T>::type;
     constexpr int SZ = sizeof(V);
@@ -618,7 +621,8 @@ __device__ __forceinline__ void band_stage(unsigned char *smem, const BandArgs<T
         const uint32_t mirror = s_rowbase[s * N + qc] + soff + boff_nxt;
         const T *dgo = dg + slot * twoN + (1 - s) * N;       // other spin's diagonal
         const T dq = dgo[qc];
-        const T aq = DRIVE ? s_amp[s * N + qc] : T(0);        // drive amplitude of column q
+        const T *fld = FIELD ? s_field + slot * twoN + s * N : nullptr;   // this spin's diagonal field
+        const T fq = FIELD ? fld[qc] : T(0);
         // rows are processed two at a time: independent work for the same warp
         for (int r = 0; r < count; r += 2, e += 2) {
             const bool two = r + 1 < count;
@@ -656,9 +660,10 @@ __device__ __forceinline__ void band_stage(unsigned char *smem, const BandArgs<T
                     cfma(-t, CLUSTER ? ldc2(ad, T()) : lds2(ad, T()), h);
                 }
                 // + U (Re rho_pp,sbar - Re rho_qq,sbar) rho_pq
-                // (+ (v_p(t) - v_q(t)) rho_pq, the time-dependent on-site drive)
-                T coef = a.U * (dgo[p] - dq);
-                if constexpr (DRIVE) coef = fma(fs, s_amp[s * N + p] - aq, coef);
+                // (FIELD: + (h_pp,s - h_qq,s) rho_pq from the tabulated field)
+                T coef;
+                if constexpr (FIELD) coef = fld[p] - fq;
+                else coef = a.U * (dgo[p] - dq);
                 cfma(coef, own, h);
                 // k = i h; the diagonal of Eq. 6 is real (its imaginary part is
                 // rounding residue and is dropped)
@@ -717,7 +722,47 @@ __device__ __forceinline__ void band_stage(unsigned char *smem, const BandArgs<T
     }
 }
 
-template <typename T, bool CLUSTER, bool UNIFORM_T, bool DRIVE>
+// FIELD: the diagonal field of the coming stage for every slot and spin,
+//   h_pp,s = sum_k u_pk (Re rho_kk,sbar + 1/2)     (long-range u of Eq. 1)
+//          = U (Re rho_pp,sbar + 1/2)               (on-site U)
+//          + amp_s,p f(t_stage)                     (time-dependent drive),
+// from the stage's diagonal buffer dg [S][2N]; each CTA of a cluster holds
+// all diagonals and computes the whole table (a warp per row for u).  Ends
+// with a CTA barrier.
+template <typename T>
+__device__ __forceinline__ void diag_field(const BandArgs<T> &a, const T *dg, const T *s_amp, T f, T *s_field)
+{
+    const int N = a.N, twoN = 2 * N;
+    if (a.u) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+        for (int r = warp; r < a.S * N; r += n_warps) {
+            const int slot = r / N, p = r % N;
+            const T *d = dg + slot * twoN;
+            T up = T(0), dn = T(0);        // fields of spin up (from dn density) and spin dn
+            for (int k = lane; k < N; k += 32) {
+                const T u = a.u[(size_t)p * N + k];
+                up = fma(u, d[N + k] + T(0.5), up);
+                dn = fma(u, d[k] + T(0.5), dn);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                up += __shfl_xor_sync(0xffffffffu, up, o);
+                dn += __shfl_xor_sync(0xffffffffu, dn, o);
+            }
+            if (lane == 0) {
+                s_field[slot * twoN + p] = fma(s_amp[p], f, up);
+                s_field[slot * twoN + N + p] = fma(s_amp[N + p], f, dn);
+            }
+        }
+    } else {
+        for (int i = threadIdx.x; i < a.S * twoN; i += blockDim.x) {
+            const int slot = i / twoN, sp = i % twoN, s = sp / N, p = sp % N;
+            s_field[i] = fma(s_amp[sp], f, a.U * (dg[slot * twoN + (1 - s) * N + p] + T(0.5)));
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T, bool CLUSTER, bool UNIFORM_T, bool FIELD>
 __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
 {
     using V = typename C2<T>::type;
@@ -744,10 +789,12 @@ __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
     ptr += 16 * ((4 * twoN + 15) / 16);
     T *s_diag = reinterpret_cast<T *>(ptr);
     ptr += 16 * ((sizeof(T) * 2 * S * twoN + 15) / 16);
-    T *s_amp = nullptr;
-    if constexpr (DRIVE) {
-        s_amp = reinterpret_cast<T *>(ptr);
+    T *s_amp = nullptr, *s_field = nullptr;
+    if constexpr (FIELD) {
+        s_amp = reinterpret_cast<T *>(ptr);                   // [2N]
         ptr += 16 * ((sizeof(T) * twoN + 15) / 16);
+        s_field = reinterpret_cast<T *>(ptr);                 // [S][2N]
+        ptr += 16 * ((sizeof(T) * S * twoN + 15) / 16);
     }
     const uint32_t bufA_s = smem_addr(ptr);
     const uint32_t diag_s = smem_addr(s_diag);
@@ -768,8 +815,8 @@ __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
         s_nbr[i] = a.nbr[i];
         for (int n = 0; n < 4; ++n) s_t[4 * i + n] = a.tnb[4 * i + n];
     }
-    if constexpr (DRIVE)
-        for (int i = threadIdx.x; i < twoN; i += blockDim.x) s_amp[i] = a.amp[i];
+    if constexpr (FIELD)
+        for (int i = threadIdx.x; i < twoN; i += blockDim.x) s_amp[i] = a.amp ? a.amp[i] : T(0);
     // row bases: element (p, k) of spin-row sr (slot 0, buffer A) at base + k * SZ
     for (int sr = threadIdx.x; sr < twoN; sr += blockDim.x) {
         int owner = 0;
@@ -884,26 +931,31 @@ __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
             const bool snap_now = a.snap && ((step + 1) % a.out_every == 0);
             const long long snap_row = (step + 1) / a.out_every;
             T fd[4] = {T(0), T(0), T(0), T(0)};
-            if constexpr (DRIVE)
-                for (int k = 0; k < 4; ++k) fd[k] = a.ftab[4 * step + k];
-            band_stage<0, T, CLUSTER, UNIFORM_T, DRIVE>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag,
+            if constexpr (FIELD)
+                if (a.ftab)
+                    for (int k = 0; k < 4; ++k) fd[k] = a.ftab[4 * step + k];
+            if constexpr (FIELD) diag_field<T>(a, s_diag + (0 & 1) * diag_stride, s_amp, fd[0], s_field);
+            band_stage<0, T, CLUSTER, UNIFORM_T, FIELD>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag,
                                                         diag_s, lane, t_state, eps_bytes, diag_stride, b, snap_now,
-                                                        snap_row, s_amp, fd[0]);
+                                                        snap_row, s_field);
             tmem_wait_st();
             if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
-            band_stage<1, T, CLUSTER, UNIFORM_T, DRIVE>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag,
+            if constexpr (FIELD) diag_field<T>(a, s_diag + (1 & 1) * diag_stride, s_amp, fd[1], s_field);
+            band_stage<1, T, CLUSTER, UNIFORM_T, FIELD>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag,
                                                         diag_s, lane, t_state, eps_bytes, diag_stride, b, snap_now,
-                                                        snap_row, s_amp, fd[1]);
+                                                        snap_row, s_field);
             tmem_wait_st();
             if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
-            band_stage<2, T, CLUSTER, UNIFORM_T, DRIVE>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag,
+            if constexpr (FIELD) diag_field<T>(a, s_diag + (2 & 1) * diag_stride, s_amp, fd[2], s_field);
+            band_stage<2, T, CLUSTER, UNIFORM_T, FIELD>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag,
                                                         diag_s, lane, t_state, eps_bytes, diag_stride, b, snap_now,
-                                                        snap_row, s_amp, fd[2]);
+                                                        snap_row, s_field);
             tmem_wait_st();
             if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
-            band_stage<3, T, CLUSTER, UNIFORM_T, DRIVE>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag,
+            if constexpr (FIELD) diag_field<T>(a, s_diag + (3 & 1) * diag_stride, s_amp, fd[3], s_field);
+            band_stage<3, T, CLUSTER, UNIFORM_T, FIELD>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag,
                                                         diag_s, lane, t_state, eps_bytes, diag_stride, b, snap_now,
-                                                        snap_row, s_amp, fd[3]);
+                                                        snap_row, s_field);
             tmem_wait_st();
             if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
         }
@@ -1179,12 +1231,12 @@ static bool band_items(int N, int S, int rb0, int rb1, int e_cap, int R, std::ve
     return true;
 }
 
-static int band_smem(int N, int S, int real_bytes, int buf_bytes, bool drive)
+static int band_smem(int N, int S, int real_bytes, int buf_bytes, bool field)
 {
     auto r16 = [](int x) { return 16 * ((x + 15) / 16); };
     int b = 64 + (int)sizeof(BandRow) * 2 * N + r16(4 * N) + r16(real_bytes * 4 * N) + r16(4 * 2 * N);
     b += r16(real_bytes * 2 * S * 2 * N);
-    if (drive) b += r16(real_bytes * 2 * N);
+    if (field) b += r16(real_bytes * 2 * N) + r16(real_bytes * S * 2 * N);
     return b + 2 * buf_bytes;
 }
 
@@ -1232,7 +1284,7 @@ int choose_band_shape(Plan *p, int64_t M, BandShape *out)
         int bestE = 0, bestK = 0;
         for (int S = 1; S <= want; ++S) {
             const int buf = ((S * eps_max * SZ + 15) / 16) * 16;
-            if (band_smem(N, S, real_bytes, buf, p->drive) > max_smem) break;
+            if (band_smem(N, S, real_bytes, buf, p->drive || p->longrange) > max_smem) break;
             std::vector<std::vector<uint32_t>> its(C);
             int E = 0, K = 0;
             bool ok = true;
@@ -1268,7 +1320,7 @@ int choose_band_shape(Plan *p, int64_t M, BandShape *out)
                     sh.items[((size_t)r * kWarps + w) * bestK + i] = best_items[r][(size_t)w * Kr + i];
         }
         sh.buf_bytes = ((best * eps_max * SZ + 15) / 16) * 16;
-        sh.smem_bytes = std::max(kMinSmem, band_smem(N, best, real_bytes, sh.buf_bytes, p->drive));
+        sh.smem_bytes = std::max(kMinSmem, band_smem(N, best, real_bytes, sh.buf_bytes, p->drive || p->longrange));
         const long long batches = (M + best - 1) / best;
         sh.grid = (int)std::min<long long>(std::max<long long>(batches, 1), std::max(1, sm / C)) * C;
         *out = sh;
@@ -1277,10 +1329,10 @@ int choose_band_shape(Plan *p, int64_t M, BandShape *out)
     return FTWA_ERR_UNSUPPORTED;
 }
 
-template <typename T, bool CLUSTER, bool UNIFORM_T, bool DRIVE>
+template <typename T, bool CLUSTER, bool UNIFORM_T, bool FIELD>
 static int band_launch(Plan *p, BandShape &sh, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s)
 {
-    auto kern = band_stepper<T, CLUSTER, UNIFORM_T, DRIVE>;
+    auto kern = band_stepper<T, CLUSTER, UNIFORM_T, FIELD>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem_bytes);
     if (e != cudaSuccess) return set_cuda_error(e);
     cudaLaunchConfig_t cfg{};
@@ -1342,11 +1394,10 @@ static int band_launch(Plan *p, BandShape &sh, void *rho, int64_t M, int64_t n_s
     a.k_items = sh.k_items;
     a.buf_bytes = sh.buf_bytes;
     a.qoff = sh.qoff;
-    a.amp = nullptr;
-    if (DRIVE)
-        a.amp = std::is_same<T, double>::value ? reinterpret_cast<const T *>(p->d_amp64)
-                                               : reinterpret_cast<const T *>(p->d_amp32);
-    a.ftab = DRIVE ? reinterpret_cast<const T *>(p->d_ftab) : nullptr;
+    const bool f64 = std::is_same<T, double>::value;
+    a.amp = p->drive ? reinterpret_cast<const T *>(f64 ? (const void *)p->d_amp64 : (const void *)p->d_amp32) : nullptr;
+    a.ftab = p->drive ? reinterpret_cast<const T *>(p->d_ftab) : nullptr;
+    a.u = p->longrange ? reinterpret_cast<const T *>(f64 ? (const void *)p->d_u64 : (const void *)p->d_u32) : nullptr;
     for (int i = 0; i <= kMaxCluster; ++i) a.row_begin[i] = sh.row_begin[i];
     a.items = p->d_items;
     a.M = M;
@@ -1361,21 +1412,21 @@ static int band_launch(Plan *p, BandShape &sh, void *rho, int64_t M, int64_t n_s
     return set_cuda_error(e);
 }
 
-template <typename T, bool DRIVE>
+template <typename T, bool FIELD>
 static int band_dispatch_d(Plan *p, BandShape &sh, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s)
 {
     if (sh.cluster > 1)
-        return p->uniform_t ? band_launch<T, true, true, DRIVE>(p, sh, rho, M, n_steps, snap, s)
-                            : band_launch<T, true, false, DRIVE>(p, sh, rho, M, n_steps, snap, s);
-    return p->uniform_t ? band_launch<T, false, true, DRIVE>(p, sh, rho, M, n_steps, snap, s)
-                        : band_launch<T, false, false, DRIVE>(p, sh, rho, M, n_steps, snap, s);
+        return p->uniform_t ? band_launch<T, true, true, FIELD>(p, sh, rho, M, n_steps, snap, s)
+                            : band_launch<T, true, false, FIELD>(p, sh, rho, M, n_steps, snap, s);
+    return p->uniform_t ? band_launch<T, false, true, FIELD>(p, sh, rho, M, n_steps, snap, s)
+                        : band_launch<T, false, false, FIELD>(p, sh, rho, M, n_steps, snap, s);
 }
 
 template <typename T>
 static int band_dispatch(Plan *p, BandShape &sh, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s)
 {
-    return p->drive ? band_dispatch_d<T, true>(p, sh, rho, M, n_steps, snap, s)
-                    : band_dispatch_d<T, false>(p, sh, rho, M, n_steps, snap, s);
+    return (p->drive || p->longrange) ? band_dispatch_d<T, true>(p, sh, rho, M, n_steps, snap, s)
+                                      : band_dispatch_d<T, false>(p, sh, rho, M, n_steps, snap, s);
 }
 
 // pulse values f(t) of the on-site drive at the four RK4 stage times of every
@@ -1420,12 +1471,13 @@ static int prepare_drive(Plan *p, int64_t n_steps, double t_start, cudaStream_t 
 
 int launch_evolve(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s, double t_start)
 {
-    if (p->drive) {
-        // the time-dependent drive runs on the banded stepper (both precisions)
+    if (p->drive || p->longrange) {
+        // the tabulated diagonal field (drive, long-range u) runs on the
+        // banded stepper (both precisions)
         BandShape bs;
         int rc = choose_band_shape(p, M, &bs);
         if (rc != FTWA_OK) return rc;
-        if (M > 0 && !p->dry_run) {
+        if (p->drive && M > 0 && !p->dry_run) {
             rc = prepare_drive(p, n_steps, t_start, s);
             if (rc != FTWA_OK) return rc;
         }

@@ -87,6 +87,10 @@ struct Plan {
     float *d_amp32 = nullptr;         // [2][N]
     void *d_ftab = nullptr;           // [n_steps][4] pulse values of the last evolve call
     size_t ftab_bytes = 0;
+    // long-range interaction u_ij of Eq. 1 (replaces the on-site U)
+    bool longrange = false;
+    double *d_u64 = nullptr;          // [N][N]
+    float *d_u32 = nullptr;           // [N][N]
 };
 
 int set_cuda_error(cudaError_t e);
@@ -102,6 +106,7 @@ int launch_philox(uint64_t seed, int64_t m, int32_t spin, int64_t p0, int64_t co
 int launch_evolve(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s,
                  double t_start = 0.0);
 void free_drive(Plan *p);
+void free_interaction(Plan *p);
 int choose_stepper_shape(Plan *p, int64_t M, StepperShape *out);
 int choose_band_shape(Plan *p, int64_t M, BandShape *out);
 int launch_moments(Plan *p, const void *snap, int64_t M, int32_t T, double *occ, double *conn, double *g2,

@@ -32,6 +32,15 @@ void free_drive(Plan *p)
     p->drive = false;
 }
 
+void free_interaction(Plan *p)
+{
+    cudaFree(p->d_u64);
+    cudaFree(p->d_u32);
+    p->d_u64 = nullptr;
+    p->d_u32 = nullptr;
+    p->longrange = false;
+}
+
 static void free_tables(Plan *p)
 {
     cudaFree(p->d_nbr);
@@ -46,6 +55,7 @@ static void free_tables(Plan *p)
     cudaFree(p->d_adj_ws);
     free_basis(p);
     free_drive(p);
+    free_interaction(p);
     p->d_adj_ws = nullptr;
     p->adj_ws_bytes = 0;
     p->d_items = nullptr;
@@ -374,6 +384,38 @@ int ftwa_evolve_at(ftwa_plan_t *p, void *rho_dev, int64_t M, int64_t n_steps, do
     if (!p || M < 0 || n_steps < 0 || (M > 0 && !rho_dev) || !std::isfinite(t_start))
         return FTWA_ERR_INVALID_ARGUMENT;
     return launch_evolve(p, rho_dev, M, n_steps, snap_dev, static_cast<cudaStream_t>(stream), t_start);
+}
+
+int ftwa_set_interaction(ftwa_plan_t *p, const double *u)
+{
+    if (!p) return FTWA_ERR_INVALID_ARGUMENT;
+    if (!u) {
+        free_interaction(p);
+        return FTWA_OK;
+    }
+    const int N = p->N;
+    double scale = 0.0;
+    for (size_t k = 0; k < (size_t)N * N; ++k) {
+        if (!std::isfinite(u[k])) return FTWA_ERR_INVALID_ARGUMENT;
+        scale = std::max(scale, std::fabs(u[k]));
+    }
+    for (int i = 0; i < N; ++i)
+        for (int j = i + 1; j < N; ++j)
+            if (std::fabs(u[(size_t)i * N + j] - u[(size_t)j * N + i]) > 1e-12 * std::max(scale, 1.0))
+                return FTWA_ERR_INVALID_ARGUMENT;
+    free_interaction(p);
+    const size_t n = (size_t)N * N;
+    std::vector<float> u32(u, u + n);
+    cudaError_t e = cudaMalloc(&p->d_u64, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_u64, u, sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_u32, sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_u32, u32.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_interaction(p);
+        return set_cuda_error(e);
+    }
+    p->longrange = true;
+    return FTWA_OK;
 }
 
 int ftwa_set_drive(ftwa_plan_t *p, const double *amp, double t0, double sigma, double omega, double phase)

@@ -73,9 +73,10 @@ def test_drive_fp32_parity_198(ftwa):
 
 
 def test_drive_neutral_and_unsupported(ftwa):
-    """A zero-amplitude drive reproduces the undriven stepper bit for bit;
-    removing the drive restores it; evolve_at without a drive ignores the
-    start time; the adjoint and CUDA-graph batches refuse a driven plan."""
+    """A zero-amplitude drive reproduces the undriven stepper (to rounding:
+    the driven stepper tabulates the diagonal field); removing the drive
+    restores it bit for bit; evolve_at without a drive ignores the start time;
+    the adjoint and CUDA-graph batches refuse a driven plan."""
     lat = W.hexagon_chain(2)
     nu, nd = W.neel_state(lat)
     with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=0, out_every=10, variant=1) as P:
@@ -87,7 +88,7 @@ def test_drive_neutral_and_unsupported(ftwa):
         P.set_drive(np.zeros((2, lat.n_sites)), 1.0, 0.4, 4.0, 0.3)
         r2 = P.sample(3, 4)
         P.evolve(r2, 120, snap=None, t_start=0.5)
-        assert torch.equal(r2, ref)
+        assert _rel(r2.cpu().numpy(), ref.cpu().numpy()) <= 1e-12
         P.set_drive(_drive(lat.n_sites)["amp"], 1.0, 0.4, 4.0, 0.3)
         r3 = P.sample(3, 4)
         P.evolve(r3, 120, snap=None)

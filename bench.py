@@ -329,6 +329,44 @@ def bench_drive(F, args):
     return out
 
 
+def bench_ed(F, args):
+    """GPU exact diagonalisation (Sec. 8(f) fourth extension): the 16-site
+    brick-wall flake (4 x 4) at half filling, N_up = N_dn = 8 (basis
+    12870^2 = 1.66e8 determinants), Neel start, U/t = 1.6, propagated to
+    T = 1 in 10 Chebyshev intervals with <n> and <n n> at every interval."""
+    import numpy as np
+    import torch
+    from scipy.special import jv
+    import workloads as W
+    lat = W.brick_wall_flake(4, 4)
+    nu, nd = W.neel_state(lat)
+    G = F.ED(lat, 1.6, int(nu.sum()), int(nd.sum()))
+    dim, a_sp, _ = G.info()
+    dt, n_out = 0.1, 10
+    G.evolve(nu, nd, dt, 1)              # warm-up
+    torch.cuda.synchronize()
+    a, b = _events()
+    a.record()
+    occ, _ = G.evolve(nu, nd, dt, n_out)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    G.close()
+    x = a_sp * dt                        # Chebyshev terms per interval, the library's rule
+    k = 0
+    while not (k > x + 10 and abs(jv(k, x)) < 1e-17):
+        k += 1
+    terms = k * n_out
+    bytes_per_term = 80.0 * dim          # read T_k, T_k-1, acc; write T_k+1, acc (complex128)
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6784.5)
+    gbs = bytes_per_term * terms / (ms / 1000.0) / 1e9
+    return {"workload": "16-site brick-wall flake, N_up = N_dn = 8, U/t = 1.6, T = 1 (10 intervals of 0.1)",
+            "dim": dim, "ms": ms, "chebyshev_terms": terms, "ms_per_term": ms / terms,
+            "achieved_gbs": gbs, "hbm_peak_gbs": hbm, "frac_of_hbm_peak": gbs / hbm,
+            "occ_sum_check": float(occ[-1].sum().item())}
+
+
 def bench_batched(F, args):
     """Config 3: honeycomb flakes of 24, 54, 96, 150 and 198 sites x U/t in
     {0.5, 1.0, 1.6, 2.5}, M samples each, FP32 state, one CUDA-graph launch
@@ -558,6 +596,8 @@ def run_gpu(args):
         extra["general_state"] = bench_general(F, args)
     if not args.no_drive:
         extra["drive"] = bench_drive(F, args)
+    if not args.no_ed:
+        extra["ed"] = bench_ed(F, args)
 
     # ---- roofline of the dominant kernel (the RK4 stepper) -----------------------
     pk = peaks()
@@ -657,6 +697,7 @@ def main():
     ap.add_argument("--no-gram", action="store_true")
     ap.add_argument("--no-general", action="store_true")
     ap.add_argument("--no-drive", action="store_true")
+    ap.add_argument("--no-ed", action="store_true")
     ap.add_argument("--drive-samples", type=int, default=4096)
     ap.add_argument("--drive-steps", type=int, default=200)
     ap.add_argument("--general-samples", type=int, default=4096)

@@ -310,6 +310,34 @@ int ftwa_batch_launch(ftwa_batch_t *batch, void *stream);
 /* Release a batch (NULL is accepted). */
 void ftwa_batch_destroy(ftwa_batch_t *batch);
 
+/* Exact diagonalisation on the GPU (Sec. III.A and App. B, the paper's
+ * reference method, for lattices of up to 24 sites): the state of Eq. 1 in
+ * the basis of Slater determinants with fixed N_up, N_dn, propagated by
+ * psi(t) = exp(-iHt) psi(0) (Schroedinger form) with a Chebyshev expansion
+ * (truncated where the Bessel coefficients fall below 1e-17) over intervals
+ * dt_out.  ftwa_ed_plan builds the hopping matrices of both species (CSR,
+ * fermionic signs for spin-up orbitals ordered before spin-down ones, same
+ * species counted between the two sites) and allocates four state vectors
+ * (16 dim bytes each, dim = C(N, N_up) C(N, N_dn)).  Errors:
+ * FTWA_ERR_INVALID_ARGUMENT, FTWA_ERR_UNSUPPORTED (N > 24),
+ * FTWA_ERR_OUT_OF_MEMORY, FTWA_ERR_CUDA. */
+typedef struct ftwa_ed ftwa_ed_t;
+int ftwa_ed_plan(const ftwa_lattice *lattice, double U, int32_t n_up, int32_t n_dn, ftwa_ed_t **out);
+void ftwa_ed_destroy(ftwa_ed_t *ed);
+/* Basis size and the spectral map H~ = (H - b) / a of the Chebyshev series
+ * (a, b may be NULL). */
+int ftwa_ed_info(const ftwa_ed_t *ed, int64_t *dim, double *spectral_a, double *spectral_b);
+
+/* Propagate the Fock state given by host occupations n_up, n_dn ([N], 0 or
+ * 1, counts N_up, N_dn) and record, at t = k dt_out for k = 0 .. n_out,
+ * occ_dev[k][s N + i] = <n_i,s> and (if nn_dev is not NULL)
+ * nn_dev[k][a][b] = <n_a n_b> over the 2N site-spins a, b (device doubles;
+ * the a = b entries hold <n_a>).  Asynchronous on `stream`; the plan's state
+ * vectors are reused, so calls on one plan must not overlap.  Errors:
+ * FTWA_ERR_INVALID_ARGUMENT, FTWA_ERR_CUDA. */
+int ftwa_ed_evolve(ftwa_ed_t *ed, const double *n_up, const double *n_dn, double dt_out, int32_t n_out,
+                   double *occ_dev, double *nn_dev, void *stream);
+
 /* Synchronise `stream`, then return and clear the plan's device status word
  * (FTWA_OK, FTWA_ERR_DEVICE_TIMEOUT or FTWA_ERR_NONFINITE), or FTWA_ERR_CUDA
  * if the synchronisation itself failed. */

@@ -208,6 +208,54 @@ def plan(lattice, U, **kw) -> Plan:
     return Plan(lattice, U, **kw)
 
 
+class ED:
+    """Exact diagonalisation on the GPU (ftwa_ed_*): the Hubbard model of a
+    small lattice with fixed N_up, N_dn, propagated from a Fock state."""
+
+    def __init__(self, lattice, U, n_up, n_dn):
+        import numpy as np
+        self.N = lattice.n_sites
+        bonds = np.ascontiguousarray(lattice.bonds, dtype=np.int32)
+        tb = np.ascontiguousarray(lattice.t_bond, dtype=np.float64)
+        self._keep = (bonds, tb)
+        lat = _lib.Lattice(self.N, int(bonds.shape[0]), ctypes.c_void_p(bonds.ctypes.data),
+                           ctypes.c_void_p(tb.ctypes.data))
+        h = ctypes.c_void_p()
+        check(load().ftwa_ed_plan(ctypes.byref(lat), float(U), int(n_up), int(n_dn), ctypes.byref(h)), "ftwa_ed_plan")
+        self._h = h
+
+    def info(self):
+        """(basis size, a, b) with H~ = (H - b) / a the Chebyshev map."""
+        d, a, b = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        check(load().ftwa_ed_info(self._h, ctypes.byref(d), ctypes.cast(ctypes.byref(a), ctypes.c_void_p),
+                                  ctypes.cast(ctypes.byref(b), ctypes.c_void_p)), "ftwa_ed_info")
+        return d.value, a.value, b.value
+
+    def evolve(self, n_up, n_dn, dt_out, n_out, nn=True, stream=None):
+        """(occ [n_out+1, 2N], nn [n_out+1, 2N, 2N] or None), float64 device tensors."""
+        import numpy as np
+        import torch
+        nu = np.ascontiguousarray(n_up, dtype=np.float64)
+        nd = np.ascontiguousarray(n_dn, dtype=np.float64)
+        K = 2 * self.N
+        occ = torch.empty((n_out + 1, K), dtype=torch.float64, device="cuda")
+        mm = torch.empty((n_out + 1, K, K), dtype=torch.float64, device="cuda") if nn else None
+        check(load().ftwa_ed_evolve(self._h, ctypes.c_void_p(nu.ctypes.data), ctypes.c_void_p(nd.ctypes.data),
+                                    float(dt_out), int(n_out), _ptr(occ), _ptr(mm), _stream(stream)), "ftwa_ed_evolve")
+        return occ, mm
+
+    def close(self):
+        if self._h:
+            load().ftwa_ed_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 class Batch:
     """One CUDA graph advancing several plans' samples (ftwa_batch_*)."""
 

@@ -727,30 +727,68 @@ __device__ __forceinline__ void band_stage(unsigned char *smem, const BandArgs<T
 //          = U (Re rho_pp,sbar + 1/2)               (on-site U)
 //          + amp_s,p f(t_stage)                     (time-dependent drive),
 // from the stage's diagonal buffer dg [S][2N]; each CTA of a cluster holds
-// all diagonals and computes the whole table (a warp per row for u).  Ends
-// with a CTA barrier.
-template <typename T>
-__device__ __forceinline__ void diag_field(const BandArgs<T> &a, const T *dg, const T *s_amp, T f, T *s_field)
+// all diagonals.  On-site U: every CTA computes the whole table.  Long-range
+// u: in a cluster the rows are split over the CTAs, each storing its rows
+// into every CTA's table (the caller then meets the cluster barrier), so that
+// u is read from L2 once per cluster and stage.  Ends with a CTA barrier.
+template <typename T, bool CLUSTER>
+__device__ __forceinline__ void diag_field(const BandArgs<T> &a, const T *dg, const T *s_amp, T f, T *s_field,
+                                           uint32_t field_s, uint32_t rank)
 {
     const int N = a.N, twoN = 2 * N;
     if (a.u) {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
-        for (int r = warp; r < a.S * N; r += n_warps) {
-            const int slot = r / N, p = r % N;
-            const T *d = dg + slot * twoN;
-            T up = T(0), dn = T(0);        // fields of spin up (from dn density) and spin dn
+        // warp w takes rows r = w, w + n_warps, ... (r = slot * N + p) four at
+        // a time: lanes over k (coalesced rows of u), eight independent
+        // accumulators, one shuffle reduction per group of four rows
+        constexpr int RG = 4;
+        const int lane = threadIdx.x & 31;
+        const int warp = (CLUSTER ? (int)rank * (int)(blockDim.x >> 5) : 0) + (int)(threadIdx.x >> 5);
+        const int n_warps = (CLUSTER ? a.C : 1) * (int)(blockDim.x >> 5);
+        const int rows = a.S * N;
+        for (int r0 = warp; r0 < rows; r0 += RG * n_warps) {
+            T up[RG], dn[RG];
+            int rr[RG];
+#pragma unroll
+            for (int g = 0; g < RG; ++g) {
+                rr[g] = r0 + g * n_warps;
+                up[g] = T(0);
+                dn[g] = T(0);
+            }
             for (int k = lane; k < N; k += 32) {
-                const T u = a.u[(size_t)p * N + k];
-                up = fma(u, d[N + k] + T(0.5), up);
-                dn = fma(u, d[k] + T(0.5), dn);
+#pragma unroll
+                for (int g = 0; g < RG; ++g) {
+                    const int r = rr[g] < rows ? rr[g] : rows - 1;
+                    const int slot = r / N, p = r % N;
+                    const T *d = dg + slot * twoN;
+                    const T u = a.u[(size_t)p * N + k];
+                    up[g] = fma(u, d[N + k] + T(0.5), up[g]);   // spin up feels the dn density
+                    dn[g] = fma(u, d[k] + T(0.5), dn[g]);
+                }
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                up += __shfl_xor_sync(0xffffffffu, up, o);
-                dn += __shfl_xor_sync(0xffffffffu, dn, o);
-            }
+#pragma unroll
+            for (int g = 0; g < RG; ++g)
+                for (int o = 16; o > 0; o >>= 1) {
+                    up[g] += __shfl_xor_sync(0xffffffffu, up[g], o);
+                    dn[g] += __shfl_xor_sync(0xffffffffu, dn[g], o);
+                }
             if (lane == 0) {
-                s_field[slot * twoN + p] = fma(s_amp[p], f, up);
-                s_field[slot * twoN + N + p] = fma(s_amp[N + p], f, dn);
+#pragma unroll
+                for (int g = 0; g < RG; ++g) {
+                    if (rr[g] >= rows) continue;
+                    const int slot = rr[g] / N, p = rr[g] % N;
+                    const T vu = fma(s_amp[p], f, up[g]), vd = fma(s_amp[N + p], f, dn[g]);
+                    if constexpr (CLUSTER) {
+                        const uint32_t au = field_s + (uint32_t)((slot * twoN + p) * (int)sizeof(T));
+                        const uint32_t ad = field_s + (uint32_t)((slot * twoN + N + p) * (int)sizeof(T));
+                        for (int c = 0; c < a.C; ++c) {
+                            stc1(map_rank(au, (uint32_t)c), vu);
+                            stc1(map_rank(ad, (uint32_t)c), vd);
+                        }
+                    } else {
+                        s_field[slot * twoN + p] = vu;
+                        s_field[slot * twoN + N + p] = vd;
+                    }
+                }
             }
         }
     } else {
@@ -798,6 +836,7 @@ __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
     }
     const uint32_t bufA_s = smem_addr(ptr);
     const uint32_t diag_s = smem_addr(s_diag);
+    const uint32_t field_s = FIELD ? smem_addr(s_field) : 0u;
     const int diag_stride = S * twoN;
 
     const int rb0 = a.row_begin[rank], rb1 = a.row_begin[rank + 1];
@@ -934,25 +973,37 @@ __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
             if constexpr (FIELD)
                 if (a.ftab)
                     for (int k = 0; k < 4; ++k) fd[k] = a.ftab[4 * step + k];
-            if constexpr (FIELD) diag_field<T>(a, s_diag + (0 & 1) * diag_stride, s_amp, fd[0], s_field);
+            if constexpr (FIELD) {
+                diag_field<T, CLUSTER>(a, s_diag + (0 & 1) * diag_stride, s_amp, fd[0], s_field, field_s, rank);
+                if (CLUSTER && a.u && !stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
+            }
             band_stage<0, T, CLUSTER, UNIFORM_T, FIELD>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag,
                                                         diag_s, lane, t_state, eps_bytes, diag_stride, b, snap_now,
                                                         snap_row, s_field);
             tmem_wait_st();
             if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
-            if constexpr (FIELD) diag_field<T>(a, s_diag + (1 & 1) * diag_stride, s_amp, fd[1], s_field);
+            if constexpr (FIELD) {
+                diag_field<T, CLUSTER>(a, s_diag + (1 & 1) * diag_stride, s_amp, fd[1], s_field, field_s, rank);
+                if (CLUSTER && a.u && !stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
+            }
             band_stage<1, T, CLUSTER, UNIFORM_T, FIELD>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag,
                                                         diag_s, lane, t_state, eps_bytes, diag_stride, b, snap_now,
                                                         snap_row, s_field);
             tmem_wait_st();
             if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
-            if constexpr (FIELD) diag_field<T>(a, s_diag + (2 & 1) * diag_stride, s_amp, fd[2], s_field);
+            if constexpr (FIELD) {
+                diag_field<T, CLUSTER>(a, s_diag + (2 & 1) * diag_stride, s_amp, fd[2], s_field, field_s, rank);
+                if (CLUSTER && a.u && !stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
+            }
             band_stage<2, T, CLUSTER, UNIFORM_T, FIELD>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag,
                                                         diag_s, lane, t_state, eps_bytes, diag_stride, b, snap_now,
                                                         snap_row, s_field);
             tmem_wait_st();
             if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
-            if constexpr (FIELD) diag_field<T>(a, s_diag + (3 & 1) * diag_stride, s_amp, fd[3], s_field);
+            if constexpr (FIELD) {
+                diag_field<T, CLUSTER>(a, s_diag + (3 & 1) * diag_stride, s_amp, fd[3], s_field, field_s, rank);
+                if (CLUSTER && a.u && !stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
+            }
             band_stage<3, T, CLUSTER, UNIFORM_T, FIELD>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag,
                                                         diag_s, lane, t_state, eps_bytes, diag_stride, b, snap_now,
                                                         snap_row, s_field);

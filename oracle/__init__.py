@@ -56,7 +56,8 @@ def _load():
             lib.orc_rhs.argtypes = [i32, i32, P, P, f64, P, P]
             lib.orc_evolve.argtypes = [i32, i32, P, P, f64, f64, i64, i64, P, P]
             lib.orc_evolve_longrange.argtypes = [i32, i32, P, P, P, f64, i64, i64, P, P]
-            lib.orc_evolve_drive.argtypes = [i32, i32, P, P, f64, f64, i64, i64, P, P, P, f64, f64, f64, f64, f64]
+            lib.orc_evolve_drive.argtypes = [i32, i32, P, P, f64, f64, i64, i64, P, P, P, f64, f64, f64, f64, f64,
+                                             f64, f64, f64, f64, f64]
             lib.orc_run.argtypes = [i32, i32, P, P, f64, P, P, u64, i64, i64, f64, i64, i64, P, P, i32]
             lib.orc_run.restype = ctypes.c_int
             lib.orc_energy.argtypes = [i32, i32, P, P, f64, P, P]
@@ -136,7 +137,9 @@ def evolve(lat, U, rho0, dt, n_steps, out_every=0, t_bond=None, drive=None, t_st
 
     drive: optional time-dependent on-site potential v_i,s(t) = amp[s][i] f(t),
     f(t) = exp(-(t - t0)^2 / (2 sigma^2)) cos(omega (t - t0) + phase), given as
-    dict(amp=[2, N], t0=, sigma=, omega=, phase=); t_start is the time of rho0.
+    dict(amp=[2, N], t0=, sigma=, omega=, phase=) (amp may be None), optionally
+    with hop=dict(eps=, t0=, sigma=, omega=, phase=): every hopping scaled by
+    m(t) = 1 + eps g(t), g the same pulse shape; t_start is the time of rho0.
     u: optional symmetric interaction matrix [N, N] of Eq. 1 (replaces U)."""
     lib = _load()
     b, t = _lat_arrays(lat, t_bond)
@@ -153,10 +156,14 @@ def evolve(lat, U, rho0, dt, n_steps, out_every=0, t_bond=None, drive=None, t_st
     elif drive is None:
         lib.orc_evolve(lat.n_sites, lat.n_bonds, _p(b), _p(t), U, dt, n_steps, out_every, _p(r), _p(snap))
     else:
-        amp = np.ascontiguousarray(drive["amp"], dtype=np.float64).reshape(2, lat.n_sites)
+        amp = drive.get("amp")
+        amp = None if amp is None else np.ascontiguousarray(amp, dtype=np.float64).reshape(2, lat.n_sites)
+        hop = drive.get("hop") or {}
         lib.orc_evolve_drive(lat.n_sites, lat.n_bonds, _p(b), _p(t), U, dt, n_steps, out_every, _p(r), _p(snap),
-                             _p(amp), float(t_start), float(drive["t0"]), float(drive["sigma"]),
-                             float(drive["omega"]), float(drive["phase"]))
+                             _p(amp), float(t_start), float(drive.get("t0", 0.0)), float(drive.get("sigma", 0.0)),
+                             float(drive.get("omega", 0.0)), float(drive.get("phase", 0.0)),
+                             float(hop.get("eps", 0.0)), float(hop.get("t0", 0.0)), float(hop.get("sigma", 0.0)),
+                             float(hop.get("omega", 0.0)), float(hop.get("phase", 0.0)))
     return r, snap
 
 

@@ -180,7 +180,7 @@ static void free_adjacency(adjacency *a)
  *                            + (u_ki - u_kj)(rho_kk,sbar + 1/2) rho_ij,s )
  * With u_ij = U delta_ij the k-sum of the interaction term reduces to
  * U [(rho_ii,sbar + 1/2) - (rho_jj,sbar + 1/2)]. */
-static void rhs(const adjacency *a, double U, const cplx *rho, cplx *f)
+static void rhs(const adjacency *a, double U, double hs, const cplx *rho, cplx *f)
 {
     const int N = a->N;
     for (int s = 0; s < 2; ++s) {
@@ -194,6 +194,7 @@ static void rhs(const adjacency *a, double U, const cplx *rho, cplx *f)
                     acc += a->hop[e] * r[(size_t)i * N + a->nbr[e]];
                 for (int e = a->start[i]; e < a->start[i + 1]; ++e)       /* j_ki rho_kj */
                     acc -= a->hop[e] * r[(size_t)a->nbr[e] * N + j];
+                acc *= hs;                                                /* hopping scale m(t) */
                 cplx ui = U * (rb[(size_t)i * N + i] + 0.5);
                 cplx uj = U * (rb[(size_t)j * N + j] + 0.5);
                 acc += (ui - uj) * r[(size_t)i * N + j];
@@ -210,12 +211,23 @@ static void rhs(const adjacency *a, double U, const cplx *rho, cplx *f)
 typedef struct {
     const double *amp;   /* [2][N] or NULL */
     double t0, sigma, omega, phase;
+    /* hopping modulation j_ij(t) = j_ij m(t), m(t) = 1 + eps g(t) with g the
+     * same pulse shape and its own parameters (eps = 0: none) */
+    double hop_eps, hop_t0, hop_sigma, hop_omega, hop_phase;
 } drive;
 
-static double drive_f(const drive *d, double t)
+static double pulse(double t, double t0, double sigma, double omega, double phase)
 {
-    const double env = d->sigma > 0.0 ? exp(-(t - d->t0) * (t - d->t0) / (2.0 * d->sigma * d->sigma)) : 1.0;
-    return env * cos(d->omega * (t - d->t0) + d->phase);
+    const double env = sigma > 0.0 ? exp(-(t - t0) * (t - t0) / (2.0 * sigma * sigma)) : 1.0;
+    return env * cos(omega * (t - t0) + phase);
+}
+
+static double drive_f(const drive *d, double t) { return pulse(t, d->t0, d->sigma, d->omega, d->phase); }
+
+static double hop_scale(const drive *d, double t)
+{
+    if (!d || d->hop_eps == 0.0) return 1.0;
+    return 1.0 + d->hop_eps * pulse(t, d->hop_t0, d->hop_sigma, d->hop_omega, d->hop_phase);
 }
 
 static void add_drive(int N, const drive *d, double t, const cplx *rho, cplx *f)
@@ -290,7 +302,7 @@ void orc_rhs(int32_t N, int32_t B, const int32_t *bonds, const double *t_bond, d
              const double *rho, double *f)
 {
     adjacency a = build_adjacency(N, B, bonds, t_bond);
-    rhs(&a, U, (const cplx *)rho, (cplx *)f);
+    rhs(&a, U, 1.0, (const cplx *)rho, (cplx *)f);
     free_adjacency(&a);
 }
 
@@ -300,16 +312,16 @@ static void rk4_step(const adjacency *a, double U, double dt, cplx *y, cplx *k, 
                      const drive *d, double t)
 {
     const size_t n = 2 * (size_t)a->N * a->N;
-    rhs(a, U, y, k);                                         /* k1 = f(t, y) */
+    rhs(a, U, hop_scale(d, t), y, k);                        /* k1 = f(t, y) */
     add_drive(a->N, d, t, y, k);
     for (size_t e = 0; e < n; ++e) { acc[e] = k[e]; ys[e] = y[e] + 0.5 * dt * k[e]; }
-    rhs(a, U, ys, k);                                        /* k2 = f(t + dt/2, y + dt/2 k1) */
+    rhs(a, U, hop_scale(d, t + 0.5 * dt), ys, k);            /* k2 = f(t + dt/2, y + dt/2 k1) */
     add_drive(a->N, d, t + 0.5 * dt, ys, k);
     for (size_t e = 0; e < n; ++e) { acc[e] += 2.0 * k[e]; ys[e] = y[e] + 0.5 * dt * k[e]; }
-    rhs(a, U, ys, k);                                        /* k3 = f(t + dt/2, y + dt/2 k2) */
+    rhs(a, U, hop_scale(d, t + 0.5 * dt), ys, k);            /* k3 = f(t + dt/2, y + dt/2 k2) */
     add_drive(a->N, d, t + 0.5 * dt, ys, k);
     for (size_t e = 0; e < n; ++e) { acc[e] += 2.0 * k[e]; ys[e] = y[e] + dt * k[e]; }
-    rhs(a, U, ys, k);                                        /* k4 = f(t + dt, y + dt k3) */
+    rhs(a, U, hop_scale(d, t + dt), ys, k);                  /* k4 = f(t + dt, y + dt k3) */
     add_drive(a->N, d, t + dt, ys, k);
     for (size_t e = 0; e < n; ++e) y[e] += dt / 6.0 * (acc[e] + k[e]);
 }
@@ -347,10 +359,11 @@ void orc_evolve(int32_t N, int32_t B, const int32_t *bonds, const double *t_bond
 /* orc_evolve with the time-dependent on-site drive, from time t_start. */
 void orc_evolve_drive(int32_t N, int32_t B, const int32_t *bonds, const double *t_bond, double U, double dt,
                       int64_t n_steps, int64_t out_every, double *rho, double *snap, const double *amp,
-                      double t_start, double t0, double sigma, double omega, double phase)
+                      double t_start, double t0, double sigma, double omega, double phase, double hop_eps,
+                      double hop_t0, double hop_sigma, double hop_omega, double hop_phase)
 {
     adjacency a = build_adjacency(N, B, bonds, t_bond);
-    drive d = {amp, t0, sigma, omega, phase};
+    drive d = {amp, t0, sigma, omega, phase, hop_eps, hop_t0, hop_sigma, hop_omega, hop_phase};
     evolve_one(&a, U, dt, n_steps, out_every, (cplx *)rho, snap, 2 * N, &d, t_start);
     free_adjacency(&a);
 }

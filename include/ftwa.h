@@ -196,6 +196,15 @@ int ftwa_evolve(ftwa_plan_t *plan, void *rho_dev, int64_t M, int64_t n_steps,
  * non-finite values), FTWA_ERR_CUDA, FTWA_ERR_OUT_OF_MEMORY. */
 int ftwa_set_drive(ftwa_plan_t *plan, const double *amp, double t0, double sigma, double omega, double phase);
 
+/* Time-dependent hopping (a second form of the time-dependent Hamiltonians
+ * that Sec. III admits): every j_ij of Eq. 1 is scaled by
+ * m(t) = 1 + eps g(t), g(t) = exp(-(t - t0)^2 / (2 sigma^2))
+ * cos(omega (t - t0) + phase) (sigma <= 0: no envelope), evaluated at the RK4
+ * stage times; eps = 0 removes it.  Start times as in ftwa_evolve_at; the
+ * same restrictions as ftwa_set_drive (banded stepper; no adjoint, no graph
+ * batch).  Errors: FTWA_ERR_INVALID_ARGUMENT (null plan, non-finite values). */
+int ftwa_set_hopping_drive(ftwa_plan_t *plan, double eps, double t0, double sigma, double omega, double phase);
+
 /* Long-range interaction (Eq. 1 with a general u_ij; Eq. 6 with its sum over
  * k): u is a host [N][N] symmetric matrix (copied; u_ii is the on-site term
  * and replaces the plan's U).  Eq. 6 then uses the diagonal field

@@ -140,6 +140,12 @@ class Plan:
         check(load().ftwa_set_drive(self._h, ctypes.c_void_p(a.ctypes.data), float(t0), float(sigma), float(omega),
                                     float(phase)), "ftwa_set_drive")
 
+    def set_hopping_drive(self, eps, t0=0.0, sigma=0.0, omega=0.0, phase=0.0):
+        """Scale every hopping by m(t) = 1 + eps g(t), g the pulse shape of
+        set_drive; eps = 0 removes it."""
+        check(load().ftwa_set_hopping_drive(self._h, float(eps), float(t0), float(sigma), float(omega), float(phase)),
+              "ftwa_set_hopping_drive")
+
     def set_interaction(self, u):
         """Long-range interaction u [N, N] (symmetric, u_ii = on-site term) of
         Eq. 1 in place of U; None returns to the on-site U."""

@@ -24,7 +24,7 @@ FTWA_MOMENTS_NOALLOC_MAX_TK = 131072
 
 # every symbol include/ftwa.h declares
 EXPORTS = ("ftwa_plan", "ftwa_destroy", "ftwa_get_info", "ftwa_sample", "ftwa_set_initial_basis", "ftwa_philox",
-           "ftwa_evolve", "ftwa_evolve_at", "ftwa_set_drive", "ftwa_set_interaction",
+           "ftwa_evolve", "ftwa_evolve_at", "ftwa_set_drive", "ftwa_set_hopping_drive", "ftwa_set_interaction",
            "ftwa_ed_plan", "ftwa_ed_destroy", "ftwa_ed_info", "ftwa_ed_evolve",
            "ftwa_moments", "ftwa_moments_noalloc", "ftwa_adjoint", "ftwa_autotune", "ftwa_batch_create",
            "ftwa_batch_launch", "ftwa_batch_destroy", "ftwa_status", "ftwa_debug_force_timeout", "ftwa_error_string",
@@ -83,6 +83,7 @@ def load(path: str = LIB_PATH):
     lib.ftwa_evolve_at.argtypes = [P, P, i64, i64, f64, P, P]
     lib.ftwa_set_drive.argtypes = [P, P, f64, f64, f64, f64]
     lib.ftwa_set_interaction.argtypes = [P, P]
+    lib.ftwa_set_hopping_drive.argtypes = [P, f64, f64, f64, f64, f64]
     lib.ftwa_ed_plan.argtypes = [ctypes.POINTER(Lattice), f64, i32, i32, ctypes.POINTER(P)]
     lib.ftwa_ed_destroy.argtypes = [P]
     lib.ftwa_ed_destroy.restype = None

@@ -563,7 +563,7 @@ int launch_adjoint(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, int32_t c
     // derivatives the adjoint does not carry
     if (p->general_basis) return FTWA_ERR_UNSUPPORTED;
     // nor through the time-dependent drive or a long-range interaction
-    if (p->drive || p->longrange) return FTWA_ERR_UNSUPPORTED;
+    if (p->drive || p->longrange || p->hop_drive) return FTWA_ERR_UNSUPPORTED;
     if (p->precision == FTWA_FP64) return launch_adjoint_t<double>(p, seed, M, n_steps, ckpt_every, dL, gU, gt, gn, s);
     return launch_adjoint_t<float>(p, seed, M, n_steps, ckpt_every, dL, gU, gt, gn, s);
 }

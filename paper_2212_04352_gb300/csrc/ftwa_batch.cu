@@ -102,7 +102,7 @@ int ftwa_batch_create(ftwa_plan_t *const *plans, int32_t n, void *const *rho_dev
     // a time-dependent drive fills its pulse table per call, and graphs carry
     // only the plain steppers: driven and long-range plans are not captured
     for (int i = 0; i < n; ++i)
-        if (plans[i]->drive || plans[i]->longrange) return FTWA_ERR_UNSUPPORTED;
+        if (plans[i]->drive || plans[i]->longrange || plans[i]->hop_drive) return FTWA_ERR_UNSUPPORTED;
     cudaStream_t prep = nullptr, cap = nullptr;
     if (cudaStreamCreateWithFlags(&prep, cudaStreamNonBlocking) != cudaSuccess) return FTWA_ERR_CUDA;
     // prepare: choose every shape and upload every table outside the capture

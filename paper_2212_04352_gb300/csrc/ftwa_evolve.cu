@@ -552,7 +552,7 @@ struct BandArgs {
     // FIELD: the diagonal field h_pp,s of every stage is tabulated in shared
     // memory (on-site U or a long-range u, plus the time-dependent drive)
     const T *amp;               // [2][N] drive amplitudes, or null
-    const T *ftab;              // [n_steps][4] pulse value at the RK4 stage times, or null
+    const T *ftab;              // [n_steps][4][2] (site pulse f, hopping scale m) at the RK4 stage times, or null
     const T *u;                 // [N][N] symmetric interaction of Eq. 1, or null (on-site U)
     long long M, n_steps;
     int out_every;
@@ -582,7 +582,7 @@ __device__ __forceinline__ void band_stage(unsigned char *smem, const BandArgs<T
                                            const uint32_t *my_items, const int32_t *s_nbr, const T *s_t, T *s_diag,
                                            uint32_t diag_s, int lane, uint32_t t_state, int eps_bytes,
                                            int diag_stride, long long b, bool snap_now, long long snap_row,
-                                           const T *s_field)
+                                           const T *s_field, T ms)
 {
     using V = typename C2<T>::type;
     constexpr int SZ = sizeof(V);
@@ -658,6 +658,11 @@ __device__ __forceinline__ void band_stage(unsigned char *smem, const BandArgs<T
                     const T t = UNIFORM_T ? (n < d.deg ? a.t_uniform : T(0)) : s_t[4 * p + n];
                     const uint32_t ad = d.base_k[n] + soff + boff_cur + qsz;
                     cfma(-t, CLUSTER ? ldc2(ad, T()) : lds2(ad, T()), h);
+                }
+                // (FIELD: every hopping scaled by m(t_stage))
+                if constexpr (FIELD) {
+                    h.x *= ms;
+                    h.y *= ms;
                 }
                 // + U (Re rho_pp,sbar - Re rho_qq,sbar) rho_pq
                 // (FIELD: + (h_pp,s - h_qq,s) rho_pq from the tabulated field)
@@ -969,17 +974,20 @@ __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
         for (long long step = 0; step < a.n_steps && h->abort == 0; ++step) {
             const bool snap_now = a.snap && ((step + 1) % a.out_every == 0);
             const long long snap_row = (step + 1) / a.out_every;
-            T fd[4] = {T(0), T(0), T(0), T(0)};
+            T fd[4] = {T(0), T(0), T(0), T(0)}, md[4] = {T(1), T(1), T(1), T(1)};
             if constexpr (FIELD)
                 if (a.ftab)
-                    for (int k = 0; k < 4; ++k) fd[k] = a.ftab[4 * step + k];
+                    for (int k = 0; k < 4; ++k) {
+                        fd[k] = a.ftab[2 * (4 * step + k)];
+                        md[k] = a.ftab[2 * (4 * step + k) + 1];
+                    }
             if constexpr (FIELD) {
                 diag_field<T, CLUSTER>(a, s_diag + (0 & 1) * diag_stride, s_amp, fd[0], s_field, field_s, rank);
                 if (CLUSTER && a.u && !stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
             }
             band_stage<0, T, CLUSTER, UNIFORM_T, FIELD>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag,
                                                         diag_s, lane, t_state, eps_bytes, diag_stride, b, snap_now,
-                                                        snap_row, s_field);
+                                                        snap_row, s_field, md[0]);
             tmem_wait_st();
             if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
             if constexpr (FIELD) {
@@ -988,7 +996,7 @@ __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
             }
             band_stage<1, T, CLUSTER, UNIFORM_T, FIELD>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag,
                                                         diag_s, lane, t_state, eps_bytes, diag_stride, b, snap_now,
-                                                        snap_row, s_field);
+                                                        snap_row, s_field, md[1]);
             tmem_wait_st();
             if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
             if constexpr (FIELD) {
@@ -997,7 +1005,7 @@ __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
             }
             band_stage<2, T, CLUSTER, UNIFORM_T, FIELD>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag,
                                                         diag_s, lane, t_state, eps_bytes, diag_stride, b, snap_now,
-                                                        snap_row, s_field);
+                                                        snap_row, s_field, md[2]);
             tmem_wait_st();
             if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
             if constexpr (FIELD) {
@@ -1006,7 +1014,7 @@ __global__ void __launch_bounds__(kThreads, 1) band_stepper(const BandArgs<T> a)
             }
             band_stage<3, T, CLUSTER, UNIFORM_T, FIELD>(smem, a, s_row, s_rowbase, my_items, s_nbr, s_t, s_diag,
                                                         diag_s, lane, t_state, eps_bytes, diag_stride, b, snap_now,
-                                                        snap_row, s_field);
+                                                        snap_row, s_field, md[3]);
             tmem_wait_st();
             if (!stage_barrier<CLUSTER>(h, phase, C, limit, a.status)) break;
         }
@@ -1335,7 +1343,7 @@ int choose_band_shape(Plan *p, int64_t M, BandShape *out)
         int bestE = 0, bestK = 0;
         for (int S = 1; S <= want; ++S) {
             const int buf = ((S * eps_max * SZ + 15) / 16) * 16;
-            if (band_smem(N, S, real_bytes, buf, p->drive || p->longrange) > max_smem) break;
+            if (band_smem(N, S, real_bytes, buf, p->drive || p->longrange || p->hop_drive) > max_smem) break;
             std::vector<std::vector<uint32_t>> its(C);
             int E = 0, K = 0;
             bool ok = true;
@@ -1371,7 +1379,7 @@ int choose_band_shape(Plan *p, int64_t M, BandShape *out)
                     sh.items[((size_t)r * kWarps + w) * bestK + i] = best_items[r][(size_t)w * Kr + i];
         }
         sh.buf_bytes = ((best * eps_max * SZ + 15) / 16) * 16;
-        sh.smem_bytes = std::max(kMinSmem, band_smem(N, best, real_bytes, sh.buf_bytes, p->drive || p->longrange));
+        sh.smem_bytes = std::max(kMinSmem, band_smem(N, best, real_bytes, sh.buf_bytes, p->drive || p->longrange || p->hop_drive));
         const long long batches = (M + best - 1) / best;
         sh.grid = (int)std::min<long long>(std::max<long long>(batches, 1), std::max(1, sm / C)) * C;
         *out = sh;
@@ -1447,7 +1455,7 @@ static int band_launch(Plan *p, BandShape &sh, void *rho, int64_t M, int64_t n_s
     a.qoff = sh.qoff;
     const bool f64 = std::is_same<T, double>::value;
     a.amp = p->drive ? reinterpret_cast<const T *>(f64 ? (const void *)p->d_amp64 : (const void *)p->d_amp32) : nullptr;
-    a.ftab = p->drive ? reinterpret_cast<const T *>(p->d_ftab) : nullptr;
+    a.ftab = (p->drive || p->hop_drive) ? reinterpret_cast<const T *>(p->d_ftab) : nullptr;
     a.u = p->longrange ? reinterpret_cast<const T *>(f64 ? (const void *)p->d_u64 : (const void *)p->d_u32) : nullptr;
     for (int i = 0; i <= kMaxCluster; ++i) a.row_begin[i] = sh.row_begin[i];
     a.items = p->d_items;
@@ -1476,28 +1484,38 @@ static int band_dispatch_d(Plan *p, BandShape &sh, void *rho, int64_t M, int64_t
 template <typename T>
 static int band_dispatch(Plan *p, BandShape &sh, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s)
 {
-    return (p->drive || p->longrange) ? band_dispatch_d<T, true>(p, sh, rho, M, n_steps, snap, s)
+    return (p->drive || p->longrange || p->hop_drive) ? band_dispatch_d<T, true>(p, sh, rho, M, n_steps, snap, s)
                                       : band_dispatch_d<T, false>(p, sh, rho, M, n_steps, snap, s);
 }
 
-// pulse values f(t) of the on-site drive at the four RK4 stage times of every
-// step, t = t_start + (step + c) dt, c = 0, 1/2, 1/2, 1 (in double)
+// per RK4 stage time t = t_start + (step + c) dt, c = 0, 1/2, 1/2, 1 (in
+// double): the on-site pulse f(t) (0 without a site drive) and the hopping
+// scale m(t) = 1 + eps g(t) (1 without a hopping drive), interleaved
+struct PulseArgs {
+    double t0, sigma, omega, phase;
+    int on;
+};
+__device__ __forceinline__ double pulse_at(const PulseArgs &q, double t)
+{
+    const double env = q.sigma > 0.0 ? exp(-(t - q.t0) * (t - q.t0) / (2.0 * q.sigma * q.sigma)) : 1.0;
+    return env * cos(q.omega * (t - q.t0) + q.phase);
+}
 template <typename T>
-__global__ void drive_table_kernel(T *ftab, long long n_steps, double t_start, double dt, double t0, double sigma,
-                                   double omega, double phase)
+__global__ void drive_table_kernel(T *ftab, long long n_steps, double t_start, double dt, PulseArgs site,
+                                   PulseArgs hop, double hop_eps)
 {
     const double c[4] = {0.0, 0.5, 0.5, 1.0};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 4 * n_steps;
          i += (long long)gridDim.x * blockDim.x) {
         const double t = t_start + ((double)(i / 4) + c[i % 4]) * dt;
-        const double env = sigma > 0.0 ? exp(-(t - t0) * (t - t0) / (2.0 * sigma * sigma)) : 1.0;
-        ftab[i] = (T)(env * cos(omega * (t - t0) + phase));
+        ftab[2 * i] = (T)(site.on ? pulse_at(site, t) : 0.0);
+        ftab[2 * i + 1] = (T)(hop.on ? 1.0 + hop_eps * pulse_at(hop, t) : 1.0);
     }
 }
 
 static int prepare_drive(Plan *p, int64_t n_steps, double t_start, cudaStream_t s)
 {
-    const size_t bytes = (size_t)(p->precision == FTWA_FP64 ? 8 : 4) * 4 * (size_t)std::max<int64_t>(n_steps, 1);
+    const size_t bytes = (size_t)(p->precision == FTWA_FP64 ? 8 : 4) * 8 * (size_t)std::max<int64_t>(n_steps, 1);
     if (p->ftab_bytes < bytes) {
         cudaFree(p->d_ftab);
         p->d_ftab = nullptr;
@@ -1509,26 +1527,26 @@ static int prepare_drive(Plan *p, int64_t n_steps, double t_start, cudaStream_t 
     if (n_steps == 0) return FTWA_OK;
     const long long n = 4 * n_steps;
     const int grid = (int)std::min<long long>((n + 255) / 256, 4096);
+    const PulseArgs site{p->drive_t0, p->drive_sigma, p->drive_omega, p->drive_phase, p->drive ? 1 : 0};
+    const PulseArgs hop{p->hop_t0, p->hop_sigma, p->hop_omega, p->hop_phase, p->hop_drive ? 1 : 0};
     if (p->precision == FTWA_FP64)
         drive_table_kernel<double><<<grid, 256, 0, s>>>(reinterpret_cast<double *>(p->d_ftab), n_steps, t_start,
-                                                       p->dt, p->drive_t0, p->drive_sigma, p->drive_omega,
-                                                       p->drive_phase);
+                                                       p->dt, site, hop, p->hop_eps);
     else
         drive_table_kernel<float><<<grid, 256, 0, s>>>(reinterpret_cast<float *>(p->d_ftab), n_steps, t_start,
-                                                      p->dt, p->drive_t0, p->drive_sigma, p->drive_omega,
-                                                      p->drive_phase);
+                                                      p->dt, site, hop, p->hop_eps);
     return set_cuda_error(cudaGetLastError());
 }
 
 int launch_evolve(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s, double t_start)
 {
-    if (p->drive || p->longrange) {
+    if (p->drive || p->longrange || p->hop_drive) {
         // the tabulated diagonal field (drive, long-range u) runs on the
         // banded stepper (both precisions)
         BandShape bs;
         int rc = choose_band_shape(p, M, &bs);
         if (rc != FTWA_OK) return rc;
-        if (p->drive && M > 0 && !p->dry_run) {
+        if ((p->drive || p->hop_drive) && M > 0 && !p->dry_run) {
             rc = prepare_drive(p, n_steps, t_start, s);
             if (rc != FTWA_OK) return rc;
         }

@@ -87,6 +87,9 @@ struct Plan {
     float *d_amp32 = nullptr;         // [2][N]
     void *d_ftab = nullptr;           // [n_steps][4] pulse values of the last evolve call
     size_t ftab_bytes = 0;
+    // time-dependent hopping scale m(t) = 1 + hop_eps g(t)
+    bool hop_drive = false;
+    double hop_eps = 0, hop_t0 = 0, hop_sigma = 0, hop_omega = 0, hop_phase = 0;
     // long-range interaction u_ij of Eq. 1 (replaces the on-site U)
     bool longrange = false;
     double *d_u64 = nullptr;          // [N][N]

@@ -386,6 +386,20 @@ int ftwa_evolve_at(ftwa_plan_t *p, void *rho_dev, int64_t M, int64_t n_steps, do
     return launch_evolve(p, rho_dev, M, n_steps, snap_dev, static_cast<cudaStream_t>(stream), t_start);
 }
 
+int ftwa_set_hopping_drive(ftwa_plan_t *p, double eps, double t0, double sigma, double omega, double phase)
+{
+    if (!p || !std::isfinite(eps) || !std::isfinite(t0) || !std::isfinite(sigma) || !std::isfinite(omega) ||
+        !std::isfinite(phase))
+        return FTWA_ERR_INVALID_ARGUMENT;
+    p->hop_drive = eps != 0.0;
+    p->hop_eps = eps;
+    p->hop_t0 = t0;
+    p->hop_sigma = sigma;
+    p->hop_omega = omega;
+    p->hop_phase = phase;
+    return FTWA_OK;
+}
+
 int ftwa_set_interaction(ftwa_plan_t *p, const double *u)
 {
     if (!p) return FTWA_ERR_INVALID_ARGUMENT;

@@ -103,3 +103,27 @@ def test_drive_neutral_and_unsupported(ftwa):
         P.evolve(r4, 120, snap=None)
         assert torch.equal(r4, ref)
         assert P.status() == 0
+
+
+@pytest.mark.parametrize("precision,cluster,tol", [(0, 1, 1e-10), (0, 4, 1e-10), (1, 0, 1e-4)])
+def test_hopping_drive_parity(ftwa, precision, cluster, tol):
+    """Every hopping scaled by m(t) = 1 + eps g(t), together with the site
+    pulse, against the oracle (54 sites, start time 0.3, 200 steps)."""
+    lat = W.hexagonal_flake(3)
+    nu, nd = W.neel_state(lat)
+    d = _drive(lat.n_sites, seed=5)
+    hop = dict(eps=0.5, t0=1.2, sigma=0.6, omega=3.0, phase=0.1)
+    M, steps, t_start = 3, 200, 0.3
+    rho0 = np.stack([oracle.sample(lat.n_sites, nu, nd, 12, m) for m in range(M)])
+    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=precision, cluster=cluster) as P:
+        P.set_drive(d["amp"], d["t0"], d["sigma"], d["omega"], d["phase"])
+        P.set_hopping_drive(hop["eps"], hop["t0"], hop["sigma"], hop["omega"], hop["phase"])
+        dtype = np.complex128 if precision == 0 else np.complex64
+        rho = torch.from_numpy(rho0.astype(dtype)).cuda()
+        P.evolve(rho, steps, snap=None, t_start=t_start)
+        assert P.status() == 0
+        fin = rho.cpu().numpy().astype(np.complex128)
+        P.set_hopping_drive(0.0)
+    for m in range(M):
+        fo, _ = oracle.evolve(lat, 1.6, rho0[m], 0.01, steps, drive=dict(d, hop=hop), t_start=t_start)
+        assert _rel(fin[m], fo) <= tol

@@ -20,8 +20,8 @@ from ._lib import (  # noqa: F401
     FTWA_FP32, FTWA_FP64, FTWA_GRAM_BF16X3, FTWA_GRAM_FP64, FtwaError, check, load,
 )
 
-__all__ = ["Plan", "Batch", "plan", "philox", "moments_noalloc", "FTWA_FP32", "FTWA_FP64", "FTWA_GRAM_FP64", "FTWA_GRAM_BF16X3",
-           "FtwaError", "load"]
+__all__ = ["Plan", "Batch", "ED", "plan", "philox", "moments_noalloc", "occupations", "FTWA_FP32", "FTWA_FP64",
+           "FTWA_GRAM_FP64", "FTWA_GRAM_BF16X3", "FtwaError", "load"]
 
 
 def _stream(stream=None):
@@ -212,6 +212,101 @@ class Plan:
 
 def plan(lattice, U, **kw) -> Plan:
     return Plan(lattice, U, **kw)
+
+
+class _Bonds:
+    """Lattice view (sites, bonds, per-bond hopping) handed to ftwa_plan."""
+
+    def __init__(self, n_sites, bonds, t_bond):
+        self.n_sites = int(n_sites)
+        self.bonds = np.ascontiguousarray(bonds, dtype=np.int32)
+        self.t_bond = np.ascontiguousarray(t_bond, dtype=np.float64)
+        self.n_bonds = int(self.bonds.shape[0])
+
+
+def _default_ckpt(n_steps, out_every):
+    """Checkpoint spacing for the adjoint: the multiple of out_every dividing
+    n_steps that is closest to sqrt(n_steps) (memory ~ n_steps/c + c)."""
+    cands = [c for c in range(out_every, n_steps + 1, out_every) if n_steps % c == 0]
+    if not cands:
+        return out_every
+    return min(cands, key=lambda c: abs(c - n_steps ** 0.5))
+
+
+_OCC_FN = None
+
+
+def _occupation_function():
+    global _OCC_FN
+    if _OCC_FN is not None:
+        return _OCC_FN
+    import torch
+
+    class FtwaOccupations(torch.autograd.Function):
+        """Forward: Eq. 7 samples -> RK4 of Eq. 6 -> FP64 sample means (Eq. 5)
+        of the occupations, all in libftwa.  Backward: the discrete RK4
+        adjoint (ftwa_adjoint) of the same samples (same seed, regenerated
+        on the device), given dL/d<n> from autograd."""
+
+        @staticmethod
+        def forward(ctx, U, t_bond, n0, bonds, seed, M, n_steps, precision, dt, out_every, ckpt_every):
+            n0h = n0.detach().to("cpu", torch.float64).numpy()
+            lat = _Bonds(n0h.shape[1], bonds, t_bond.detach().to("cpu", torch.float64).numpy())
+            P = Plan(lat, float(U.detach()), n_up=n0h[0], n_dn=n0h[1], precision=precision, dt=dt,
+                     out_every=out_every)
+            try:
+                rho = P.sample(seed, M)
+                X = P.evolve(rho, n_steps)
+                del rho
+                occ = P.moments(X, g2=False)[0]
+                st = P.status()
+                if st != 0:
+                    raise FtwaError(st, "ftwa_evolve", "device status word set (timeout)")
+            except BaseException:
+                P.close()
+                raise
+            ctx.plan = P
+            ctx.args = (seed, M, n_steps, ckpt_every)
+            ctx.like = [(x.shape, x.device, x.dtype) for x in (U, t_bond, n0)]
+            return occ
+
+        @staticmethod
+        def backward(ctx, g):
+            P = ctx.plan
+            seed, M, n_steps, ckpt_every = ctx.args
+            gU, gt, gn = P.adjoint(seed, M, n_steps, ckpt_every, g.contiguous())
+            st = P.status()
+            if st != 0:
+                raise FtwaError(st, "ftwa_adjoint", "device status word set (timeout)")
+            grads = [x.reshape(shape).to(dev, dt) for x, (shape, dev, dt) in zip((gU, gt, gn), ctx.like)]
+            return (*grads, None, None, None, None, None, None, None, None)
+
+    _OCC_FN = FtwaOccupations
+    return _OCC_FN
+
+
+def occupations(lattice, U, t_bond, n0, seed, M, n_steps, precision=FTWA_FP64, dt=0.01, out_every=10,
+                ckpt_every=None):
+    """Differentiable fTWA occupations <n_k>(t) (Eq. 5 estimator of Re rho_kk
+    + 1/2 over samples m = 0 .. M-1 of ``seed``), [n_steps/out_every + 1, 2N]
+    float64 on the device, k = s*N + i.
+
+    U (0-dim), t_bond ([n_bonds], the lattice's bond order) and n0 ([2, N]
+    initial occupations) are torch tensors; those with requires_grad receive
+    dL/dU, dL/dt_b, dL/dn0 from the RK4 adjoint on backward (exact for the
+    integrated samples, common random numbers).  The lattice supplies only
+    the sites and bonds.  ckpt_every must divide n_steps and be a multiple of
+    out_every (default: near sqrt(n_steps)).  Each call builds a plan for the
+    given values; the plan is released with the autograd graph (backward may
+    run more than once with retain_graph)."""
+    import torch
+    if ckpt_every is None:
+        ckpt_every = _default_ckpt(int(n_steps), int(out_every))
+    U = torch.as_tensor(U, dtype=torch.float64)
+    t_bond = torch.as_tensor(t_bond, dtype=torch.float64)
+    n0 = torch.as_tensor(n0, dtype=torch.float64)
+    return _occupation_function().apply(U, t_bond, n0, np.asarray(lattice.bonds), int(seed), int(M), int(n_steps),
+                                        int(precision), float(dt), int(out_every), int(ckpt_every))
 
 
 class ED:

@@ -103,3 +103,12 @@ def test_workload_inputs():
     nu, nd = W.charge_imbalanced_state(lat)
     assert nu.sum() == 99 and nd.sum() == 99
     assert ((nu + nd) == 2).sum() == 6 and ((nu + nd) == 0).sum() == 6
+
+
+def test_adjoint_checkpoint_default():
+    """The autograd wrapper's default checkpoint spacing divides n_steps, is a
+    multiple of out_every and lies near sqrt(n_steps)."""
+    import paper_2212_04352_gb300 as F
+    for n_steps, every, want in [(40, 10, 10), (1000, 10, 40), (30, 10, 10), (400, 20, 20), (3600, 10, 60)]:
+        c = F._default_ckpt(n_steps, every)
+        assert c == want and n_steps % c == 0 and c % every == 0

@@ -20,8 +20,8 @@ from ._lib import (  # noqa: F401
     FTWA_FP32, FTWA_FP64, FTWA_GRAM_BF16X3, FTWA_GRAM_FP64, FtwaError, check, load,
 )
 
-__all__ = ["Plan", "Batch", "ED", "plan", "philox", "moments_noalloc", "occupations", "FTWA_FP32", "FTWA_FP64",
-           "FTWA_GRAM_FP64", "FTWA_GRAM_BF16X3", "FtwaError", "load"]
+__all__ = ["Plan", "Batch", "ED", "plan", "philox", "moments_noalloc", "occupations", "FTWAFunction", "FTWA_FP32",
+           "FTWA_FP64", "FTWA_GRAM_FP64", "FTWA_GRAM_BF16X3", "FtwaError", "load"]
 
 
 def _stream(stream=None):
@@ -242,7 +242,7 @@ def _occupation_function():
         return _OCC_FN
     import torch
 
-    class FtwaOccupations(torch.autograd.Function):
+    class FTWAFunction(torch.autograd.Function):
         """Forward: Eq. 7 samples -> RK4 of Eq. 6 -> FP64 sample means (Eq. 5)
         of the occupations, all in libftwa.  Backward: the discrete RK4
         adjoint (ftwa_adjoint) of the same samples (same seed, regenerated
@@ -281,8 +281,16 @@ def _occupation_function():
             grads = [x.reshape(shape).to(dev, dt) for x, (shape, dev, dt) in zip((gU, gt, gn), ctx.like)]
             return (*grads, None, None, None, None, None, None, None, None)
 
-    _OCC_FN = FtwaOccupations
+    _OCC_FN = FTWAFunction
     return _OCC_FN
+
+
+def __getattr__(name):
+    # FTWAFunction: the autograd.Function behind occupations(), created on first
+    # use so that importing the package does not import torch.
+    if name == "FTWAFunction":
+        return _occupation_function()
+    raise AttributeError(name)
 
 
 def occupations(lattice, U, t_bond, n0, seed, M, n_steps, precision=FTWA_FP64, dt=0.01, out_every=10,

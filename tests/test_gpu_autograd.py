@@ -95,6 +95,7 @@ def test_gradcheck(ftwa):
     def f(Uv, tv, nv):
         return ftwa.occupations(lat, Uv, tv, nv, 3, 4, 30, out_every=10, ckpt_every=10)
 
+    assert ftwa.FTWAFunction.__name__ == "FTWAFunction"
     assert torch.autograd.gradcheck(f, (U, tb, n), eps=1e-6, atol=1e-7, rtol=1e-5, nondet_tol=1e-10,
                                     fast_mode=True)
 

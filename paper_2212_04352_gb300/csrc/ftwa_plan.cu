@@ -107,6 +107,115 @@ static bool two_colour(int N, const std::vector<int32_t> &bonds, std::vector<int
     return true;
 }
 
+// Slot order for shared-memory banks.  A warp of the banded stepper takes 32
+// consecutive columns q = qoff + 32 blk + lane (qoff = N - 32 ceil(N/32);
+// lanes with q < 0 take column 0) and, for each slot n, gathers
+// rho_p,k(q,n) from one row p.  In FP32 (8-byte elements) a half-warp is
+// served in one shared-memory wavefront when its distinct k are distinct
+// mod 16; in FP64 (16-byte elements) a quarter-warp, mod 8.  The sum over a
+// site's slots is order-free, so the real neighbours may be permuted among
+// slots 0 .. deg-1 (the kernels take slots below the degree as bonds), and
+// an empty slot (hopping 0) may point at any column within +-3 of the site
+// and within the band (|k - i| <= bw, stored in every row that reads it).
+// Greedy sweeps over these choices minimise, per group of columns, the
+// wavefronts and then the sum of squared bank loads.
+struct SlotSearch {
+    int N, bw, qoff;
+    const std::vector<int> &deg;
+    std::vector<int> &slot_k;
+
+    // first site and end (exclusive) of the column group of site i
+    void group(int i, int w, int &g0, int &g1) const
+    {
+        const int g = (i - qoff) / w;
+        g0 = std::max(0, qoff + g * w);
+        g1 = std::min(N, qoff + (g + 1) * w);
+    }
+    double group_cost(int g0, int g1, int mod) const
+    {
+        double c = 0;
+        for (int n = 0; n < 3; ++n) {
+            int ks[16], nk = 0, cnt[16] = {0};
+            for (int x = g0; x < g1; ++x) {
+                const int k = slot_k[3 * x + n];
+                bool seen = false;
+                for (int y = 0; y < nk; ++y) seen = seen || ks[y] == k;
+                if (!seen) {
+                    ks[nk++] = k;
+                    cnt[k % mod]++;
+                }
+            }
+            int mx = 0, sq = 0;
+            for (int b = 0; b < mod; ++b) {
+                mx = std::max(mx, cnt[b]);
+                sq += cnt[b] * cnt[b];
+            }
+            c += 64.0 * mx + sq;
+        }
+        return c;
+    }
+    double site_cost(int i) const
+    {
+        int a0, a1, b0, b1;
+        group(i, 16, a0, a1);
+        group(i, 8, b0, b1);
+        return group_cost(a0, a1, 16) + 0.5 * group_cost(b0, b1, 8);
+    }
+};
+
+static void order_slots_for_banks(int N, int bw, const std::vector<int> &deg, std::vector<int> &slot_k,
+                                  std::vector<double> &t64, std::vector<int32_t> &bond)
+{
+    SlotSearch S{N, bw, N - 32 * ((N + 31) / 32), deg, slot_k};
+    for (int sweep = 0; sweep < 8; ++sweep) {
+        bool changed = false;
+        for (int i = 0; i < N; ++i) {
+            const int d = deg[i];
+            int k0[3], b0[3];
+            double t0[3];
+            for (int n = 0; n < 3; ++n) {
+                k0[n] = slot_k[3 * i + n];
+                b0[n] = bond[3 * i + n];
+                t0[n] = t64[4 * i + n];
+            }
+            std::vector<int> ph;   // placeholder columns
+            for (int k = i - 3; k <= i + 3; ++k)
+                if (k >= 0 && k < N && std::abs(k - i) <= bw) ph.push_back(k);
+            double best = S.site_cost(i);
+            int best_perm[3] = {0, 1, 2}, best_ph[3] = {k0[0], k0[1], k0[2]};
+            int perm[3] = {0, 1, 2};
+            do {
+                int sel[3] = {0, 0, 0};   // odometer over the empty slots' columns
+                while (true) {
+                    for (int n = 0; n < 3; ++n) slot_k[3 * i + n] = n < d ? k0[perm[n]] : ph[sel[n]];
+                    const double c = S.site_cost(i);
+                    if (c < best - 1e-9) {
+                        best = c;
+                        for (int n = 0; n < 3; ++n) {
+                            best_perm[n] = perm[n];
+                            best_ph[n] = slot_k[3 * i + n];
+                        }
+                    }
+                    int n = d;
+                    while (n < 3 && ++sel[n] == (int)ph.size()) sel[n++] = 0;
+                    if (n >= 3) break;
+                }
+            } while (std::next_permutation(perm, perm + d));
+            for (int n = 0; n < 3; ++n) {
+                if (n < d) {
+                    slot_k[3 * i + n] = k0[best_perm[n]];
+                    bond[3 * i + n] = b0[best_perm[n]];
+                    t64[4 * i + n] = t0[best_perm[n]];
+                } else {
+                    slot_k[3 * i + n] = best_ph[n];
+                }
+                changed = changed || slot_k[3 * i + n] != k0[n];
+            }
+        }
+        if (!changed) break;
+    }
+}
+
 }  // namespace ftwa
 
 using namespace ftwa;
@@ -249,10 +358,9 @@ int ftwa_plan(const ftwa_lattice *lat, double U, double t, double filling, const
         p->nbr_bond[3 * j + fill[j]] = b;
         fill[j]++;
     }
-    // order each site's slots by distance |k - i| (then k): on lattices
-    // numbered along rows, slot 0 and 1 are then the in-row neighbours i -+ 1
-    // for most sites, so that a warp's gathers of one slot over consecutive
-    // columns touch consecutive addresses (fewer shared-memory bank conflicts)
+    // order each site's slots by distance |k - i| (then k): the starting point
+    // of order_slots_for_banks (on lattices numbered along rows, slots 0 and 1
+    // are then the in-row neighbours i -+ 1 for most sites)
     for (int i = 0; i < N; ++i) {
         int idx[3] = {0, 1, 2};
         std::sort(idx, idx + fill[i], [&](int x, int y) {
@@ -274,6 +382,7 @@ int ftwa_plan(const ftwa_lattice *lat, double U, double t, double filling, const
             t64[4 * i + n] = t2[n];
         }
     }
+    order_slots_for_banks(N, p->bandwidth, fill, slot_k, t64, p->nbr_bond);
     for (int i = 0; i < N; ++i)
         p->nbr_host[i] = slot_k[3 * i] | (slot_k[3 * i + 1] << 8) | (slot_k[3 * i + 2] << 16) | (fill[i] << 24);
     std::vector<float> t32(t64.begin(), t64.end());

@@ -31,6 +31,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "ftwa_internal.h"
 
@@ -112,19 +113,21 @@ __device__ __forceinline__ double2 xi_of(unsigned long long seed, long long m, i
     return make_double2(r * cs, r * sn);
 }
 
+template <typename T>
 struct Smem {
     uint32_t *elem;     // [NE]: a | b << 8 | s << 16
     int32_t *nbr;       // [N]
     int32_t *bond;      // [N][3]
     int32_t *bxy;       // [B][2]
-    double *cdiag;      // [2][N] diagonal coupling accumulator
+    T *cacc;            // [2][N] diagonal coupling sums of one VJP
+    T *bacc;            // [B] bond sums of one VJP
     double *gt;         // [B]
     double *gn;         // [2][N]
 };
 
 // out = f(y) (Eq. 6) on the packed upper triangle
 template <typename T>
-__device__ void f_eval(const AdjArgs<T> &a, const Smem &sm, const typename C2T<T>::type *y,
+__device__ void f_eval(const AdjArgs<T> &a, const Smem<T> &sm, const typename C2T<T>::type *y,
                        typename C2T<T>::type *out)
 {
     using V = typename C2T<T>::type;
@@ -163,16 +166,120 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// w = VJP_f(Y)[v]; accumulates dL/dU (register) and dL/dt_b (shared memory).
+// w = VJP_f(Y)[v] for FP32 plans; accumulates dL/dU (register) and dL/dt_b
+// (shared memory), in one pass over the stored upper triangle, a warp per row (coalesced):
+//  - elementwise: w = -f_D(v) with D from Y, and the U gradient;
+//  - the U term's coupling to the other spin's diagonal,
+//      c_k = -2U sum_j P_kj,  P_kj = Im(conj(v_kj) Y_kj)   (full row k);
+//    P is antisymmetric for Hermitian v, Y (P_jk = -P_kj), so a stored
+//    element (i, j), i < j, adds P_ij to c_i and -P_ij to c_j;
+//  - the hopping gradient of bond b = (x, y): with Hermitian v and Y,
+//      <v, d f / d t_b> = -2 Im[(v Y)_xy + (v Y)_yx],
+//    (v Y)_pk = sum_q v_pq conj(Y_kq) for k in nb(p).  The ordered pair
+//    (p, q) = (i, j) of a stored element gives Im(v_ij conj(Y_kj)), k in
+//    nb(i) (the column-part neighbours of Eq. 6), to the bond (i, k); the
+//    mirrored pair (p, q) = (j, i), i < j, gives Im(conj(v_ij) Y_ik), k in
+//    nb(j) (the row-part neighbours), to the bond (j, k).
+// Row-fixed sums (c_i, bonds of row i) are reduced over the warp once per
+// row; column-dependent ones (c_j, bonds of column j) are added per lane to
+// shared memory (distinct columns per lane: little contention).
+template <typename T>
+__device__ void vjp_rows(const AdjArgs<T> &a, const Smem<T> &sm, const typename C2T<T>::type *Y,
+                    const typename C2T<T>::type *v, typename C2T<T>::type *w, double &gU)
+{
+    using V = typename C2T<T>::type;
+    const int N = a.N;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) sm.cacc[i] = T(0);
+    for (int b = threadIdx.x; b < a.B; b += blockDim.x) sm.bacc[b] = T(0);
+    __syncthreads();
+    for (int r = warp; r < 2 * N; r += n_warps) {
+        const int s = r / N, i = r % N;
+        const int ni = sm.nbr[i], degi = (ni >> 24) & 0xFF;
+        const int e0 = pidx(N, s, i, i);
+        const T di = Y[pidx(N, 1 - s, i, i)].x;
+        T ci = T(0), gu = T(0), bi[3] = {T(0), T(0), T(0)};
+        for (int j = i + lane; j < N; j += 32) {
+            const int e = e0 + (j - i);
+            const int nj = sm.nbr[j], degj = (nj >> 24) & 0xFF;
+            const V vo = v[e], yo = Y[e];
+            T hr = T(0), hi = T(0);
+            // row part: neighbours k of j
+            for (int n = 0; n < degj; ++n) {
+                const int k = (nj >> (8 * n)) & 0xFF;
+                const V vk = getc(v, N, s, i, k);
+                const T t = a.tnb[4 * j + n];
+                hr = fma(t, vk.x, hr);
+                hi = fma(t, vk.y, hi);
+                if (i != j) {
+                    // Im(conj(v_ij) Y_ik) -> bond (j, k)
+                    const V yk = getc(Y, N, s, i, k);
+                    atomicAdd(&sm.bacc[sm.bond[3 * j + n]], vo.x * yk.y - vo.y * yk.x);
+                }
+            }
+            // column part: neighbours k of i
+            for (int n = 0; n < degi; ++n) {
+                const int k = (ni >> (8 * n)) & 0xFF;
+                const V vk = getc(v, N, s, k, j);
+                const T t = a.tnb[4 * i + n];
+                hr = fma(-t, vk.x, hr);
+                hi = fma(-t, vk.y, hi);
+                // Im(v_ij conj(Y_kj)) -> bond (i, k)
+                const V yk = getc(Y, N, s, k, j);
+                bi[n] += vo.y * yk.x - vo.x * yk.y;
+            }
+            const T dj = Y[pidx(N, 1 - s, j, j)].x;
+            const T g = a.U * (di - dj);
+            hr = fma(g, vo.x, hr);
+            hi = fma(g, vo.y, hi);
+            // w = -i (hr + i hi) = (hi, -hr)
+            V o;
+            o.x = hi;
+            o.y = (i == j) ? T(0) : -hr;
+            w[e] = o;
+            if (i != j) {
+                const T P = vo.x * yo.y - vo.y * yo.x;   // Im(conj(v_ij) Y_ij)
+                gu = fma(di - dj, P, gu);
+                ci += P;
+                atomicAdd(&sm.cacc[s * N + j], -P);
+            }
+        }
+        // dL/dU: weight 2, the stored (i, j) stands for (i, j) and (j, i); the
+        // row's sum is taken in T (no FP64 work per element in FP32 plans)
+        gU += -2.0 * (double)gu;
+        for (int o = 16; o > 0; o >>= 1) {
+            ci += __shfl_xor_sync(0xffffffffu, ci, o);
+#pragma unroll
+            for (int n = 0; n < 3; ++n) bi[n] += __shfl_xor_sync(0xffffffffu, bi[n], o);
+        }
+        if (lane == 0) {
+            atomicAdd(&sm.cacc[s * N + i], ci);
+            for (int n = 0; n < degi; ++n) atomicAdd(&sm.bacc[sm.bond[3 * i + n]], bi[n]);
+        }
+    }
+    __syncthreads();
+    // coupling to the other spin's diagonal; bond sums into the CTA's totals
+    for (int e = threadIdx.x; e < 2 * N; e += blockDim.x) {
+        const int s = e / N, k = e % N;
+        V &x = w[pidx(N, 1 - s, k, k)];
+        x.x += (T)(-2.0 * (double)a.U * (double)sm.cacc[e]);
+    }
+    for (int b = threadIdx.x; b < a.B; b += blockDim.x) sm.gt[b] += -2.0 * (double)sm.bacc[b];
+    __syncthreads();
+}
+
+// w = VJP_f(Y)[v] for FP64 plans (the same sums as vjp_rows, taken as dot
+// products): accumulates dL/dU (register) and dL/dt_b (shared memory).
 //  - elementwise: w = -f_D(v) with D from Y, and the U gradient;
 //  - the U term's coupling to the other spin's diagonal,
 //      c_k = -2U sum_j Im(conj(v_kj) Y_kj)   (full row k), one warp per row;
 //  - the hopping gradient of bond b = (x, y): with Hermitian v and Y,
 //      <v, d f / d t_b> = -2 Im[(v Y)_xy + (v Y)_yx]   (per spin),
 //    dot products over the full rows/columns, one warp per bond.
-// Every shared-memory sum has one writer: no atomics.
+// Every shared-memory sum has one writer: no atomics (measured faster than
+// vjp_rows for FP64, whose shared-memory atomics on doubles are slow).
 template <typename T>
-__device__ void vjp(const AdjArgs<T> &a, const Smem &sm, const typename C2T<T>::type *Y,
+__device__ void vjp_dot(const AdjArgs<T> &a, const Smem<T> &sm, const typename C2T<T>::type *Y,
                     const typename C2T<T>::type *v, typename C2T<T>::type *w, double &gU)
 {
     using V = typename C2T<T>::type;
@@ -221,7 +328,7 @@ __device__ void vjp(const AdjArgs<T> &a, const Smem &sm, const typename C2T<T>::
             acc += (double)vk.x * yk.y - (double)vk.y * yk.x;
         }
         acc = warp_sum(acc);
-        if (lane == 0) sm.cdiag[r] = -2.0 * (double)a.U * acc;
+        if (lane == 0) sm.cacc[r] = (T)(-2.0 * (double)a.U * acc);
     }
     for (int b = warp; b < a.B; b += n_warps) {
         const int x = sm.bxy[2 * b], y = sm.bxy[2 * b + 1];
@@ -241,9 +348,17 @@ __device__ void vjp(const AdjArgs<T> &a, const Smem &sm, const typename C2T<T>::
     for (int e = threadIdx.x; e < 2 * N; e += blockDim.x) {
         const int s = e / N, k = e % N;
         V &x = w[pidx(N, 1 - s, k, k)];
-        x.x += (T)sm.cdiag[e];
+        x.x += sm.cacc[e];
     }
     __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void vjp(const AdjArgs<T> &a, const Smem<T> &sm, const typename C2T<T>::type *Y,
+                                    const typename C2T<T>::type *v, typename C2T<T>::type *w, double &gU)
+{
+    if constexpr (std::is_same<T, double>::value) vjp_dot(a, sm, Y, v, w, gU);
+    else vjp_rows(a, sm, Y, v, w, gU);
 }
 
 template <typename V, typename T>
@@ -260,7 +375,7 @@ __device__ __forceinline__ void axpy(int NE, V *out, const V *x, T c, const V *y
 
 // one RK4 step: y1 = y0 + h/6 (k1 + 2 k2 + 2 k3 + k4) (k, ys, acc scratch)
 template <typename T>
-__device__ void rk4(const AdjArgs<T> &a, const Smem &sm, const typename C2T<T>::type *y0,
+__device__ void rk4(const AdjArgs<T> &a, const Smem<T> &sm, const typename C2T<T>::type *y0,
                     typename C2T<T>::type *y1, typename C2T<T>::type *k, typename C2T<T>::type *ys,
                     typename C2T<T>::type *acc)
 {
@@ -306,10 +421,12 @@ __global__ void __launch_bounds__(kThreadsA, kCtasPerSm) adjoint_kernel(const Ad
     using V = typename C2T<T>::type;
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = a.N, NE = a.NE;
-    Smem sm;
+    Smem<T> sm;
     unsigned char *p = smem;
-    sm.cdiag = reinterpret_cast<double *>(p);
+    sm.cacc = reinterpret_cast<T *>(p);
     p += sizeof(double) * 2 * N;
+    sm.bacc = reinterpret_cast<T *>(p);
+    p += sizeof(double) * std::max(a.B, 1);
     sm.gt = reinterpret_cast<double *>(p);
     p += sizeof(double) * std::max(a.B, 1);
     sm.gn = reinterpret_cast<double *>(p);
@@ -508,7 +625,7 @@ static int launch_adjoint_t(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, 
     const int NE = N * (N + 1);
     const int n_seg = (int)(n_steps / ckpt_every);
     const long long stride = (long long)(n_seg + ckpt_every + 1 + 12) * NE;
-    const int smem_tables = (int)(sizeof(double) * (4 * N + std::max(p->B, 1)) + sizeof(int32_t) * 4 * N +
+    const int smem_tables = (int)(sizeof(double) * (4 * N + 2 * std::max(p->B, 1)) + sizeof(int32_t) * 4 * N +
                                   sizeof(int32_t) * 2 * std::max(p->B, 1) + sizeof(uint32_t) * NE + 64);
     const int grid = (int)std::min<long long>(M, (long long)kCtasPerSm * std::max(1, p->sm_count));
     const size_t bytes = sizeof(V) * (size_t)stride * grid;

@@ -103,7 +103,7 @@ def test_gradcheck(ftwa):
 def test_fp32_and_partial_requires_grad(ftwa):
     """FP32 plan gradients within 2e-3 of FP64; inputs without requires_grad
     receive none; a second backward through a retained graph repeats the
-    first (to rounding: the adjoint sums samples with atomics)."""
+    first (to rounding: the adjoint sums with atomics)."""
     lat, n0 = _setup()
     res = []
     for precision in (0, 1):
@@ -116,9 +116,11 @@ def test_fp32_and_partial_requires_grad(ftwa):
         first = (U.grad.clone(), tb.grad.clone())
         U.grad, tb.grad = None, None
         L.backward()
-        sc = float(first[1].abs().max())           # sample sums are reduced with atomics: equal to rounding
-        assert abs(float(U.grad - first[0])) <= 1e-13 * sc
-        assert float((tb.grad - first[1]).abs().max()) <= 1e-13 * sc
+        # sums are reduced with atomics (in FP32 plans partly in FP32): equal
+        # to rounding of the plan's precision
+        sc, rt = float(first[1].abs().max()), (1e-12 if precision == 0 else 1e-6)
+        assert abs(float(U.grad - first[0])) <= rt * sc
+        assert float((tb.grad - first[1]).abs().max()) <= rt * sc
         assert n.grad is None
         res.append(np.concatenate([U.grad.reshape(1).numpy(), tb.grad.numpy()]))
     assert np.abs(res[1] - res[0]).max() <= 2e-3 * np.abs(res[0]).max()

@@ -43,13 +43,11 @@ template <typename T> struct C2T;
 template <> struct C2T<float> { using type = float2; };
 template <> struct C2T<double> { using type = double2; };
 
-// Four samples per SM at a time (256 threads each): the per-sample work is a
-// sequence of dependent passes whose neighbour gathers read L2; independent
-// samples hide its latency.  (Staging each evaluation's input in shared
-// memory, one sample per SM, measured slower: 2.0 s against 1.7 s for 608
-// FP32 samples of the 96-site flake.)
-constexpr int kThreadsA = 256;
-constexpr int kCtasPerSm = 4;
+// Launch shapes: the per-sample work is a sequence of dependent passes over
+// the sample's matrices in a per-CTA workspace (L2-resident when few enough
+// samples are in flight).  FP32 runs one 1024-thread CTA per SM, FP64 four
+// 256-thread CTAs (see launch_adjoint_t).  (Staging each evaluation's input
+// in shared memory, one sample per SM, measured slower.)
 
 template <typename T>
 struct AdjArgs {
@@ -121,43 +119,81 @@ struct Smem {
     int32_t *bxy;       // [B][2]
     T *cacc;            // [2][N] diagonal coupling sums of one VJP
     T *bacc;            // [B] bond sums of one VJP
+    T *wd;              // [2][N] diagonal of W before the coupling
     double *gt;         // [B]
     double *gn;         // [2][N]
 };
 
-// out = f(y) (Eq. 6) on the packed upper triangle
-template <typename T>
-__device__ void f_eval(const AdjArgs<T> &a, const Smem<T> &sm, const typename C2T<T>::type *y,
-                       typename C2T<T>::type *out)
+// One RK4 stage pass on the packed upper triangle, k = f(src) (Eq. 6)
+// combined in the same pass (no separate k buffer):
+//   MODE 0: out = y0 + c k              (stage states of the reverse sweep)
+//   MODE 1: acc = k;      out = y0 + c k
+//   MODE 2: acc += 2 k;   out = y0 + c k
+//   MODE 3: out = y0 + c (acc + k)      (c = h/6: the step's result)
+// out must not alias src (other threads gather src).  With lam != nullptr
+// the pass also starts the reverse step's cotangents: g4 = h/6 lam,
+// lam_new = lam.  Ends with a CTA barrier.
+template <int MODE, typename T>
+__device__ void f_pass(const AdjArgs<T> &a, const Smem<T> &sm, const typename C2T<T>::type *src,
+                       const typename C2T<T>::type *y0, typename C2T<T>::type *acc, typename C2T<T>::type *out,
+                       T c, const typename C2T<T>::type *lam = nullptr, typename C2T<T>::type *g4 = nullptr,
+                       typename C2T<T>::type *lam_new = nullptr)
 {
     using V = typename C2T<T>::type;
     const int N = a.N;
+    const T h6 = a.dt / T(6);
     for (int e = threadIdx.x; e < a.NE; e += blockDim.x) {
         const uint32_t d = sm.elem[e];
         const int i = d & 0xFF, j = (d >> 8) & 0xFF, s = d >> 16;
         const int nj = sm.nbr[j], ni = sm.nbr[i];
         T hr = T(0), hi = T(0);
         for (int n = 0; n < ((nj >> 24) & 0xFF); ++n) {
-            const V v = getc(y, N, s, i, (nj >> (8 * n)) & 0xFF);
+            const V v = getc(src, N, s, i, (nj >> (8 * n)) & 0xFF);
             const T t = a.tnb[4 * j + n];
             hr = fma(t, v.x, hr);
             hi = fma(t, v.y, hi);
         }
         for (int n = 0; n < ((ni >> 24) & 0xFF); ++n) {
-            const V v = getc(y, N, s, (ni >> (8 * n)) & 0xFF, j);
+            const V v = getc(src, N, s, (ni >> (8 * n)) & 0xFF, j);
             const T t = a.tnb[4 * i + n];
             hr = fma(-t, v.x, hr);
             hi = fma(-t, v.y, hi);
         }
-        const V own = y[e];
-        const T g = a.U * (y[pidx(N, 1 - s, i, i)].x - y[pidx(N, 1 - s, j, j)].x);
+        const V own = src[e];
+        const T g = a.U * (src[pidx(N, 1 - s, i, i)].x - src[pidx(N, 1 - s, j, j)].x);
         hr = fma(g, own.x, hr);
         hi = fma(g, own.y, hi);
+        V k;
+        k.x = -hi;
+        k.y = (i == j) ? T(0) : hr;
+        const V b = y0[e];
         V o;
-        o.x = -hi;
-        o.y = (i == j) ? T(0) : hr;
+        if constexpr (MODE == 3) {
+            const V q = acc[e];
+            o.x = fma(c, q.x + k.x, b.x);
+            o.y = fma(c, q.y + k.y, b.y);
+        } else {
+            if constexpr (MODE == 1) acc[e] = k;
+            if constexpr (MODE == 2) {
+                V q = acc[e];
+                q.x = fma(T(2), k.x, q.x);
+                q.y = fma(T(2), k.y, q.y);
+                acc[e] = q;
+            }
+            o.x = fma(c, k.x, b.x);
+            o.y = fma(c, k.y, b.y);
+        }
         out[e] = o;
+        if (lam) {
+            const V l = lam[e];
+            V q;
+            q.x = h6 * l.x;
+            q.y = h6 * l.y;
+            g4[e] = q;
+            lam_new[e] = l;
+        }
     }
+    __syncthreads();
 }
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -166,8 +202,30 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// w = VJP_f(Y)[v] for FP32 plans; accumulates dL/dU (register) and dL/dt_b
-// (shared memory), in one pass over the stored upper triangle, a warp per row (coalesced):
+// Cotangent bookkeeping of one reversed RK4 stage for element e with
+// W = VJP(Y_s)[G_s]: lam_new += W and the next stage's G = ca lam + cb W, or,
+// for the first stage (last = true), lam = lam_new + W.
+template <typename V, typename T>
+__device__ __forceinline__ void cot_update(int e, V o, V *gout, V *lam, V *lam_new, T ca, T cb, bool last)
+{
+    V ln = lam_new[e];
+    ln.x += o.x;
+    ln.y += o.y;
+    if (last) {
+        lam[e] = ln;
+    } else {
+        lam_new[e] = ln;
+        const V l = lam[e];
+        V g;
+        g.x = fma(cb, o.x, ca * l.x);
+        g.y = fma(cb, o.y, ca * l.y);
+        gout[e] = g;
+    }
+}
+
+// W = VJP_f(Y)[v] for FP32 plans, with the cotangent update of the stage
+// (cot_update) fused; accumulates dL/dU (register) and dL/dt_b (shared
+// memory), in one pass over the stored upper triangle, a warp per row (coalesced):
 //  - elementwise: w = -f_D(v) with D from Y, and the U gradient;
 //  - the U term's coupling to the other spin's diagonal,
 //      c_k = -2U sum_j P_kj,  P_kj = Im(conj(v_kj) Y_kj)   (full row k);
@@ -185,7 +243,8 @@ __device__ __forceinline__ double warp_sum(double v)
 // shared memory (distinct columns per lane: little contention).
 template <typename T>
 __device__ void vjp_rows(const AdjArgs<T> &a, const Smem<T> &sm, const typename C2T<T>::type *Y,
-                    const typename C2T<T>::type *v, typename C2T<T>::type *w, double &gU)
+                         const typename C2T<T>::type *v, typename C2T<T>::type *gout, typename C2T<T>::type *lam,
+                         typename C2T<T>::type *lam_new, T ca, T cb, bool last, double &gU)
 {
     using V = typename C2T<T>::type;
     const int N = a.N;
@@ -235,13 +294,15 @@ __device__ void vjp_rows(const AdjArgs<T> &a, const Smem<T> &sm, const typename 
             // w = -i (hr + i hi) = (hi, -hr)
             V o;
             o.x = hi;
-            o.y = (i == j) ? T(0) : -hr;
-            w[e] = o;
+            o.y = -hr;
             if (i != j) {
                 const T P = vo.x * yo.y - vo.y * yo.x;   // Im(conj(v_ij) Y_ij)
                 gu = fma(di - dj, P, gu);
                 ci += P;
                 atomicAdd(&sm.cacc[s * N + j], -P);
+                cot_update(e, o, gout, lam, lam_new, ca, cb, last);
+            } else {
+                sm.wd[s * N + i] = hi;   // the coupling is added once all rows are done
             }
         }
         // dL/dU: weight 2, the stored (i, j) stands for (i, j) and (j, i); the
@@ -258,11 +319,14 @@ __device__ void vjp_rows(const AdjArgs<T> &a, const Smem<T> &sm, const typename 
         }
     }
     __syncthreads();
-    // coupling to the other spin's diagonal; bond sums into the CTA's totals
+    // diagonal elements: w_kk,s plus the coupling c of row (sbar, k); bond
+    // sums into the CTA's totals
     for (int e = threadIdx.x; e < 2 * N; e += blockDim.x) {
         const int s = e / N, k = e % N;
-        V &x = w[pidx(N, 1 - s, k, k)];
-        x.x += (T)(-2.0 * (double)a.U * (double)sm.cacc[e]);
+        V o;
+        o.x = sm.wd[e] + (T)(-2.0 * (double)a.U * (double)sm.cacc[(1 - s) * N + k]);
+        o.y = T(0);
+        cot_update(pidx(N, s, k, k), o, gout, lam, lam_new, ca, cb, last);
     }
     for (int b = threadIdx.x; b < a.B; b += blockDim.x) sm.gt[b] += -2.0 * (double)sm.bacc[b];
     __syncthreads();
@@ -353,70 +417,22 @@ __device__ void vjp_dot(const AdjArgs<T> &a, const Smem<T> &sm, const typename C
     __syncthreads();
 }
 
-template <typename T>
-__device__ __forceinline__ void vjp(const AdjArgs<T> &a, const Smem<T> &sm, const typename C2T<T>::type *Y,
-                                    const typename C2T<T>::type *v, typename C2T<T>::type *w, double &gU)
-{
-    if constexpr (std::is_same<T, double>::value) vjp_dot(a, sm, Y, v, w, gU);
-    else vjp_rows(a, sm, Y, v, w, gU);
-}
-
-template <typename V, typename T>
-__device__ __forceinline__ void axpy(int NE, V *out, const V *x, T c, const V *y)   // out = x + c y
-{
-    for (int e = threadIdx.x; e < NE; e += blockDim.x) {
-        V r;
-        r.x = fma(c, y[e].x, x[e].x);
-        r.y = fma(c, y[e].y, x[e].y);
-        out[e] = r;
-    }
-    __syncthreads();
-}
-
-// one RK4 step: y1 = y0 + h/6 (k1 + 2 k2 + 2 k3 + k4) (k, ys, acc scratch)
+// one RK4 step y1 = y0 + h/6 (k1 + 2 k2 + 2 k3 + k4) in four fused passes
+// (ys, ys2: stage states; acc: the weighted sum of the k's)
 template <typename T>
 __device__ void rk4(const AdjArgs<T> &a, const Smem<T> &sm, const typename C2T<T>::type *y0,
-                    typename C2T<T>::type *y1, typename C2T<T>::type *k, typename C2T<T>::type *ys,
+                    typename C2T<T>::type *y1, typename C2T<T>::type *ys, typename C2T<T>::type *ys2,
                     typename C2T<T>::type *acc)
 {
     const T h = a.dt;
-    f_eval(a, sm, y0, k);
-    __syncthreads();
-    for (int e = threadIdx.x; e < a.NE; e += blockDim.x) {
-        acc[e] = k[e];
-        ys[e].x = fma(h * T(0.5), k[e].x, y0[e].x);
-        ys[e].y = fma(h * T(0.5), k[e].y, y0[e].y);
-    }
-    __syncthreads();
-    f_eval(a, sm, ys, k);
-    __syncthreads();
-    for (int e = threadIdx.x; e < a.NE; e += blockDim.x) {
-        acc[e].x = fma(T(2), k[e].x, acc[e].x);
-        acc[e].y = fma(T(2), k[e].y, acc[e].y);
-        ys[e].x = fma(h * T(0.5), k[e].x, y0[e].x);
-        ys[e].y = fma(h * T(0.5), k[e].y, y0[e].y);
-    }
-    __syncthreads();
-    f_eval(a, sm, ys, k);
-    __syncthreads();
-    for (int e = threadIdx.x; e < a.NE; e += blockDim.x) {
-        acc[e].x = fma(T(2), k[e].x, acc[e].x);
-        acc[e].y = fma(T(2), k[e].y, acc[e].y);
-        ys[e].x = fma(h, k[e].x, y0[e].x);
-        ys[e].y = fma(h, k[e].y, y0[e].y);
-    }
-    __syncthreads();
-    f_eval(a, sm, ys, k);
-    __syncthreads();
-    for (int e = threadIdx.x; e < a.NE; e += blockDim.x) {
-        y1[e].x = fma(h / T(6), acc[e].x + k[e].x, y0[e].x);
-        y1[e].y = fma(h / T(6), acc[e].y + k[e].y, y0[e].y);
-    }
-    __syncthreads();
+    f_pass<1>(a, sm, y0, y0, acc, ys, h * T(0.5));
+    f_pass<2>(a, sm, ys, y0, acc, ys2, h * T(0.5));
+    f_pass<2>(a, sm, ys2, y0, acc, ys, h);
+    f_pass<3>(a, sm, ys, y0, acc, y1, h / T(6));
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreadsA, kCtasPerSm) adjoint_kernel(const AdjArgs<T> a)
+template <typename T, int THREADS, int CTAS>
+__global__ void __launch_bounds__(THREADS, CTAS) adjoint_kernel(const AdjArgs<T> a)
 {
     using V = typename C2T<T>::type;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -427,6 +443,8 @@ __global__ void __launch_bounds__(kThreadsA, kCtasPerSm) adjoint_kernel(const Ad
     p += sizeof(double) * 2 * N;
     sm.bacc = reinterpret_cast<T *>(p);
     p += sizeof(double) * std::max(a.B, 1);
+    sm.wd = reinterpret_cast<T *>(p);
+    p += sizeof(double) * 2 * N;
     sm.gt = reinterpret_cast<double *>(p);
     p += sizeof(double) * std::max(a.B, 1);
     sm.gn = reinterpret_cast<double *>(p);
@@ -459,7 +477,7 @@ __global__ void __launch_bounds__(kThreadsA, kCtasPerSm) adjoint_kernel(const Ad
     V *ckpt = ws;                                         // [n_seg][NE]
     V *seg = ckpt + (long long)n_seg * NE;                // [ckpt_every + 1][NE]
     V *Y2 = seg + (long long)(a.ckpt_every + 1) * NE;
-    V *Y3 = Y2 + NE, *Y4 = Y3 + NE, *K = Y4 + NE, *A = K + NE, *lam = A + NE, *G = lam + NE, *W = G + NE,
+    V *Y3 = Y2 + NE, *Y4 = Y3 + NE, *A = Y4 + NE, *lam = A + NE, *G = lam + NE, *W = G + NE,
       *lam_new = W + NE, *cur = lam_new + NE, *nxt = cur + NE;
     const T h = a.dt;
     const int twoN = 2 * N;
@@ -493,7 +511,7 @@ __global__ void __launch_bounds__(kThreadsA, kCtasPerSm) adjoint_kernel(const Ad
                 for (int e = threadIdx.x; e < NE; e += blockDim.x) c[e] = cur[e];
                 __syncthreads();
             }
-            rk4(a, sm, cur, nxt, K, Y2, A);
+            rk4(a, sm, cur, nxt, Y2, Y3, A);
             V *t = cur;
             cur = nxt;
             nxt = t;
@@ -518,56 +536,51 @@ __global__ void __launch_bounds__(kThreadsA, kCtasPerSm) adjoint_kernel(const Ad
         for (int sg = n_seg - 1; sg >= 0; --sg) {
             for (int e = threadIdx.x; e < NE; e += blockDim.x) seg[e] = ckpt[(long long)sg * NE + e];
             __syncthreads();
-            for (int r = 0; r < a.ckpt_every; ++r) rk4(a, sm, seg + (long long)r * NE, seg + (long long)(r + 1) * NE, K, Y2, A);
+            for (int r = 0; r < a.ckpt_every; ++r) rk4(a, sm, seg + (long long)r * NE, seg + (long long)(r + 1) * NE, Y2, Y3, A);
             for (int r = a.ckpt_every - 1; r >= 0; --r) {
                 const V *y = seg + (long long)r * NE;
-                // stage states
-                f_eval(a, sm, y, K);
-                __syncthreads();
-                axpy(NE, Y2, y, h * T(0.5), K);
-                f_eval(a, sm, Y2, K);
-                __syncthreads();
-                axpy(NE, Y3, y, h * T(0.5), K);
-                f_eval(a, sm, Y3, K);
-                __syncthreads();
-                axpy(NE, Y4, y, h, K);
-                // stage 4
-                for (int e = threadIdx.x; e < NE; e += blockDim.x) {
-                    G[e].x = h / T(6) * lam[e].x;
-                    G[e].y = h / T(6) * lam[e].y;
-                    lam_new[e] = lam[e];
+                // stage states Y2..Y4 (and G = h/6 lam, lam_new = lam)
+                f_pass<0>(a, sm, y, y, (V *)nullptr, Y2, h * T(0.5), lam, G, lam_new);
+                f_pass<0>(a, sm, Y2, y, (V *)nullptr, Y3, h * T(0.5));
+                f_pass<0>(a, sm, Y3, y, (V *)nullptr, Y4, h);
+                if constexpr (std::is_same<T, float>::value) {
+                    // stage cotangents alternate between G and W
+                    vjp_rows(a, sm, Y4, G, W, lam, lam_new, h / T(3), h, false, gU);
+                    vjp_rows(a, sm, Y3, W, G, lam, lam_new, h / T(3), h * T(0.5), false, gU);
+                    vjp_rows(a, sm, Y2, G, W, lam, lam_new, h / T(6), h * T(0.5), false, gU);
+                    vjp_rows(a, sm, y, W, (V *)nullptr, lam, lam_new, T(0), T(0), true, gU);
+                } else {
+                    vjp_dot(a, sm, Y4, G, W, gU);
+                    for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+                        lam_new[e].x += W[e].x;
+                        lam_new[e].y += W[e].y;
+                        G[e].x = fma(h, W[e].x, h / T(3) * lam[e].x);
+                        G[e].y = fma(h, W[e].y, h / T(3) * lam[e].y);
+                    }
+                    __syncthreads();
+                    vjp_dot(a, sm, Y3, G, W, gU);
+                    for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+                        lam_new[e].x += W[e].x;
+                        lam_new[e].y += W[e].y;
+                        G[e].x = fma(h * T(0.5), W[e].x, h / T(3) * lam[e].x);
+                        G[e].y = fma(h * T(0.5), W[e].y, h / T(3) * lam[e].y);
+                    }
+                    __syncthreads();
+                    vjp_dot(a, sm, Y2, G, W, gU);
+                    for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+                        lam_new[e].x += W[e].x;
+                        lam_new[e].y += W[e].y;
+                        G[e].x = fma(h * T(0.5), W[e].x, h / T(6) * lam[e].x);
+                        G[e].y = fma(h * T(0.5), W[e].y, h / T(6) * lam[e].y);
+                    }
+                    __syncthreads();
+                    vjp_dot(a, sm, y, G, W, gU);
+                    for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+                        lam[e].x = lam_new[e].x + W[e].x;
+                        lam[e].y = lam_new[e].y + W[e].y;
+                    }
+                    __syncthreads();
                 }
-                __syncthreads();
-                vjp(a, sm, Y4, G, W, gU);
-                for (int e = threadIdx.x; e < NE; e += blockDim.x) {
-                    lam_new[e].x += W[e].x;
-                    lam_new[e].y += W[e].y;
-                    G[e].x = fma(h, W[e].x, h / T(3) * lam[e].x);
-                    G[e].y = fma(h, W[e].y, h / T(3) * lam[e].y);
-                }
-                __syncthreads();
-                vjp(a, sm, Y3, G, W, gU);
-                for (int e = threadIdx.x; e < NE; e += blockDim.x) {
-                    lam_new[e].x += W[e].x;
-                    lam_new[e].y += W[e].y;
-                    G[e].x = fma(h * T(0.5), W[e].x, h / T(3) * lam[e].x);
-                    G[e].y = fma(h * T(0.5), W[e].y, h / T(3) * lam[e].y);
-                }
-                __syncthreads();
-                vjp(a, sm, Y2, G, W, gU);
-                for (int e = threadIdx.x; e < NE; e += blockDim.x) {
-                    lam_new[e].x += W[e].x;
-                    lam_new[e].y += W[e].y;
-                    G[e].x = fma(h * T(0.5), W[e].x, h / T(6) * lam[e].x);
-                    G[e].y = fma(h * T(0.5), W[e].y, h / T(6) * lam[e].y);
-                }
-                __syncthreads();
-                vjp(a, sm, y, G, W, gU);
-                for (int e = threadIdx.x; e < NE; e += blockDim.x) {
-                    lam[e].x = lam_new[e].x + W[e].x;
-                    lam[e].y = lam_new[e].y + W[e].y;
-                }
-                __syncthreads();
                 inject((long long)sg * a.ckpt_every + r);
             }
         }
@@ -592,7 +605,7 @@ __global__ void __launch_bounds__(kThreadsA, kCtasPerSm) adjoint_kernel(const Ad
         __syncthreads();
     }
     // ---- publish this CTA's sums -------------------------------------------------
-    __shared__ double red[kThreadsA / 32];
+    __shared__ double red[THREADS / 32];
     double v = gU;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
@@ -624,10 +637,14 @@ static int launch_adjoint_t(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, 
     const int N = p->N;
     const int NE = N * (N + 1);
     const int n_seg = (int)(n_steps / ckpt_every);
-    const long long stride = (long long)(n_seg + ckpt_every + 1 + 12) * NE;
-    const int smem_tables = (int)(sizeof(double) * (4 * N + 2 * std::max(p->B, 1)) + sizeof(int32_t) * 4 * N +
+    const long long stride = (long long)(n_seg + ckpt_every + 1 + 11) * NE;
+    const int smem_tables = (int)(sizeof(double) * (6 * N + 2 * std::max(p->B, 1)) + sizeof(int32_t) * 4 * N +
                                   sizeof(int32_t) * 2 * std::max(p->B, 1) + sizeof(uint32_t) * NE + 64);
-    const int grid = (int)std::min<long long>(M, (long long)kCtasPerSm * std::max(1, p->sm_count));
+    // FP32: one 1024-thread CTA per SM, so that the samples in flight keep
+    // their working sets in L2 (measured 1.4x faster than four 256-thread
+    // CTAs); FP64 is bound by the FP64 pipe either way
+    const int ctas = std::is_same<T, float>::value ? 1 : 4, threads = 1024 / ctas;
+    const int grid = (int)std::min<long long>(M, (long long)ctas * std::max(1, p->sm_count));
     const size_t bytes = sizeof(V) * (size_t)stride * grid;
     if (p->adj_ws_bytes < bytes) {
         cudaFree(p->d_adj_ws);
@@ -667,9 +684,10 @@ static int launch_adjoint_t(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, 
     a.status = p->d_status;
     const int smem = smem_tables;
     if (smem > 227 * 1024) return FTWA_ERR_UNSUPPORTED;
-    cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    auto kern = ctas == 4 ? adjoint_kernel<T, 256, 4> : adjoint_kernel<T, 1024, 1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return set_cuda_error(e);
-    adjoint_kernel<T><<<grid, kThreadsA, smem, s>>>(a);
+    kern<<<grid, threads, smem, s>>>(a);
     return set_cuda_error(cudaGetLastError());
 }
 

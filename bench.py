@@ -680,6 +680,35 @@ def run_profile_gram(args):
         raise SystemExit(1)
 
 
+def run_profile_adjoint(args):
+    """A small adjoint case for ncu: 96-site flake, U/t = 1.6, softened Neel
+    occupations, 608 samples (one per CTA slot), 50 RK4 steps, checkpoints and
+    outputs every 10 steps, repeated --prof-repeat times (CUDA-event times)."""
+    import torch
+    import paper_2212_04352_gb300 as F
+    import workloads as W
+    lat = W.hexagonal_flake(4)
+    nu, nd = W.neel_state(lat)
+    nu, nd = W.softened(nu), W.softened(nd)
+    M, steps, every, ckpt = 608, 50, 10, 10
+    prec = F.FTWA_FP64 if args.precision == "fp64" else F.FTWA_FP32
+    times = []
+    with F.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=prec, out_every=every) as P:
+        g = torch.full((steps // every + 1, 2 * lat.n_sites), 0.3, dtype=torch.float64, device="cuda")
+        for _ in range(args.prof_repeat):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            P.adjoint(1, M, steps, ckpt, g)
+            e.record()
+            torch.cuda.synchronize()
+            times.append(s.elapsed_time(e))
+        st = P.status()
+    print(json.dumps({"profile_adjoint": True, "precision": args.precision, "samples": M, "steps": steps,
+                      "ms": times, "status": st}))
+    if st != 0:
+        raise SystemExit(1)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -708,6 +737,7 @@ def main():
     ap.add_argument("--gram-times", type=int, default=200)
     ap.add_argument("--profile", action="store_true", help="small case for ncu captures")
     ap.add_argument("--profile-gram", action="store_true", help="small Gram case for ncu captures")
+    ap.add_argument("--profile-adjoint", action="store_true", help="small adjoint case for ncu captures")
     ap.add_argument("--prof-steps", type=int, default=20)
     ap.add_argument("--prof-repeat", type=int, default=2)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
@@ -720,6 +750,9 @@ def main():
         return
     if args.profile_gram:
         run_profile_gram(args)
+        return
+    if args.profile_adjoint:
+        run_profile_adjoint(args)
         return
     if args.warmup < 3 and args.impl == "native":
         print("note: fewer than 3 warm-up steps; the timing contract asks for >= 3", file=sys.stderr)

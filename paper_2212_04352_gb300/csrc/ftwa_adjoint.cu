@@ -147,13 +147,16 @@ __device__ void f_pass(const AdjArgs<T> &a, const Smem<T> &sm, const typename C2
         const int i = d & 0xFF, j = (d >> 8) & 0xFF, s = d >> 16;
         const int nj = sm.nbr[j], ni = sm.nbr[i];
         T hr = T(0), hi = T(0);
-        for (int n = 0; n < ((nj >> 24) & 0xFF); ++n) {
+        // all three slots: an empty slot has t = 0 and a valid column
+#pragma unroll
+        for (int n = 0; n < 3; ++n) {
             const V v = getc(src, N, s, i, (nj >> (8 * n)) & 0xFF);
             const T t = a.tnb[4 * j + n];
             hr = fma(t, v.x, hr);
             hi = fma(t, v.y, hi);
         }
-        for (int n = 0; n < ((ni >> 24) & 0xFF); ++n) {
+#pragma unroll
+        for (int n = 0; n < 3; ++n) {
             const V v = getc(src, N, s, (ni >> (8 * n)) & 0xFF, j);
             const T t = a.tnb[4 * i + n];
             hr = fma(-t, v.x, hr);
@@ -263,21 +266,25 @@ __device__ void vjp_rows(const AdjArgs<T> &a, const Smem<T> &sm, const typename 
             const int nj = sm.nbr[j], degj = (nj >> 24) & 0xFF;
             const V vo = v[e], yo = Y[e];
             T hr = T(0), hi = T(0);
-            // row part: neighbours k of j
-            for (int n = 0; n < degj; ++n) {
+            // row part: neighbours k of j (all three slots: an empty slot has
+            // t = 0 and a valid column, so the loads are unconditional)
+#pragma unroll
+            for (int n = 0; n < 3; ++n) {
                 const int k = (nj >> (8 * n)) & 0xFF;
                 const V vk = getc(v, N, s, i, k);
                 const T t = a.tnb[4 * j + n];
                 hr = fma(t, vk.x, hr);
                 hi = fma(t, vk.y, hi);
-                if (i != j) {
+                if (i != j && n < degj) {
                     // Im(conj(v_ij) Y_ik) -> bond (j, k)
                     const V yk = getc(Y, N, s, i, k);
                     atomicAdd(&sm.bacc[sm.bond[3 * j + n]], vo.x * yk.y - vo.y * yk.x);
                 }
             }
-            // column part: neighbours k of i
-            for (int n = 0; n < degi; ++n) {
+            // column part: neighbours k of i (empty slots accumulate into bi[n]
+            // but are never flushed)
+#pragma unroll
+            for (int n = 0; n < 3; ++n) {
                 const int k = (ni >> (8 * n)) & 0xFF;
                 const V vk = getc(v, N, s, k, j);
                 const T t = a.tnb[4 * i + n];
@@ -356,14 +363,16 @@ __device__ void vjp_dot(const AdjArgs<T> &a, const Smem<T> &sm, const typename C
         const V vo = v[e], yo = Y[e];
         T hr = T(0), hi = T(0);
         // row part: neighbours k of j
-        for (int n = 0; n < ((nj >> 24) & 0xFF); ++n) {
+#pragma unroll
+        for (int n = 0; n < 3; ++n) {
             const V vk = getc(v, N, s, i, (nj >> (8 * n)) & 0xFF);
             const T t = a.tnb[4 * j + n];
             hr = fma(t, vk.x, hr);
             hi = fma(t, vk.y, hi);
         }
         // column part: neighbours k of i
-        for (int n = 0; n < ((ni >> 24) & 0xFF); ++n) {
+#pragma unroll
+        for (int n = 0; n < 3; ++n) {
             const V vk = getc(v, N, s, (ni >> (8 * n)) & 0xFF, j);
             const T t = a.tnb[4 * i + n];
             hr = fma(-t, vk.x, hr);

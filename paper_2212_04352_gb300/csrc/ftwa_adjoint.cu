@@ -545,7 +545,10 @@ __global__ void __launch_bounds__(THREADS, CTAS) adjoint_kernel(const AdjArgs<T>
         for (int sg = n_seg - 1; sg >= 0; --sg) {
             for (int e = threadIdx.x; e < NE; e += blockDim.x) seg[e] = ckpt[(long long)sg * NE + e];
             __syncthreads();
-            for (int r = 0; r < a.ckpt_every; ++r) rk4(a, sm, seg + (long long)r * NE, seg + (long long)(r + 1) * NE, Y2, Y3, A);
+            // states 1 .. ckpt_every-1 of the segment (the reverse sweep never
+            // reads the last one)
+            for (int r = 0; r + 1 < a.ckpt_every; ++r)
+                rk4(a, sm, seg + (long long)r * NE, seg + (long long)(r + 1) * NE, Y2, Y3, A);
             for (int r = a.ckpt_every - 1; r >= 0; --r) {
                 const V *y = seg + (long long)r * NE;
                 // stage states Y2..Y4 (and G = h/6 lam, lam_new = lam)
@@ -651,7 +654,8 @@ static int launch_adjoint_t(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, 
                                   sizeof(int32_t) * 2 * std::max(p->B, 1) + sizeof(uint32_t) * NE + 64);
     // FP32: one 1024-thread CTA per SM, so that the samples in flight keep
     // their working sets in L2 (measured 1.4x faster than four 256-thread
-    // CTAs); FP64 is bound by the FP64 pipe either way
+    // CTAs, and faster than 768 threads with more registers each); FP64 is
+    // bound by the FP64 pipe either way
     const int ctas = std::is_same<T, float>::value ? 1 : 4, threads = 1024 / ctas;
     const int grid = (int)std::min<long long>(M, (long long)ctas * std::max(1, p->sm_count));
     const size_t bytes = sizeof(V) * (size_t)stride * grid;

@@ -112,3 +112,12 @@ def test_adjoint_checkpoint_default():
     for n_steps, every, want in [(40, 10, 10), (1000, 10, 40), (30, 10, 10), (400, 20, 20), (3600, 10, 60)]:
         c = F._default_ckpt(n_steps, every)
         assert c == want and n_steps % c == 0 and c % every == 0
+
+
+def test_autograd_function_is_exposed():
+    """FTWAFunction is a torch.autograd.Function (created without touching the
+    CUDA library); occupations() is the entry point that applies it."""
+    torch = pytest.importorskip("torch")
+    import paper_2212_04352_gb300 as F
+    assert issubclass(F.FTWAFunction, torch.autograd.Function)
+    assert F.FTWAFunction is F.FTWAFunction and callable(F.occupations)

@@ -120,3 +120,26 @@ def test_adjoint_96_sites_fp64_spot_check(ftwa):
     scale = max(abs(f) for _, f in checks)
     for got, want in checks:
         assert abs(got - want) <= 1e-6 * scale, (got, want)
+
+
+@pytest.mark.parametrize("lat_name", ["flake96", "flake150", "brick198"])
+def test_adjoint_fp32_follows_fp64_large(ftwa, lat_name):
+    """The FP32 adjoint (row-pass VJP, one 1024-thread CTA per SM) against the
+    FP64 adjoint (dot-product VJP) on the larger lattices (8 samples, 20
+    steps).  Gate: 2e-3 of the largest gradient entry (the FP32 gate of the
+    finite-difference test)."""
+    lat = {"flake96": W.hexagonal_flake(4), "flake150": W.hexagonal_flake(5),
+           "brick198": W.brick_wall_flake()}[lat_name]
+    n0u, n0d = W.neel_state(lat)
+    nu, nd = W.softened(n0u), W.softened(n0d)
+    seed, M, steps, every, ckpt = 11, 8, 20, 10, 10
+    rng = np.random.default_rng(2)
+    g = torch.from_numpy(rng.standard_normal((steps // every + 1, 2 * lat.n_sites))).cuda()
+    res = []
+    for precision in (0, 1):
+        with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=precision, out_every=every) as P:
+            res.append([x.cpu().numpy() for x in P.adjoint(seed, M, steps, ckpt, g)])
+            assert P.status() == 0
+    scale = max(np.abs(x).max() for x in res[0])
+    for a, b in zip(res[1], res[0]):
+        assert np.abs(a - b).max() <= 2e-3 * scale

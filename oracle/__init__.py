@@ -6,7 +6,8 @@ no code, header or helper with it and never imports it.  Only ``tests/``,
 ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may use
 it.  Its C part (``ftwa_oracle.c``) is compiled on first use with the host
 gcc; ``ed.py`` and ``closed_forms.py`` hold the independent checks the oracle
-itself is pinned to.
+itself is pinned to; ``adjoint.py`` is the discrete RK4 adjoint (numpy),
+pinned to finite differences of this integration.
 
 Parity status: every function here is pinned by a test in ``tests/``
 (closed forms, worked values of the paper, invariants, exact

@@ -143,3 +143,27 @@ def test_adjoint_fp32_follows_fp64_large(ftwa, lat_name):
     scale = max(np.abs(x).max() for x in res[0])
     for a, b in zip(res[1], res[0]):
         assert np.abs(a - b).max() <= 2e-3 * scale
+
+
+@pytest.mark.parametrize("lat_name,U,ckpt", [("chain10", 1.6, 10), ("periodic8", 2.5, 30), ("flake24", 1.0, 15)])
+def test_adjoint_matches_oracle_adjoint(ftwa, lat_name, U, ckpt):
+    """The GPU adjoint against the oracle's discrete RK4 adjoint (numpy, full
+    matrices, pinned to finite differences at 1e-8) for a random linear loss:
+    FP64 to 1e-10 of the largest gradient entry (the two differ only by
+    rounding), FP32 to 2e-3."""
+    from oracle import adjoint as OA
+    lat = {"chain10": W.hexagon_chain(2), "periodic8": W.periodic_honeycomb(),
+           "flake24": W.hexagonal_flake(2)}[lat_name]
+    n0u, n0d = W.neel_state(lat)
+    nu, nd = W.softened(n0u), W.softened(n0d)
+    N, seed, M, steps, every = lat.n_sites, 9, 5, 30, 5
+    g = np.random.default_rng(3).standard_normal((steps // every + 1, 2 * N))
+    want = OA.adjoint(lat, U, nu, nd, seed, M, 0.01, steps, every, g)
+    scale = max(abs(want[0]), np.abs(want[1]).max(), np.abs(want[2]).max())
+    for precision, tol in ((0, 1e-10), (1, 2e-3)):
+        with ftwa.Plan(lat, U, n_up=nu, n_dn=nd, precision=precision, out_every=every) as P:
+            got = [x.cpu().numpy() for x in P.adjoint(seed, M, steps, ckpt, torch.from_numpy(g).cuda())]
+            assert P.status() == 0
+        assert abs(got[0][0] - want[0]) <= tol * scale
+        assert np.abs(got[1] - want[1]).max() <= tol * scale
+        assert np.abs(got[2] - want[2]).max() <= tol * scale

@@ -422,3 +422,52 @@ def test_hopping_modulation_closed_form():
     assert errs[0] / errs[1] > 12
     z, _ = oracle.evolve(lat, 1.6, r0, 0.01, 100, drive=dict(amp=None, hop=dict(hop, eps=0.0)))
     assert np.array_equal(z, oracle.evolve(lat, 1.6, r0, 0.01, 100)[0])
+
+
+def test_adjoint_oracle_forward_is_eq6():
+    """The adjoint oracle's f (full matrices, numpy) is the C oracle's
+    right-hand side of Eq. 6."""
+    from oracle import adjoint as OA
+    lat = W.hexagon_chain(2)
+    nu, nd = W.softened(W.neel_state(lat)[0]), W.softened(W.neel_state(lat)[1])
+    rho = oracle.sample(lat.n_sites, nu, nd, 5, 1)
+    J = OA.hopping_matrix(lat)
+    assert np.abs(OA.f(J, 1.6, rho) - oracle.rhs(lat, 1.6, rho)).max() <= 1e-14
+
+
+@pytest.mark.parametrize("lat_name,U", [("chain10", 1.6), ("periodic8", 2.5)])
+def test_adjoint_oracle_matches_finite_differences(lat_name, U):
+    """The discrete RK4 adjoint of the oracle against central differences
+    (h = 1e-5, same seed) of the C oracle's integration, for the linear loss
+    L = sum_t sum_k g_tk <n_k>(t): dL/dU, every dL/dt_b and every dL/dn_is
+    (softened occupations) to 1e-8 of the largest entry."""
+    from oracle import adjoint as OA
+    lat = {"chain10": W.hexagon_chain(2), "periodic8": W.periodic_honeycomb()}[lat_name]
+    n0u, n0d = W.neel_state(lat)
+    nu, nd = W.softened(n0u), W.softened(n0d)
+    N, seed, M, steps, every = lat.n_sites, 5, 3, 30, 10
+    g = np.random.default_rng(0).standard_normal((steps // every + 1, 2 * N))
+    gU, gt, gn = OA.adjoint(lat, U, nu, nd, seed, M, 0.01, steps, every, g)
+    tb0 = np.array(lat.t_bond, dtype=np.float64)
+
+    def L(u, tb, a, b):
+        snap, _ = oracle.run(lat, u, a, b, seed, 0, M, 0.01, steps, every, t_bond=tb)
+        return float((g * (snap.mean(axis=1) + 0.5)).sum())
+
+    h = 1e-5
+    fdU = (L(U + h, tb0, nu, nd) - L(U - h, tb0, nu, nd)) / (2 * h)
+    fdt = np.array([(L(U, tb0 + h * e, nu, nd) - L(U, tb0 - h * e, nu, nd)) / (2 * h)
+                    for e in np.eye(lat.n_bonds)])
+    fdn = np.zeros((2, N))
+    for s in range(2):
+        for i in range(N):
+            e = np.zeros(N)
+            e[i] = h
+            if s == 0:
+                fdn[s, i] = (L(U, tb0, nu + e, nd) - L(U, tb0, nu - e, nd)) / (2 * h)
+            else:
+                fdn[s, i] = (L(U, tb0, nu, nd + e) - L(U, tb0, nu, nd - e)) / (2 * h)
+    scale = max(abs(fdU), np.abs(fdt).max(), np.abs(fdn).max())
+    assert abs(gU - fdU) <= 1e-8 * scale
+    assert np.abs(gt - fdt).max() <= 1e-8 * scale
+    assert np.abs(gn - fdn).max() <= 1e-8 * scale

@@ -266,6 +266,74 @@ def test_moments_definitions():
         assert np.allclose(g2[t], g, rtol=1e-12)
 
 
+def _g2_delta_se(x, k, l):
+    """Standard error of the ratio estimator mean(x_k x_l) / (mean(x_k) mean(x_l))
+    by the delta method (per-sample influence function), from the samples."""
+    a, b = x[:, k], x[:, l]
+    A, B, C = np.mean(a * b), a.mean(), b.mean()
+    psi = (a * b - A) / (B * C) - A * (a - B) / (B * B * C) - A * (b - C) / (B * C * C)
+    return psi.std() / math.sqrt(x.shape[0])
+
+
+def test_g2_estimator_equals_wick_at_U0():
+    """Eq. 10 (g2_fTWA) pinned without the estimator's own formula: at U = 0 the
+    method is exact for the quadratic Hamiltonian, so the oracle's g2 output
+    must equal the free-fermion value.  Same spin, Wick (Eq. A4):
+    g2_ij = 1 - |n_ij|^2 / (n_ii n_jj) with n(t) = W diag(n0) W^dagger;
+    opposite spin: the up and down Slater determinants are independent, so
+    g2 = 1 exactly.  |z| < 5 with the delta-method standard error of the ratio
+    (pairs with an occupation below 0.05 are skipped: the ratio is ill
+    conditioned there)."""
+    lat = W.periodic_honeycomb()
+    nu, nd = W.neel_state(lat)
+    N, M = 8, 20000
+    snap, _ = oracle.run(lat, 0.0, nu, nd, 23, 0, M, 0.01, 300, 50)
+    _, _, g2 = oracle.moments(snap)
+    checked = 0
+    for k in range(1, snap.shape[0]):
+        t = 0.5 * k
+        x = snap[k] + 0.5
+        n_up = cf.free_fermion_one_body(lat, nu, t)
+        n_dn = cf.free_fermion_one_body(lat, nd, t)
+        for s, nm in ((0, n_up), (1, n_dn)):
+            d = np.real(np.diag(nm))
+            for i in range(N):
+                for j in range(N):
+                    if i == j or d[i] < 0.05 or d[j] < 0.05:
+                        continue
+                    exact = 1.0 - abs(nm[i, j]) ** 2 / (d[i] * d[j])
+                    kk, ll = s * N + i, s * N + j
+                    z = (g2[k][kk, ll] - exact) / _g2_delta_se(x, kk, ll)
+                    assert abs(z) < 5, (t, s, i, j, g2[k][kk, ll], exact)
+                    checked += 1
+        du, dd = np.real(np.diag(n_up)), np.real(np.diag(n_dn))
+        for i in range(N):
+            for j in range(N):
+                if du[i] < 0.05 or dd[j] < 0.05:
+                    continue
+                z = (g2[k][i, N + j] - 1.0) / _g2_delta_se(x, i, N + j)
+                assert abs(z) < 5, (t, i, j, g2[k][i, N + j])
+                checked += 1
+    assert checked > 500
+
+
+def test_g2_short_time_limit_app_c():
+    """App. C, Eq. C8 (form_g_st_2): for a filled site next to an empty site
+    whose three bonds all have hopping j, the same-spin g2 tends to
+    (3 j^2 - j^2) / (3 j^2) = 2/3 as t -> 0+ (independent of U).  Statistical
+    check of the oracle's g2 at t = 0.05 on the 8-site periodic lattice
+    (Neel start, U = 1.6): the mean over the 12 bonds, spin up, is within 0.02
+    of 2/3 (sampling error about 0.004 at M = 200000; the O(t) correction is
+    smaller)."""
+    vals = {r[0]: float(r[1]) for r in read_golden("paper_values.txt")}
+    lat = W.periodic_honeycomb()
+    nu, nd = W.neel_state(lat)
+    snap, _ = oracle.run(lat, 1.6, nu, nd, 29, 0, 200000, 0.01, 5, 5)
+    _, _, g2 = oracle.moments(snap)
+    bond_vals = [g2[1][i, j] for (i, j) in lat.bonds]
+    assert abs(np.mean(bond_vals) - vals["g2_short_time_three_neighbours"]) < 0.02
+
+
 def test_paper_asymptotes():
     vals = {r[0]: float(r[1]) for r in read_golden("paper_values.txt")}
     for n in [4, 6, 10]:

@@ -163,8 +163,21 @@ def cpu_baseline(seconds_target=15.0):
     t0 = time.perf_counter()
     oracle.run(wl["lat"], wl["U"], wl["n_up"], wl["n_dn"], 2, 0, S, 0.01, n2, 10, threads=threads)
     dt = time.perf_counter() - t0
-    return {"value": S * n2 / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+    return {"value": S * n2 / dt, "unit": UNIT, "cores": threads, "cpu_model": cpu_model(), "kind": "oracle",
             "sample": f"{S} samples x {n2} RK4 steps of the 198-site workload (FP64 C oracle, OpenMP)"}
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu), for the CPU baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def run_reference(args):
@@ -196,7 +209,8 @@ def run_reference(args):
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                       "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                       "config": config_dict(wl, {"reference_sample": sample}),
-                      "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+                      "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "cpu_model": cpu_model(),
+                                       "kind": "oracle", "sample": sample},
                       "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
@@ -500,6 +514,9 @@ def run_gpu(args):
             ev[k][1].record(stream)
         check(lib.ftwa_moments(P._h, ctypes.c_void_p(X.data_ptr()), M, T, ctypes.c_void_p(occ.data_ptr()),
                                ctypes.c_void_p(conn.data_ptr()), ctypes.c_void_p(g2.data_ptr()), 0, sp), "moments")
+        if ws > 1:
+            # exchange step: the estimators over the union of all ranks' samples
+            shard.combine_moments(M, occ, conn, ws)
 
     for _ in range(args.warmup):
         one_step(0, False)
@@ -622,7 +639,8 @@ def run_gpu(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": config_dict(wl, {"parallelism": f"samples split over {ws} GPU(s), no collective",
+            "config": config_dict(wl, {"parallelism": f"samples split over {ws} GPU(s); estimators all-reduced "
+                                                        f"at the end of each step when more than one",
                                        "launch": info}),
             "e2e": e2e, "roofline": roof, "clocks": clk, "gpu_launches": 4 * args.steps,
             "evolve_ms": evolve_ms, "fp64": fp64, **extra}
@@ -716,7 +734,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--samples", type=int, default=16384)
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--fp64-samples", type=int, default=512)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")

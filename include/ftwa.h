@@ -281,15 +281,22 @@ int ftwa_adjoint(ftwa_plan_t *plan, uint64_t seed, int64_t M, int64_t n_steps, i
  * means, is a static device array of FTWA_MOMENTS_NOALLOC_MAX_TK doubles
  * (1 MiB, held by every device that loads the library until the process
  * exits); n_times * 2 n_sites beyond that limit is rejected with
- * FTWA_ERR_UNSUPPORTED.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  Every call shares the array and
- * overwrites the entries it uses before reading them, so nothing needs
- * clearing; calls whose work overlaps on the GPU (other streams, other host
- * threads) race on it and must be serialised by the caller.  Errors:
- * FTWA_ERR_INVALID_ARGUMENT (null snap/occ/conn, M < 1, n_times < 1,
- * n_sites outside [1, FTWA_MAX_SITES], bad precision), FTWA_ERR_UNSUPPORTED
- * (size limit), FTWA_ERR_CUDA. */
+ * FTWA_ERR_UNSUPPORTED, and so is n_times > 65535.  Each call on a stream
+ * that is not capturing looks up the array's device address
+ * (cudaGetSymbolAddress) with the calling device current, so a device reset
+ * or another current context between calls is followed; a call on a
+ * capturing stream reuses the address of the last non-capturing call on the
+ * device (FTWA_ERR_UNSUPPORTED if there was none), so make a first call
+ * before any stream capture and do not reset the device between that call
+ * and a capture.  Every call shares the array and overwrites the entries it
+ * uses before reading them, so nothing needs clearing; calls whose work
+ * overlaps on the GPU (other streams, other host threads) race on it and
+ * must be serialised by the caller.  The means are plain FP64 sums in a
+ * fixed order (for FP32 snapshots ftwa_moments uses an exact fixed-point sum
+ * instead, so the two agree to rounding, about 1e-14, not bit for bit).
+ * Errors: FTWA_ERR_INVALID_ARGUMENT (null snap/occ/conn, M < 1,
+ * n_times < 1, n_sites outside [1, FTWA_MAX_SITES], bad precision),
+ * FTWA_ERR_UNSUPPORTED (size limits), FTWA_ERR_CUDA. */
 #define FTWA_MOMENTS_NOALLOC_MAX_TK  131072
 int ftwa_moments_noalloc(const void *snap_dev, int32_t precision, int32_t n_sites, int64_t M, int32_t n_times,
                          double *occ_dev, double *conn_dev, double *g2_dev, void *stream);

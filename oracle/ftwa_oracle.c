@@ -446,6 +446,8 @@ void orc_moments(int64_t T, int64_t M, int64_t K, const double *X, double *occ, 
             mu[k] /= (double)M;
             occ[t * K + k] = mu[k] + 0.5;
         }
+        /* entries are independent: one thread per row k (same sums, same order) */
+#pragma omp parallel for schedule(dynamic)
         for (int64_t k = 0; k < K; ++k)
             for (int64_t l = 0; l < K; ++l) {
                 double c = 0.0, g = 0.0;

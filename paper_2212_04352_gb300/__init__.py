@@ -188,6 +188,11 @@ class Plan:
     def adjoint(self, seed, M, n_steps, ckpt_every, dL_docc, stream=None):
         """(dL/dU [1], dL/dt_b [n_bonds], dL/dn0 [2, N]), float64 device tensors."""
         import torch
+        want = (int(n_steps) // self.out_every + 1, 2 * self.N)
+        if tuple(dL_docc.shape) != want:
+            raise ValueError(f"dL_docc must be [n_steps/out_every + 1, 2N] = {want}, got {tuple(dL_docc.shape)}")
+        if not dL_docc.is_cuda:
+            raise ValueError("dL_docc must be a CUDA tensor")
         dev = dL_docc.device
         gU = torch.zeros(1, dtype=torch.float64, device=dev)
         gt = torch.zeros(self.n_bonds, dtype=torch.float64, device=dev)
@@ -405,13 +410,32 @@ def moments_noalloc(X, precision, n_sites, g2=True, stream=None, out=None):
     given precision; ``out`` = (occ, conn, g2-or-None) preallocated float64
     tensors, or None to have them allocated here by torch."""
     import torch
+    if X.dim() != 3:
+        raise ValueError(f"X must be [T, M, 2N], got shape {tuple(X.shape)}")
     T, M, K = X.shape
+    want = torch.float64 if int(precision) == FTWA_FP64 else torch.float32
+    if int(precision) not in (FTWA_FP64, FTWA_FP32):
+        raise ValueError(f"precision must be FTWA_FP64 or FTWA_FP32, got {precision}")
+    if K != 2 * int(n_sites):
+        raise ValueError(f"X has {K} columns, expected 2 * n_sites = {2 * int(n_sites)}")
+    if X.dtype != want:
+        raise ValueError(f"X is {X.dtype}, precision {precision} needs {want}")
+    if not X.is_cuda or not X.is_contiguous():
+        raise ValueError("X must be a contiguous CUDA tensor")
     if out is None:
         occ = torch.empty((T, K), dtype=torch.float64, device=X.device)
         conn = torch.empty((T, K, K), dtype=torch.float64, device=X.device)
         g = torch.empty((T, K, K), dtype=torch.float64, device=X.device) if g2 else None
     else:
         occ, conn, g = out
+        for name, t, shape in (("occ", occ, (T, K)), ("conn", conn, (T, K, K)), ("g2", g, (T, K, K))):
+            if t is None and name != "g2":
+                raise ValueError(f"{name} output is required")
+            if t is None:
+                continue
+            if tuple(t.shape) != shape or t.dtype != torch.float64 or not t.is_contiguous() \
+                    or t.device != X.device:
+                raise ValueError(f"{name} output must be a contiguous float64 tensor {shape} on {X.device}")
     check(load().ftwa_moments_noalloc(_ptr(X), int(precision), int(n_sites), int(M), int(T), _ptr(occ), _ptr(conn),
                                       _ptr(g), _stream(stream)), "ftwa_moments_noalloc")
     return occ, conn, g

@@ -277,8 +277,12 @@ int launch_moments(Plan *p, const void *snap, int64_t M, int32_t T, double *occ,
 // array below (FTWA_MOMENTS_NOALLOC_MAX_TK doubles, 1 MiB, resident on every
 // device that loads the library until the process exits).  Host code must
 // not use the array's name as a device address: its device address is looked
-// up with cudaGetSymbolAddress, once per device, on the first call made with
-// that device current.
+// up with cudaGetSymbolAddress with the calling device current.  The lookup
+// is repeated on every call whose stream is not capturing, so a device reset
+// (which gives the array a new address in the new context) or a switch of
+// the current context between calls is picked up; a call on a capturing
+// stream reuses the address found by the last non-capturing call on that
+// device, which is why a first call must precede any stream capture.
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) double g_noalloc_mu[FTWA_MOMENTS_NOALLOC_MAX_TK];
 
@@ -299,21 +303,27 @@ extern "C" int ftwa_moments_noalloc(const void *snap_dev, int32_t precision, int
     if (precision != FTWA_FP64 && precision != FTWA_FP32) return FTWA_ERR_INVALID_ARGUMENT;
     const int K = 2 * n_sites;
     if ((int64_t)n_times * K > FTWA_MOMENTS_NOALLOC_MAX_TK) return FTWA_ERR_UNSUPPORTED;
+    if (n_times > 65535) return FTWA_ERR_UNSUPPORTED;   // grid y / z extent of the two kernels
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return FTWA_ERR_CUDA;
     if (dev < 0 || dev >= kNoallocMaxDevices) return FTWA_ERR_UNSUPPORTED;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return FTWA_ERR_CUDA;
     double *mu = nullptr;
     {
         std::lock_guard<std::mutex> guard(g_noalloc_lock);
-        if (!g_noalloc_addr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {
+            // fresh lookup: the address belongs to the current context
             void *a = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_mu);
             if (e != cudaSuccess || !a) return FTWA_ERR_CUDA;
             g_noalloc_addr[dev] = static_cast<double *>(a);
+        } else if (!g_noalloc_addr[dev]) {
+            return FTWA_ERR_UNSUPPORTED;   // no earlier non-capturing call on this device
         }
         mu = g_noalloc_addr[dev];
     }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     // the mean kernel writes every mu[t][k] (t < n_times, k < 2N) before the
     // Gram kernel reads it, so the shared array needs no clearing
     dim3 gm((K + 31) / 32, n_times);

@@ -220,6 +220,33 @@ def occupation_loss(lat, U, n_up, n_dn, seed, M, dt, n_steps, out_every, target,
     return float(((occ[1:] - target) ** 2).sum())
 
 
+def correlation_loss(lat, U, n_up, n_dn, seed, M, dt, n_steps, out_every, weight, t_bond=None):
+    """L = sum_t sum_kl weight[t, k, l] C_kl(t) over all output rows (the
+    connected correlator of Eq. 5 from this oracle's moments)."""
+    snap, _ = run(lat, U, n_up, n_dn, seed, 0, M, dt, n_steps, out_every, t_bond=t_bond)
+    _, conn, _ = moments(snap, want_g2=False)
+    return float((weight * conn).sum())
+
+
+def fd_gradient_corr(lat, U, n_up, n_dn, seed, M, dt, n_steps, out_every, weight, which, h=1e-5):
+    """Central finite differences of :func:`correlation_loss` (common random
+    numbers); ``which`` as in :func:`fd_gradient`."""
+    out = []
+    for w in which:
+        def L(delta):
+            tb = np.array(lat.t_bond, dtype=np.float64)
+            u, nu, nd = U, np.array(n_up, dtype=np.float64), np.array(n_dn, dtype=np.float64)
+            if w[0] == "U":
+                u = U + delta
+            elif w[0] == "t":
+                tb[w[1]] += delta
+            else:
+                (nu if w[1] == 0 else nd)[w[2]] += delta
+            return correlation_loss(lat, u, nu, nd, seed, M, dt, n_steps, out_every, weight, t_bond=tb)
+        out.append((L(h) - L(-h)) / (2 * h))
+    return np.array(out)
+
+
 def fd_gradient(lat, U, n_up, n_dn, seed, M, dt, n_steps, out_every, target, which, h=1e-5):
     """Central finite differences of :func:`occupation_loss` with common random
     numbers (same seed).  ``which`` is a list of ("U",), ("t", b) or ("n", s, i)."""

@@ -30,6 +30,15 @@ rho_ji = conj(rho_ij), s_ij = sqrt((n_i + n_j - 2 n_i n_j)/2), so
 ds_ij/dn_i = (1 - 2 n_j) / (4 s_ij); pairs with s_ij = 0 are skipped (n -> s
 is not differentiable there).
 
+Correlation losses: with gC[t, k, l] = dL/dC_kl(t) for the connected
+correlator of Eq. 5, C_kl = (1/M) sum_m x_mk x_ml - mu_k mu_l (x_mk =
+Re rho^m_kk, mu = mean over samples), the derivative of C_kl with respect
+to one sample's diagonal is (1/M)[delta_jk (x_ml - mu_l) + delta_jl
+(x_mk - mu_k)], so sample m's cotangent gets
+  (1/M) sum_l (gC_jl + gC_lj)(x_ml - mu_l)
+on its diagonal entry j at every output step, mu being the mean over the M
+samples at that step (given as ``mu``).
+
 Parity: pinned by central finite differences of the C oracle's integration
 (``tests/test_oracle_pins.py``).
 """
@@ -91,9 +100,11 @@ def vjp(J, U, bonds, Y, v):
     return w, gU, gt
 
 
-def adjoint(lat, U, n_up, n_dn, seed, M, dt, n_steps, out_every, g, t_bond=None):
+def adjoint(lat, U, n_up, n_dn, seed, M, dt, n_steps, out_every, g, t_bond=None, gC=None, mu=None):
     """(dL/dU, dL/dt [n_bonds], dL/dn [2, N]) for the linearised loss
-    L = sum_t sum_k g[t, k] <n_k>(t) over the samples 0 .. M-1 of ``seed``."""
+    L = sum_t sum_k g[t, k] <n_k>(t) (+ sum_t sum_kl gC[t, k, l] C_kl(t) when
+    gC is given, with mu[t, k] the sample means of Re rho_kk) over the
+    samples 0 .. M-1 of ``seed``."""
     N = lat.n_sites
     J = hopping_matrix(lat, t_bond)
     bonds = [tuple(int(v) for v in b) for b in np.asarray(lat.bonds)]
@@ -114,6 +125,10 @@ def adjoint(lat, U, n_up, n_dn, seed, M, dt, n_steps, out_every, g, t_bond=None)
         def inject(lam, step):
             if step % out_every == 0:
                 row = g[step // out_every]
+                if gC is not None:
+                    t = step // out_every
+                    x = np.concatenate([ys[step][0].diagonal().real, ys[step][1].diagonal().real])
+                    row = row + (gC[t] + gC[t].T) @ (x - mu[t])
                 for s in range(2):
                     lam[s] += np.diag(row[s * N:(s + 1) * N] / M)
 

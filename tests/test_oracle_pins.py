@@ -539,3 +539,49 @@ def test_adjoint_oracle_matches_finite_differences(lat_name, U):
     assert abs(gU - fdU) <= 1e-8 * scale
     assert np.abs(gt - fdt).max() <= 1e-8 * scale
     assert np.abs(gn - fdn).max() <= 1e-8 * scale
+
+
+@pytest.mark.parametrize("lat_name,U", [("chain10", 1.6), ("periodic8", 2.5)])
+def test_adjoint_oracle_correlation_loss_matches_finite_differences(lat_name, U):
+    """Correlation losses (Eq. 5's connected correlator): the oracle's RK4
+    adjoint with the per-sample cotangent (1/M) sum_l (gC_jl + gC_lj)(x_ml -
+    mu_l) against central differences (h = 1e-5, same seed) of
+    L = sum_t sum_kl gC_tkl C_kl(t) + sum_t sum_k g_tk <n_k>(t), C taken from
+    the C oracle's moments (a non-symmetric random weight gC): dL/dU, every
+    dL/dt_b and every dL/dn_is to 1e-8 of the largest entry."""
+    from oracle import adjoint as OA
+    lat = {"chain10": W.hexagon_chain(2), "periodic8": W.periodic_honeycomb()}[lat_name]
+    n0u, n0d = W.neel_state(lat)
+    nu, nd = W.softened(n0u), W.softened(n0d)
+    N, seed, M, steps, every = lat.n_sites, 6, 4, 30, 10
+    rng = np.random.default_rng(2)
+    T = steps // every + 1
+    g = rng.standard_normal((T, 2 * N))
+    gC = rng.standard_normal((T, 2 * N, 2 * N))
+    snap, _ = oracle.run(lat, U, nu, nd, seed, 0, M, 0.01, steps, every)
+    mu = snap.mean(axis=1)
+    gU, gt, gn = OA.adjoint(lat, U, nu, nd, seed, M, 0.01, steps, every, g, gC=gC, mu=mu)
+    tb0 = np.array(lat.t_bond, dtype=np.float64)
+
+    def L(u, tb, a, b):
+        s, _ = oracle.run(lat, u, a, b, seed, 0, M, 0.01, steps, every, t_bond=tb)
+        occ, conn, _ = oracle.moments(s, want_g2=False)
+        return float((g * occ).sum() + (gC * conn).sum())
+
+    h = 1e-5
+    fdU = (L(U + h, tb0, nu, nd) - L(U - h, tb0, nu, nd)) / (2 * h)
+    fdt = np.array([(L(U, tb0 + h * e, nu, nd) - L(U, tb0 - h * e, nu, nd)) / (2 * h)
+                    for e in np.eye(lat.n_bonds)])
+    fdn = np.zeros((2, N))
+    for s in range(2):
+        for i in range(N):
+            e = np.zeros(N)
+            e[i] = h
+            if s == 0:
+                fdn[s, i] = (L(U, tb0, nu + e, nd) - L(U, tb0, nu - e, nd)) / (2 * h)
+            else:
+                fdn[s, i] = (L(U, tb0, nu, nd + e) - L(U, tb0, nu, nd - e)) / (2 * h)
+    scale = max(abs(fdU), np.abs(fdt).max(), np.abs(fdn).max())
+    assert abs(gU - fdU) <= 1e-8 * scale
+    assert np.abs(gt - fdt).max() <= 1e-8 * scale
+    assert np.abs(gn - fdn).max() <= 1e-8 * scale

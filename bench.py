@@ -127,9 +127,9 @@ def max_over_ranks(x, ws):
     return shard.max_over_ranks(x, ws)
 
 
-def traffic_record(kernel_src):
+def traffic_record(kernel_src, record="tile_stepper_fp32_198_traffic.txt"):
     """ncu DRAM bytes per launch recorded for this kernel source (or None)."""
-    path = os.path.join(ROOT, "profiles", "band_stepper_fp32_198_traffic.txt")
+    path = os.path.join(ROOT, "profiles", record)
     if not os.path.exists(path):
         return None
     kv = {}
@@ -215,6 +215,46 @@ def run_reference(args):
 
 
 
+def g2_error_bar(X):
+    """Delta-method standard error of the Eq. 10 estimator g2_kl =
+    mean(x_k x_l) / (mean x_k mean x_l), x = X + 1/2, from the samples
+    X [T, M, K] (FP32 products of centred columns: the scale of an error bar)."""
+    import torch
+    T, M, K = X.shape
+    out = torch.empty((T, K, K), dtype=torch.float64, device=X.device)
+    for t in range(T):
+        x = X[t].double() + 0.5
+        mu = x.mean(0)
+        xc = (x - mu).float()
+        x2 = xc * xc
+        cov = (xc.T @ xc).double() / M
+        e22 = (x2.T @ x2).double() / M
+        e21 = (x2.T @ xc).double() / M
+        B, C = mu[:, None], mu[None, :]
+        g = (cov + B * C) / (B * C)
+        var = e22 / (B * C) ** 2 - (cov / (B * C)) ** 2 + 2 * (1 - g) * (e21 / B + e21.T / C) / (B * C)
+        va = torch.diagonal(cov)
+        var = var + (1 - g) ** 2 * (va[:, None] / B ** 2 + 2 * cov / (B * C) + va[None, :] / C ** 2)
+        out[t] = torch.sqrt(var.clamp_min(0) / M)
+    return out
+
+
+def observable_errors(X64, o64, c64, g64, o32, c32, g32, M, floor=1e-6):
+    """max |FP32 - FP64| over times and entries, in units of each observable's
+    statistical error bar: s_k/sqrt(M) (occupations), s_k s_l/sqrt(M)
+    (connected correlator), the delta-method error (g2); floor 1e-6 where the
+    bar vanishes (deterministic t = 0 diagonals)."""
+    import torch
+    s = torch.sqrt(torch.diagonal(c64, dim1=1, dim2=2).clamp_min(0))
+    bo = (s / M ** 0.5).clamp_min(floor)
+    bc = (s[:, :, None] * s[:, None, :] / M ** 0.5).clamp_min(floor)
+    bg = g2_error_bar(X64).clamp_min(floor)
+    ok = ~torch.isnan(g64) & ~torch.isnan(g32)
+    return {"occupation": ((o32 - o64).abs() / bo).max().item(),
+            "connected_correlator": ((c32 - c64).abs() / bc).max().item(),
+            "g2": ((g32 - g64).abs()[ok] / bg[ok]).max().item()}
+
+
 def _events():
     import torch
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -263,6 +303,29 @@ def bench_adjoint(F, args):
                      "dL_dt_norm": float(gt.norm()), "dL_dn0_norm": float(gn.norm())}
         P.close()
         del rho, X
+    # finite-difference spot check at this workload's size (FP64, 64 samples,
+    # the full 500 steps): dL/dU and two bond gradients by central differences
+    # (h = 1e-5, same seed) of the GPU forward, against the adjoint
+    Mfd, h = 64, 1e-5
+    tb0 = np.array(lat.t_bond, dtype=np.float64)
+
+    def loss_of(U, tb):
+        lt = lat.with_t(tb)
+        with F.Plan(lt, U, n_up=nu, n_dn=nd, precision=F.FTWA_FP64, out_every=every) as Q:
+            o, _, _ = Q.moments(Q.evolve(Q.sample(21, Mfd), steps), g2=False)
+            return float(((o - target) ** 2).sum()), o
+
+    _, occ = loss_of(1.6, tb0)
+    with F.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=F.FTWA_FP64, out_every=every) as Q:
+        gU, gt, _ = Q.adjoint(21, Mfd, steps, ck, 2.0 * (occ - target))
+    checks = [("dL_dU", gU.item(), (loss_of(1.6 + h, tb0)[0] - loss_of(1.6 - h, tb0)[0]) / (2 * h))]
+    for bnd in (0, lat.n_bonds // 2):
+        e = np.zeros(lat.n_bonds)
+        e[bnd] = h
+        checks.append((f"dL_dt{bnd}", gt[bnd].item(), (loss_of(1.6, tb0 + e)[0] - loss_of(1.6, tb0 - e)[0]) / (2 * h)))
+    out["fd_check"] = {"samples": Mfd, "steps": steps, "h": h,
+                       "values": {k: {"adjoint": a_, "central_difference": f_} for k, a_, f_ in checks},
+                       "max_rel_err": max(abs(a_ - f_) / max(abs(f_), 1e-300) for _, a_, f_ in checks)}
     return out
 
 
@@ -419,9 +482,16 @@ def bench_batched(F, args):
         if P.status() != 0:
             raise RuntimeError("batched device status")
     total = len(plans) * M * steps
+    flops = sum(FLOP_PER_ELEMENT_STEP * lt.n_sites * (lt.n_sites + 1) for lt in lats) * len(Us) * M * steps
+    pk = max(F.measure_peak("fp32"), F.measure_peak("fp32x2")) / 1e12
+    pks = F.measure_peak("smem") / 1e12
+    achieved = flops / (ms / 1000.0) / 1e12
+    smem_tb = achieved * 1e12 / FLOP_PER_ELEMENT_STEP * SMEM_BYTES_PER_ELEMENT_STEP / 1e12
     out = {"workload": f"flakes 24/54/96/150/198 sites x U in {Us}, M={M} each, FP32, {steps} RK4 steps",
            "problems": len(plans), "value": total / (ms / 1000.0), "unit": UNIT, "ms": ms,
-           "shapes": shapes, "autotune_s": tune_s, "graph_launches": 1}
+           "shapes": shapes, "autotune_s": tune_s, "graph_launches": 1,
+           "roofline": {"bound": "smem", "achieved": smem_tb, "peak": pks, "unit": "TB/s", "frac": smem_tb / pks,
+                        "fp32": {"achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk}}}
     B.close()
     for P in plans:
         P.close()
@@ -513,7 +583,8 @@ def run_gpu(args):
         if timed:
             ev[k][1].record(stream)
         check(lib.ftwa_moments(P._h, ctypes.c_void_p(X.data_ptr()), M, T, ctypes.c_void_p(occ.data_ptr()),
-                               ctypes.c_void_p(conn.data_ptr()), ctypes.c_void_p(g2.data_ptr()), 0, sp), "moments")
+                               ctypes.c_void_p(conn.data_ptr()), ctypes.c_void_p(g2.data_ptr()), F.FTWA_GRAM_BF16X3,
+                               sp), "moments")
         if ws > 1:
             # exchange step: the estimators over the union of all ranks' samples
             shard.combine_moments(M, occ, conn, ws)
@@ -564,7 +635,7 @@ def run_gpu(args):
                         precision=F.FTWA_FP32, out_every=every)
             Pk.sample(7, M, first_sample=first, out=rho)
             Xk = Pk.evolve(rho, steps, snap=X)
-            o, c, g = Pk.moments(X)
+            o, c, g = Pk.moments(X, gram_mode=F.FTWA_GRAM_BF16X3)
             occ_h.copy_(o, non_blocking=True)
             conn_h.copy_(c, non_blocking=True)
             g2_h.copy_(g, non_blocking=True)
@@ -576,31 +647,63 @@ def run_gpu(args):
                "h2d_bytes_per_step": 2 * N * 8 + lat.n_bonds * 8 * 3,
                "d2h_bytes_per_step": (T * K + 2 * T * K * K) * 8}
 
-    # ---- FP64 GPU path on a subset, and the FP32 error against it ----------------
+    # ---- FP64 GPU path on a subset, and the FP32 path's error against it ---------
+    # (the FP64 path is pinned to the oracle trajectory by trajectory; every
+    # reported observable: max |FP32 - FP64| in units of its error bar)
     fp64 = None
     if not args.no_fp64:
         Ms = args.fp64_samples
-        P64 = F.Plan(lat, wl["U"], n_up=wl["n_up"], n_dn=wl["n_dn"], precision=F.FTWA_FP64, out_every=every)
-        r64 = P64.sample(11, Ms)
-        r32 = P.sample(11, Ms)
+        fp64 = {"unit": UNIT, "samples": Ms, "errors": {}}
+        for U in (1.0, wl["U"]):
+            P64 = F.Plan(lat, U, n_up=wl["n_up"], n_dn=wl["n_dn"], precision=F.FTWA_FP64, out_every=every)
+            P32 = F.Plan(lat, U, n_up=wl["n_up"], n_dn=wl["n_dn"], precision=F.FTWA_FP32, out_every=every)
+            r64 = P64.sample(11, Ms)
+            r32 = P32.sample(11, Ms)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            X64 = P64.evolve(r64, steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms64 = e0.elapsed_time(e1)
+            X32 = P32.evolve(r32, steps)
+            o64, c64, g64 = P64.moments(X64)
+            o32, c32, g32 = P32.moments(X32, gram_mode=F.FTWA_GRAM_BF16X3)
+            err = observable_errors(X64, o64, c64, g64, o32, c32, g32, Ms)
+            fp64["errors"][f"U={U}"] = err
+            if U == wl["U"]:
+                fp64["value"] = Ms * steps / (ms64 / 1000.0)
+                fp64["fp32_speedup_vs_fp64"] = (M * steps / (evolve_ms / 1000.0)) / fp64["value"]
+            P64.close()
+            P32.close()
+            del r64, r32, X64, X32
+        fp64["gate"] = "max error / error bar < 0.1 for every observable (occupation, connected correlator, g2)"
+        fp64["gate_met"] = all(v < 0.1 for e in fp64["errors"].values() for v in e.values())
+        fp64["peak_fp64_tflops"] = F.measure_peak("fp64") / 1e12
+        flops64 = FLOP_PER_ELEMENT_STEP * N * (N + 1) * fp64["value"]
+        fp64["roofline"] = {"bound": "alu", "achieved": flops64 / 1e12, "peak": fp64["peak_fp64_tflops"],
+                            "unit": "TFLOP/s", "frac": flops64 / 1e12 / fp64["peak_fp64_tflops"],
+                            "peak_source": "measured: ftwa_measure_peak FP64 FMA"}
+
+    # ---- the same step at U/t = 1.0 (the paper's regime U = J) -----------------------
+    u_alt = None
+    if not args.no_u1:
+        Pu = F.Plan(lat, 1.0, n_up=wl["n_up"], n_dn=wl["n_dn"], precision=F.FTWA_FP32, out_every=every)
+        Pu.sample(7, M, first_sample=first, out=rho)
+        Pu.evolve(rho, 5, snap=None)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        X64 = P64.evolve(r64, steps)
+        Pu.sample(7, M, first_sample=first, out=rho)
+        Pu.evolve(rho, steps, snap=X)
+        Pu.moments(X, gram_mode=F.FTWA_GRAM_BF16X3)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1)
-        X32 = P.evolve(r32, steps)
-        o64, c64, _ = P64.moments(X64, g2=False)
-        o32, _, _ = P.moments(X32, g2=False)
-        var = torch.diagonal(c64, dim1=1, dim2=2)
-        se = torch.sqrt(var / Ms)
-        mask = se > 1e-6
-        ratio = ((o32 - o64).abs()[mask] / se[mask]).max().item() if mask.any() else 0.0
-        fp64 = {"value": Ms * steps / (ms64 / 1000.0), "unit": UNIT, "samples": Ms,
-                "fp32_speedup_vs_fp64": (M * steps / (evolve_ms / 1000.0)) / (Ms * steps / (ms64 / 1000.0)),
-                "fp32_occ_err_over_stderr_max": ratio}
-        P64.close()
+        if Pu.status() != 0:
+            raise RuntimeError("U = 1.0 leg device status")
+        u_alt = {"U_over_t": 1.0, "value": ws * M * steps / (e0.elapsed_time(e1) / 1000.0), "unit": UNIT,
+                 "ms_per_step": e0.elapsed_time(e1)}
+        Pu.close()
 
     extra = {}
     if not args.no_adjoint:
@@ -617,24 +720,26 @@ def run_gpu(args):
         extra["ed"] = bench_ed(F, args)
 
     # ---- roofline of the dominant kernel (the RK4 stepper) -----------------------
-    pk = peaks()
-    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
-    sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    fp32_peak = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12     # TFLOP/s
+    # bound: shared memory (the smaller of the stepper's two bounds); the FP32
+    # fraction beside it.  Peaks measured on this device by the library's
+    # micro-benchmarks (MEASURED_PEAKS.json has neither).
+    pk_smem = F.measure_peak("smem") / 1e12                         # TB/s
+    pk_fp32 = max(F.measure_peak("fp32"), F.measure_peak("fp32x2")) / 1e12   # TFLOP/s
     flops = FLOP_PER_ELEMENT_STEP * N * (N + 1) * M * steps
     achieved = flops / (evolve_ms / 1000.0) / 1e12
-    traffic = traffic_record(os.path.join(ROOT, "paper_2212_04352_gb300", "csrc", "ftwa_evolve.cu"))
-    # the shared-memory bound: 7 complex reads + 1 write per element and
-    # stage (64 B in FP32) at 128 B per clock and SM
+    info_kernel = {1: "band_stepper<float>", 2: "rk4_stepper<float>", 3: "tile_stepper<float>"}.get(info["variant"])
+    src = "ftwa_tile.cu" if info["variant"] == 3 else "ftwa_evolve.cu"
+    rec = "tile_stepper_fp32_198_traffic.txt" if info["variant"] == 3 else "band_stepper_fp32_198_traffic.txt"
+    traffic = traffic_record(os.path.join(ROOT, "paper_2212_04352_gb300", "csrc", src), rec)
     smem_bytes = SMEM_BYTES_PER_ELEMENT_STEP * N * (N + 1) * M * steps
-    smem_peak = sm_count * 128 * sm_mhz * 1e6 / 1e12                # TB/s
     smem_achieved = smem_bytes / (evolve_ms / 1000.0) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-            "traffic": traffic, "kernel": "band_stepper<float>",
-            "peak_source": f"FP32 FMA: {sm_count} SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (max SM clock, MEASURED_PEAKS.json)",
-            "smem": {"achieved": smem_achieved, "peak": smem_peak, "unit": "TB/s", "frac": smem_achieved / smem_peak,
-                     "bytes_per_element_step": SMEM_BYTES_PER_ELEMENT_STEP,
-                     "peak_source": f"{sm_count} SMs x 128 B/clock x {sm_mhz:.0f} MHz"}}
+    roof = {"bound": "smem", "achieved": smem_achieved, "peak": pk_smem, "unit": "TB/s",
+            "frac": smem_achieved / pk_smem, "traffic": traffic, "kernel": info_kernel,
+            "bytes_per_element_step": SMEM_BYTES_PER_ELEMENT_STEP,
+            "peak_source": "measured: ftwa_measure_peak shared-memory load bandwidth (all SMs, 16-byte loads)",
+            "fp32": {"achieved": achieved, "peak": pk_fp32, "unit": "TFLOP/s", "frac": achieved / pk_fp32,
+                     "flop_per_element_step": FLOP_PER_ELEMENT_STEP,
+                     "peak_source": "measured: ftwa_measure_peak FP32 FMA (max of scalar and packed pairs)"}}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -643,7 +748,7 @@ def run_gpu(args):
                                                         f"at the end of each step when more than one",
                                        "launch": info}),
             "e2e": e2e, "roofline": roof, "clocks": clk, "gpu_launches": 4 * args.steps,
-            "evolve_ms": evolve_ms, "fp64": fp64, **extra}
+            "evolve_ms": evolve_ms, "fp64": fp64, "u_1p0": u_alt, **extra}
     if rank == 0 and ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -745,12 +850,13 @@ def main():
     ap.add_argument("--no-general", action="store_true")
     ap.add_argument("--no-drive", action="store_true")
     ap.add_argument("--no-ed", action="store_true")
+    ap.add_argument("--no-u1", action="store_true")
     ap.add_argument("--drive-samples", type=int, default=4096)
     ap.add_argument("--drive-steps", type=int, default=200)
     ap.add_argument("--general-samples", type=int, default=4096)
     ap.add_argument("--adjoint-samples", type=int, default=4096)
     ap.add_argument("--batch-samples", type=int, default=4096)
-    ap.add_argument("--batch-steps", type=int, default=100)
+    ap.add_argument("--batch-steps", type=int, default=1000)
     ap.add_argument("--gram-samples", type=int, default=65536)
     ap.add_argument("--gram-times", type=int, default=200)
     ap.add_argument("--profile", action="store_true", help="small case for ncu captures")

@@ -100,7 +100,9 @@ typedef struct {
                                  microseconds, 0 = default (5 s)             */
     int32_t variant;          /* stepper: 0 automatic, 1 banded (rows keep a
                                  mirror band of width = lattice bandwidth),
-                                 2 general packed triangle                   */
+                                 2 general packed triangle, 3 tiled (FP32,
+                                 on-site U: the banded layout in 32-column
+                                 blocks at a fixed row stride)               */
 } ftwa_options;
 
 /* Launch shape chosen by the plan (for reporting and tests). */
@@ -113,7 +115,7 @@ typedef struct {
     int32_t tmem_cols;        /* tensor-memory columns per CTA                */
     int32_t grid_clusters;    /* persistent clusters launched                 */
     int32_t units_per_warp;   /* 32-lane work units per warp and sample slot  */
-    int32_t variant;          /* stepper chosen: 1 banded, 2 general          */
+    int32_t variant;          /* stepper chosen: 1 banded, 2 general, 3 tiled */
 } ftwa_plan_info;
 
 /* Create a plan: validates the lattice and initial state, builds the
@@ -268,6 +270,25 @@ int ftwa_adjoint(ftwa_plan_t *plan, uint64_t seed, int64_t M, int64_t n_steps, i
                  const double *dL_docc_dev, double *grad_U_dev, double *grad_t_dev,
                  double *grad_n0_dev, void *stream);
 
+/* Discrete adjoint for losses of the occupations and of the connected
+ * correlator of Eq. 5 (fTWA_moments): the caller supplies dL_docc_dev as for
+ * ftwa_adjoint (or NULL) and dL_dconn_dev[t][k][l] = dL/dC_kl(t) ([T+1][2N][2N]
+ * device doubles, any matrix, or NULL; not both NULL), with occ_dev[t][k] the
+ * forward occupations <n_k>(t) of the same M samples (ftwa_moments' occ
+ * output; required with dL_dconn_dev).  C_kl = (1/M) sum_m x_mk x_ml -
+ * mu_k mu_l with x_mk = Re rho^m_kk and mu = occ - 1/2, so sample m's
+ * diagonal entry j receives (1/M) sum_l (G_jl + G_lj)(x_ml - mu_l) at every
+ * output row; a loss of <n_k n_l> or g2 (Eq. 10) reaches the library
+ * through its chain rule onto occ and conn.  Everything else (samples,
+ * checkpoints, outputs, errors) as for ftwa_adjoint; the plan also keeps a
+ * workspace of (T+1)(2N)^2 doubles for the symmetrised G.  Errors:
+ * FTWA_ERR_INVALID_ARGUMENT (both cotangents NULL, dL_dconn_dev without
+ * occ_dev, or the conditions of ftwa_adjoint), FTWA_ERR_UNSUPPORTED,
+ * FTWA_ERR_OUT_OF_MEMORY, FTWA_ERR_CUDA. */
+int ftwa_adjoint_corr(ftwa_plan_t *plan, uint64_t seed, int64_t M, int64_t n_steps, int32_t ckpt_every,
+                      const double *dL_docc_dev, const double *dL_dconn_dev, const double *occ_dev,
+                      double *grad_U_dev, double *grad_t_dev, double *grad_n0_dev, void *stream);
+
 /* Allocation-free variant of ftwa_moments with gram_mode FTWA_GRAM_FP64.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot call cudaMalloc, such as applications whose device memory is owned
@@ -365,6 +386,30 @@ int ftwa_status(ftwa_plan_t *plan, void *stream);
  * FTWA_ERR_DEVICE_TIMEOUT, skips its work and exits cleanly (the state
  * buffer is left unchanged).  Disarm with 0. */
 int ftwa_debug_force_timeout(ftwa_plan_t *plan, int32_t armed);
+
+/* Micro-benchmark of an on-chip peak of the current device, for the
+ * roofline denominators of the stepper (not part of the method): kind 0 =
+ * FP32 fused multiply-add rate (flop/s, scalar FFMA), 3 = the same with
+ * packed pairs (__ffma2_rn), 1 = FP64 FMA rate (flop/s), 2 = shared-memory
+ * load bandwidth (bytes/s, conflict-free 16-byte loads, all SMs).  Best of
+ * five timed launches on `stream`; synchronous; allocates a small sink
+ * buffer.  Errors: FTWA_ERR_INVALID_ARGUMENT, FTWA_ERR_CUDA. */
+int ftwa_measure_peak(int32_t kind, double *value, void *stream);
+
+/* Host-only consistency check of the tiled stepper's work decomposition
+ * (variant 3; the stage state of Eq. 6 split over `cluster` CTAs with
+ * `slots` samples each): every shared-memory address the kernel forms for
+ * one slot is simulated on the host and checked — reads of active lanes hit
+ * the intended element of Eq. 6 (the lane's own element for an empty
+ * neighbour slot), all reads stay inside the addressed CTA's buffer, every computed
+ * element of the upper triangle is written exactly once per stage and every
+ * mirror-band entry exactly once.  Needs no device.  Lattice arguments as
+ * for ftwa_plan (t_bond may be NULL: uniform 1).  *violations receives the
+ * number of failed checks, msg (if not NULL) a description of the first.
+ * Errors: FTWA_ERR_INVALID_ARGUMENT, FTWA_ERR_UNSUPPORTED (no decomposition
+ * of that cluster size and slot count). */
+int ftwa_debug_tile_check(int32_t n_sites, int32_t n_bonds, const int32_t *bonds, const double *t_bond,
+                          int32_t cluster, int32_t slots, int64_t *violations, char *msg, int32_t msg_len);
 
 /* Human-readable text of a status code (static storage). */
 const char *ftwa_error_string(int status);

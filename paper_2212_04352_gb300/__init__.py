@@ -20,7 +20,9 @@ from ._lib import (  # noqa: F401
     FTWA_FP32, FTWA_FP64, FTWA_GRAM_BF16X3, FTWA_GRAM_FP64, FtwaError, check, load,
 )
 
-__all__ = ["Plan", "Batch", "ED", "plan", "philox", "moments_noalloc", "occupations", "FTWAFunction", "FTWA_FP32",
+__all__ = ["Plan", "Batch", "ED", "plan", "philox", "measure_peak", "moments_noalloc", "occupations",
+           "correlations",
+           "FTWAFunction", "FTWACorrFunction", "FTWA_FP32",
            "FTWA_FP64", "FTWA_GRAM_FP64", "FTWA_GRAM_BF16X3", "FtwaError", "load"]
 
 
@@ -185,21 +187,41 @@ class Plan:
                                   int(gram_mode), _stream(stream)), "ftwa_moments")
         return occ, conn, g
 
-    def adjoint(self, seed, M, n_steps, ckpt_every, dL_docc, stream=None):
-        """(dL/dU [1], dL/dt_b [n_bonds], dL/dn0 [2, N]), float64 device tensors."""
+    def adjoint(self, seed, M, n_steps, ckpt_every, dL_docc, dL_dconn=None, occ=None, stream=None):
+        """(dL/dU [1], dL/dt_b [n_bonds], dL/dn0 [2, N]), float64 device tensors.
+
+        dL_docc [T+1, 2N] (or None with dL_dconn) is dL/d<n>; dL_dconn
+        [T+1, 2N, 2N] is dL/dC of the connected correlator and needs the
+        forward occupations ``occ`` [T+1, 2N] of the same samples."""
         import torch
-        want = (int(n_steps) // self.out_every + 1, 2 * self.N)
-        if tuple(dL_docc.shape) != want:
-            raise ValueError(f"dL_docc must be [n_steps/out_every + 1, 2N] = {want}, got {tuple(dL_docc.shape)}")
-        if not dL_docc.is_cuda:
-            raise ValueError("dL_docc must be a CUDA tensor")
-        dev = dL_docc.device
+        T1, K = int(n_steps) // self.out_every + 1, 2 * self.N
+        ref = dL_docc if dL_docc is not None else dL_dconn
+        if ref is None:
+            raise ValueError("give dL_docc, dL_dconn or both")
+        for name, t, shape in (("dL_docc", dL_docc, (T1, K)), ("dL_dconn", dL_dconn, (T1, K, K)),
+                               ("occ", occ, (T1, K))):
+            if t is None:
+                continue
+            if tuple(t.shape) != shape:
+                raise ValueError(f"{name} must be {shape} (n_steps/out_every + 1 rows), got {tuple(t.shape)}")
+            if not t.is_cuda:
+                raise ValueError(f"{name} must be a CUDA tensor")
+        if dL_dconn is not None and occ is None:
+            raise ValueError("dL_dconn needs the forward occupations occ")
+        dev = ref.device
         gU = torch.zeros(1, dtype=torch.float64, device=dev)
         gt = torch.zeros(self.n_bonds, dtype=torch.float64, device=dev)
         gn = torch.zeros((2, self.N), dtype=torch.float64, device=dev)
-        dl = dL_docc.contiguous().to(torch.float64)
-        check(load().ftwa_adjoint(self._h, int(seed), int(M), int(n_steps), int(ckpt_every), _ptr(dl), _ptr(gU),
-                                  _ptr(gt), _ptr(gn), _stream(stream)), "ftwa_adjoint")
+        dl = None if dL_docc is None else dL_docc.contiguous().to(torch.float64)
+        if dL_dconn is None:
+            check(load().ftwa_adjoint(self._h, int(seed), int(M), int(n_steps), int(ckpt_every), _ptr(dl), _ptr(gU),
+                                      _ptr(gt), _ptr(gn), _stream(stream)), "ftwa_adjoint")
+        else:
+            dc = dL_dconn.contiguous().to(torch.float64)
+            oc = occ.contiguous().to(torch.float64)
+            check(load().ftwa_adjoint_corr(self._h, int(seed), int(M), int(n_steps), int(ckpt_every), _ptr(dl),
+                                           _ptr(dc), _ptr(oc), _ptr(gU), _ptr(gt), _ptr(gn), _stream(stream)),
+                  "ftwa_adjoint_corr")
         return gU, gt, gn
 
     def autotune(self, M, probe_steps=20, stream=None):
@@ -290,11 +312,72 @@ def _occupation_function():
     return _OCC_FN
 
 
+_CORR_FN = None
+
+
+def _correlation_function():
+    global _CORR_FN
+    if _CORR_FN is not None:
+        return _CORR_FN
+    import torch
+
+    class FTWACorrFunction(torch.autograd.Function):
+        """Forward: Eq. 7 samples -> RK4 of Eq. 6 -> FP64 estimators of Eq. 5
+        (occupations and the connected correlator), all in libftwa.
+        Backward: the discrete RK4 adjoint (ftwa_adjoint_corr) of the same
+        samples, given dL/d<n> and dL/dC from autograd."""
+
+        @staticmethod
+        def forward(ctx, U, t_bond, n0, bonds, seed, M, n_steps, precision, dt, out_every, ckpt_every):
+            n0h = n0.detach().to("cpu", torch.float64).numpy()
+            lat = _Bonds(n0h.shape[1], bonds, t_bond.detach().to("cpu", torch.float64).numpy())
+            P = Plan(lat, float(U.detach()), n_up=n0h[0], n_dn=n0h[1], precision=precision, dt=dt,
+                     out_every=out_every)
+            try:
+                rho = P.sample(seed, M)
+                X = P.evolve(rho, n_steps)
+                del rho
+                occ, conn, _ = P.moments(X, g2=False)
+                st = P.status()
+                if st != 0:
+                    raise FtwaError(st, "ftwa_evolve", "device status word set (timeout)")
+            except BaseException:
+                P.close()
+                raise
+            ctx.plan = P
+            ctx.args = (seed, M, n_steps, ckpt_every)
+            ctx.occ = occ
+            ctx.like = [(x.shape, x.device, x.dtype) for x in (U, t_bond, n0)]
+            return occ, conn
+
+        @staticmethod
+        def backward(ctx, g_occ, g_conn):
+            P = ctx.plan
+            seed, M, n_steps, ckpt_every = ctx.args
+            g_occ = torch.zeros_like(ctx.occ) if g_occ is None else g_occ.contiguous()
+            if g_conn is None:
+                gU, gt, gn = P.adjoint(seed, M, n_steps, ckpt_every, g_occ)
+            else:
+                gU, gt, gn = P.adjoint(seed, M, n_steps, ckpt_every, g_occ, dL_dconn=g_conn.contiguous(),
+                                       occ=ctx.occ)
+            st = P.status()
+            if st != 0:
+                raise FtwaError(st, "ftwa_adjoint_corr", "device status word set (timeout)")
+            grads = [x.reshape(shape).to(dev, dt) for x, (shape, dev, dt) in zip((gU, gt, gn), ctx.like)]
+            return (*grads, None, None, None, None, None, None, None, None)
+
+    _CORR_FN = FTWACorrFunction
+    return _CORR_FN
+
+
 def __getattr__(name):
-    # FTWAFunction: the autograd.Function behind occupations(), created on first
-    # use so that importing the package does not import torch.
+    # FTWAFunction / FTWACorrFunction: the autograd.Functions behind
+    # occupations() and correlations(), created on first use so that
+    # importing the package does not import torch.
     if name == "FTWAFunction":
         return _occupation_function()
+    if name == "FTWACorrFunction":
+        return _correlation_function()
     raise AttributeError(name)
 
 
@@ -320,6 +403,24 @@ def occupations(lattice, U, t_bond, n0, seed, M, n_steps, precision=FTWA_FP64, d
     n0 = torch.as_tensor(n0, dtype=torch.float64)
     return _occupation_function().apply(U, t_bond, n0, np.asarray(lattice.bonds), int(seed), int(M), int(n_steps),
                                         int(precision), float(dt), int(out_every), int(ckpt_every))
+
+
+def correlations(lattice, U, t_bond, n0, seed, M, n_steps, precision=FTWA_FP64, dt=0.01, out_every=10,
+                 ckpt_every=None):
+    """Differentiable fTWA estimators of Eq. 5: (occ, conn), the occupations
+    <n_k>(t) [n_steps/out_every + 1, 2N] and the connected correlator
+    C_kl(t) = <n_k n_l> - <n_k><n_l> [.., 2N, 2N] over samples m = 0 .. M-1
+    of ``seed`` (float64, on the device).  Losses of <n_k n_l> = C + <n_k><n_l>
+    or of g2 (Eq. 10) are differentiable through these two outputs.
+    Arguments and gradients as for :func:`occupations`."""
+    import torch
+    if ckpt_every is None:
+        ckpt_every = _default_ckpt(int(n_steps), int(out_every))
+    U = torch.as_tensor(U, dtype=torch.float64)
+    t_bond = torch.as_tensor(t_bond, dtype=torch.float64)
+    n0 = torch.as_tensor(n0, dtype=torch.float64)
+    return _correlation_function().apply(U, t_bond, n0, np.asarray(lattice.bonds), int(seed), int(M), int(n_steps),
+                                         int(precision), float(dt), int(out_every), int(ckpt_every))
 
 
 class ED:
@@ -439,6 +540,16 @@ def moments_noalloc(X, precision, n_sites, g2=True, stream=None, out=None):
     check(load().ftwa_moments_noalloc(_ptr(X), int(precision), int(n_sites), int(M), int(T), _ptr(occ), _ptr(conn),
                                       _ptr(g), _stream(stream)), "ftwa_moments_noalloc")
     return occ, conn, g
+
+
+def measure_peak(kind, stream=None):
+    """On-chip peak of the current device (ftwa_measure_peak): "fp32" / "fp32x2"
+    (FMA flop/s, scalar / packed pairs), "fp64" (FMA flop/s) or "smem"
+    (shared-memory load bytes/s)."""
+    k = {"fp32": 0, "fp64": 1, "smem": 2, "fp32x2": 3}[kind]
+    v = ctypes.c_double()
+    check(load().ftwa_measure_peak(k, ctypes.byref(v), _stream(stream)), "ftwa_measure_peak")
+    return v.value
 
 
 def philox(seed, m, spin, p0, count, stream=None):

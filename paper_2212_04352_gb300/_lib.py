@@ -26,8 +26,9 @@ FTWA_MOMENTS_NOALLOC_MAX_TK = 131072
 EXPORTS = ("ftwa_plan", "ftwa_destroy", "ftwa_get_info", "ftwa_sample", "ftwa_set_initial_basis", "ftwa_philox",
            "ftwa_evolve", "ftwa_evolve_at", "ftwa_set_drive", "ftwa_set_hopping_drive", "ftwa_set_interaction",
            "ftwa_ed_plan", "ftwa_ed_destroy", "ftwa_ed_info", "ftwa_ed_evolve",
-           "ftwa_moments", "ftwa_moments_noalloc", "ftwa_adjoint", "ftwa_autotune", "ftwa_batch_create",
-           "ftwa_batch_launch", "ftwa_batch_destroy", "ftwa_status", "ftwa_debug_force_timeout", "ftwa_error_string",
+           "ftwa_moments", "ftwa_moments_noalloc", "ftwa_adjoint", "ftwa_adjoint_corr", "ftwa_autotune", "ftwa_batch_create",
+           "ftwa_batch_launch", "ftwa_batch_destroy", "ftwa_status", "ftwa_debug_force_timeout",
+           "ftwa_debug_tile_check", "ftwa_measure_peak", "ftwa_error_string",
            "ftwa_version")
 
 
@@ -92,6 +93,7 @@ def load(path: str = LIB_PATH):
     lib.ftwa_moments.argtypes = [P, P, i64, i32, P, P, P, i32, P]
     lib.ftwa_moments_noalloc.argtypes = [P, i32, i32, i64, i32, P, P, P, P]
     lib.ftwa_adjoint.argtypes = [P, u64, i64, i64, i32, P, P, P, P, P]
+    lib.ftwa_adjoint_corr.argtypes = [P, u64, i64, i64, i32, P, P, P, P, P, P, P]
     lib.ftwa_autotune.argtypes = [P, i64, i32, P]
     lib.ftwa_batch_create.argtypes = [P, i32, P, P, i64, P, ctypes.POINTER(P)]
     lib.ftwa_batch_launch.argtypes = [P, P]
@@ -99,12 +101,16 @@ def load(path: str = LIB_PATH):
     lib.ftwa_batch_destroy.restype = None
     lib.ftwa_status.argtypes = [P, P]
     lib.ftwa_debug_force_timeout.argtypes = [P, i32]
+    lib.ftwa_measure_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double), P]
+    lib.ftwa_debug_tile_check.argtypes = [i32, i32, P, P, i32, i32, ctypes.POINTER(ctypes.c_int64), ctypes.c_char_p,
+                                          i32]
     lib.ftwa_error_string.argtypes = [ctypes.c_int]
     lib.ftwa_error_string.restype = ctypes.c_char_p
     lib.ftwa_version.restype = ctypes.c_int
     for name in ("ftwa_plan", "ftwa_get_info", "ftwa_sample", "ftwa_philox", "ftwa_evolve", "ftwa_moments",
                  "ftwa_moments_noalloc", "ftwa_autotune", "ftwa_batch_create", "ftwa_batch_launch",
-                 "ftwa_adjoint", "ftwa_status", "ftwa_debug_force_timeout"):
+                 "ftwa_adjoint", "ftwa_adjoint_corr", "ftwa_status", "ftwa_debug_force_timeout",
+                 "ftwa_debug_tile_check", "ftwa_measure_peak"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

@@ -2,7 +2,12 @@
 //
 // Loss (linearised by the caller): L = sum_t sum_k g_t,k <n_k>(t), with
 // <n_k>(t) = (1/M) sum_m Re rho^m_kk(t) + 1/2 (Eq. 5), so each sample's
-// cotangent gets g_t,k / M on the diagonal at every output step.
+// cotangent gets g_t,k / M on the diagonal at every output step.  With a
+// correlation term sum_t sum_kl G_t,kl C_kl(t) (C the connected correlator
+// of Eq. 5, C_kl = (1/M) sum_m x_mk x_ml - mu_k mu_l, x_mk = Re rho^m_kk),
+// dC_kl/dx_mj = (1/M)[delta_jk (x_ml - mu_l) + delta_jl (x_mk - mu_k)], so
+// sample m's diagonal entry j also gets (1/M) sum_l S_t,jl (x_ml - mu_t,l),
+// S = G + G^T (symmetrised once per call into the plan's workspace).
 //
 // Per sample (one CTA): forward integration storing a checkpoint every
 // ckpt_every steps; then, segment by segment backwards, the segment is
@@ -61,7 +66,9 @@ struct AdjArgs {
     int out_every, ckpt_every;
     long long n_steps, M;
     unsigned long long seed;
-    const double *dL;             // [n_out][2N]
+    const double *dL;             // [n_out][2N] or null
+    const double *dS;             // [n_out][2N][2N] S = G + G^T of a correlation term, or null
+    const double *mu;             // [n_out][2N] sample means of Re rho_kk (with dS)
     double *gU, *gt, *gn;         // outputs (accumulated with atomics)
     typename C2T<T>::type *ws;    // per-CTA workspace
     long long ws_stride;          // elements per CTA
@@ -122,6 +129,7 @@ struct Smem {
     T *wd;              // [2][N] diagonal of W before the coupling
     double *gt;         // [B]
     double *gn;         // [2][N]
+    double *xc;         // [2N] centred diagonal of the sample at an output step
 };
 
 // One RK4 stage pass on the packed upper triangle, k = f(src) (Eq. 6)
@@ -458,6 +466,8 @@ __global__ void __launch_bounds__(THREADS, CTAS) adjoint_kernel(const AdjArgs<T>
     p += sizeof(double) * std::max(a.B, 1);
     sm.gn = reinterpret_cast<double *>(p);
     p += sizeof(double) * 2 * N;
+    sm.xc = reinterpret_cast<double *>(p);
+    p += sizeof(double) * 2 * N;
     sm.nbr = reinterpret_cast<int32_t *>(p);
     p += sizeof(int32_t) * N;
     sm.bond = reinterpret_cast<int32_t *>(p);
@@ -531,16 +541,39 @@ __global__ void __launch_bounds__(THREADS, CTAS) adjoint_kernel(const AdjArgs<T>
             lam[e].y = T(0);
         }
         __syncthreads();
-        auto inject = [&](long long step) {
+        // cotangent of the loss at output step `step`; y is the sample's state there
+        auto inject = [&](long long step, const V *y) {
             if (step % a.out_every) return;
-            const double *g = a.dL + (step / a.out_every) * twoN;
-            for (int e = threadIdx.x; e < twoN; e += blockDim.x) {
-                const int s = e / N, k = e % N;
-                lam[pidx(N, s, k, k)].x += (T)(g[e] * invM);
+            const long long t = step / a.out_every;
+            if (a.dS) {
+                for (int e = threadIdx.x; e < twoN; e += blockDim.x) {
+                    const int s = e / N, k = e % N;
+                    sm.xc[e] = (double)y[pidx(N, s, k, k)].x - a.mu[t * twoN + e];
+                }
+                __syncthreads();
+                // (1/M) sum_l S_jl x_l: a warp per row j, lanes over l
+                const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+                const double *S = a.dS + t * (long long)twoN * twoN;
+                for (int j = threadIdx.x >> 5; j < twoN; j += nw) {
+                    double acc = 0.0;
+                    for (int l = lane; l < twoN; l += 32) acc = fma(S[(long long)j * twoN + l], sm.xc[l], acc);
+                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    if (lane == 0) {
+                        const double gj = a.dL ? a.dL[t * twoN + j] : 0.0;
+                        const int s = j / N, k = j % N;
+                        lam[pidx(N, s, k, k)].x += (T)((gj + acc) * invM);
+                    }
+                }
+            } else {
+                const double *g = a.dL + t * twoN;
+                for (int e = threadIdx.x; e < twoN; e += blockDim.x) {
+                    const int s = e / N, k = e % N;
+                    lam[pidx(N, s, k, k)].x += (T)(g[e] * invM);
+                }
             }
             __syncthreads();
         };
-        inject(a.n_steps);
+        inject(a.n_steps, cur);
         // ---- reverse sweep ----------------------------------------------------------
         for (int sg = n_seg - 1; sg >= 0; --sg) {
             for (int e = threadIdx.x; e < NE; e += blockDim.x) seg[e] = ckpt[(long long)sg * NE + e];
@@ -593,7 +626,7 @@ __global__ void __launch_bounds__(THREADS, CTAS) adjoint_kernel(const AdjArgs<T>
                     }
                     __syncthreads();
                 }
-                inject((long long)sg * a.ckpt_every + r);
+                inject((long long)sg * a.ckpt_every + r, y);
             }
         }
         // ---- initial occupations -------------------------------------------------------
@@ -638,11 +671,23 @@ __global__ void zero_kernel(double *x, int n)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = 0.0;
 }
 
+// S_t = G_t + G_t^T and mu_t = <n>_t - 1/2 of a correlation term ([T][K][K], [T][K])
+__global__ void symmetrise_kernel(const double *G, const double *occ, int T, int K, double *S, double *mu)
+{
+    const long long n = (long long)T * K * K;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long t = i / ((long long)K * K);
+        const int k = (int)((i / K) % K), l = (int)(i % K);
+        S[i] = G[i] + G[(t * K + l) * K + k];
+        if (l == 0) mu[t * K + k] = occ[t * K + k] - 0.5;
+    }
+}
+
 }  // namespace adj
 
 template <typename T>
 static int launch_adjoint_t(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, int32_t ckpt_every, const double *dL,
-                            double *gU, double *gt, double *gn, cudaStream_t s)
+                            const double *dS, const double *mu, double *gU, double *gt, double *gn, cudaStream_t s)
 {
     using namespace adj;
     using V = typename C2T<T>::type;
@@ -650,7 +695,7 @@ static int launch_adjoint_t(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, 
     const int NE = N * (N + 1);
     const int n_seg = (int)(n_steps / ckpt_every);
     const long long stride = (long long)(n_seg + ckpt_every + 1 + 11) * NE;
-    const int smem_tables = (int)(sizeof(double) * (6 * N + 2 * std::max(p->B, 1)) + sizeof(int32_t) * 4 * N +
+    const int smem_tables = (int)(sizeof(double) * (8 * N + 2 * std::max(p->B, 1)) + sizeof(int32_t) * 4 * N +
                                   sizeof(int32_t) * 2 * std::max(p->B, 1) + sizeof(uint32_t) * NE + 64);
     // FP32: one 1024-thread CTA per SM, so that the samples in flight keep
     // their working sets in L2 (measured 1.4x faster than four 256-thread
@@ -689,6 +734,8 @@ static int launch_adjoint_t(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, 
     a.M = M;
     a.seed = seed;
     a.dL = dL;
+    a.dS = dS;
+    a.mu = mu;
     a.gU = gU;
     a.gt = gt;
     a.gn = gn;
@@ -705,15 +752,39 @@ static int launch_adjoint_t(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, 
 }
 
 int launch_adjoint(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, int32_t ckpt_every, const double *dL,
-                   double *gU, double *gt, double *gn, cudaStream_t s)
+                   const double *dC, const double *occ, double *gU, double *gt, double *gn, cudaStream_t s)
 {
     // the samples of a general initial state depend on the eigenbasis, whose
     // derivatives the adjoint does not carry
     if (p->general_basis) return FTWA_ERR_UNSUPPORTED;
     // nor through the time-dependent drive or a long-range interaction
     if (p->drive || p->longrange || p->hop_drive) return FTWA_ERR_UNSUPPORTED;
-    if (p->precision == FTWA_FP64) return launch_adjoint_t<double>(p, seed, M, n_steps, ckpt_every, dL, gU, gt, gn, s);
-    return launch_adjoint_t<float>(p, seed, M, n_steps, ckpt_every, dL, gU, gt, gn, s);
+    const double *dS = nullptr, *mu = nullptr;
+    if (dC) {
+        // S = G + G^T and mu = <n> - 1/2 for every output row, in the plan's
+        // correlation workspace (grown on demand)
+        const int K = 2 * p->N, T = (int)(n_steps / p->out_every) + 1;
+        const size_t bytes = sizeof(double) * ((size_t)T * K * K + (size_t)T * K);
+        if (p->corr_ws_bytes < bytes) {
+            cudaFree(p->d_corr_ws);
+            p->d_corr_ws = nullptr;
+            p->corr_ws_bytes = 0;
+            cudaError_t e = cudaMalloc(&p->d_corr_ws, bytes);
+            if (e != cudaSuccess) return set_cuda_error(e);
+            p->corr_ws_bytes = bytes;
+        }
+        double *S = static_cast<double *>(p->d_corr_ws);
+        double *m = S + (size_t)T * K * K;
+        const long long n = (long long)T * K * K;
+        adj::symmetrise_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 8192), 256, 0, s>>>(dC, occ, T, K, S, m);
+        const int rc = set_cuda_error(cudaGetLastError());
+        if (rc != FTWA_OK) return rc;
+        dS = S;
+        mu = m;
+    }
+    if (p->precision == FTWA_FP64)
+        return launch_adjoint_t<double>(p, seed, M, n_steps, ckpt_every, dL, dS, mu, gU, gt, gn, s);
+    return launch_adjoint_t<float>(p, seed, M, n_steps, ckpt_every, dL, dS, mu, gU, gt, gn, s);
 }
 
 }  // namespace ftwa

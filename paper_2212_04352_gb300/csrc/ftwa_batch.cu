@@ -41,14 +41,15 @@ int ftwa_autotune(ftwa_plan_t *plan, int64_t M, int32_t probe_steps, void *strea
     float best_ms = 0.0f;
     int best_v = 0, best_c = 0;
     int rc = FTWA_OK;
-    for (int v = 1; v <= 2 && rc == FTWA_OK; ++v) {
+    for (int v = 1; v <= 3 && rc == FTWA_OK; ++v) {
         for (int c = 1; c <= kMaxCluster && rc == FTWA_OK; c *= 2) {
             p->variant_override = v;
             p->cluster_override = c;
             StepperShape ss;
             BandShape bs;
             const bool ok = v == 1 ? choose_band_shape(p, Mp, &bs) == FTWA_OK
-                                   : choose_stepper_shape(p, Mp, &ss) == FTWA_OK;
+                                   : v == 2 ? choose_stepper_shape(p, Mp, &ss) == FTWA_OK
+                                            : tile_supported(p);
             if (!ok) continue;
             rc = launch_sample(p, 12345, 0, Mp, rho, s);
             if (rc != FTWA_OK) break;

@@ -1554,7 +1554,12 @@ int launch_evolve(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cu
                                          : band_dispatch<float>(p, bs, rho, M, n_steps, snap, s);
     }
     // automatic choice: the banded stepper for FP32; for FP64 (DFMA-bound on
-    // this part) the packed-triangle stepper, which does fewer flops per element
+    // this part) the packed-triangle stepper, which does fewer flops per
+    // element.  The tiled stepper runs when asked for (or chosen by the autotuner).
+    if (p->variant_override == 3) {
+        const int rc = launch_tile(p, rho, M, n_steps, snap, s);
+        if (rc != FTWA_ERR_UNSUPPORTED || p->variant_override == 3) return rc;
+    }
     const bool try_band = p->variant_override == 1 || (p->variant_override == 0 && p->precision == FTWA_FP32);
     if (try_band) {
         BandShape bs;

@@ -28,7 +28,7 @@ struct StepperShape {
     int buf_bytes = 0;      // bytes of one stage buffer (max over ranks)
     int row_begin[kMaxCluster + 1] = {0};  // spin-row partition over ranks
     int grid = 0;           // CTAs launched
-    int variant = 0;        // 1 = banded stepper, 2 = general packed-triangle stepper
+    int variant = 0;        // 1 = banded stepper, 2 = general packed-triangle stepper, 3 = tiled stepper
 };
 
 // Launch shape of the banded stepper.
@@ -67,11 +67,16 @@ struct Plan {
     void *d_ws = nullptr;             // plan-owned workspace (moments, adjoint)
     void *d_adj_ws = nullptr;         // adjoint per-CTA workspace
     size_t adj_ws_bytes = 0;
+    void *d_corr_ws = nullptr;        // adjoint: symmetrised correlation cotangents and means
+    size_t corr_ws_bytes = 0;
+    void *d_tile = nullptr;           // tiled stepper tables (tiles, row-part offsets, hoppings)
+    size_t tile_bytes = 0;
+    std::vector<unsigned char> tile_host;   // copy of the tables last uploaded
     uint32_t *d_items = nullptr;      // banded stepper work items
     size_t items_bytes = 0;
     std::vector<uint32_t> items_host; // copy of the table last uploaded
     bool dry_run = false;             // choose the shape and upload tables, launch nothing
-    int variant_override = 0;         // 0 auto, 1 banded only, 2 general only
+    int variant_override = 0;         // 0 auto, 1 banded only, 2 general only, 3 tiled only
     size_t ws_bytes = 0;
     StepperShape shape;               // chosen for the full machine
     // general (non-diagonal) initial state n = V diag(lambda) V^dagger per spin
@@ -111,11 +116,13 @@ int launch_evolve(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cu
 void free_drive(Plan *p);
 void free_interaction(Plan *p);
 int choose_stepper_shape(Plan *p, int64_t M, StepperShape *out);
+bool tile_supported(const Plan *p);
+int launch_tile(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s);
 int choose_band_shape(Plan *p, int64_t M, BandShape *out);
 int launch_moments(Plan *p, const void *snap, int64_t M, int32_t T, double *occ, double *conn, double *g2,
                    int32_t mode, cudaStream_t s);
 int launch_adjoint(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, int32_t ckpt_every, const double *dL,
-                   double *gU, double *gt, double *gn, cudaStream_t s);
+                   const double *dC, const double *occ, double *gU, double *gt, double *gn, cudaStream_t s);
 
 }  // namespace ftwa
 

@@ -52,7 +52,14 @@ static void free_tables(Plan *p)
     cudaFree(p->d_status);
     cudaFree(p->d_ws);
     cudaFree(p->d_items);
+    cudaFree(p->d_tile);
+    p->d_tile = nullptr;
+    p->tile_bytes = 0;
+    p->tile_host.clear();
     cudaFree(p->d_adj_ws);
+    cudaFree(p->d_corr_ws);
+    p->d_corr_ws = nullptr;
+    p->corr_ws_bytes = 0;
     free_basis(p);
     free_drive(p);
     free_interaction(p);
@@ -260,7 +267,7 @@ int ftwa_plan(const ftwa_lattice *lat, double U, double t, double filling, const
         (o.cluster_override & (o.cluster_override - 1)) != 0)
         return FTWA_ERR_INVALID_ARGUMENT;
     if (o.threads_override != 0 && o.threads_override != kThreads) return FTWA_ERR_UNSUPPORTED;
-    if (o.variant < 0 || o.variant > 2) return FTWA_ERR_INVALID_ARGUMENT;
+    if (o.variant < 0 || o.variant > 3) return FTWA_ERR_INVALID_ARGUMENT;
 
     ftwa_plan_t *p = new (std::nothrow) ftwa_plan_t();
     if (!p) return FTWA_ERR_OUT_OF_MEMORY;
@@ -417,6 +424,14 @@ int ftwa_plan(const ftwa_lattice *lat, double U, double t, double filling, const
     {
         BandShape bs;
         const bool try_band = p->variant_override == 1 || (p->variant_override == 0 && p->precision == FTWA_FP32);
+        if (p->variant_override == 3) {
+            // shape of the tiled stepper for one sample per cluster (tables are
+            // built and uploaded by the first evolve)
+            p->dry_run = true;
+            rc = launch_tile(p, nullptr, (int64_t)p->sm_count, 1, nullptr, nullptr);
+            p->dry_run = false;
+            if (rc == FTWA_OK || p->variant_override == 3) goto shape_done;
+        }
         if (try_band && choose_band_shape(p, (int64_t)p->sm_count, &bs) == FTWA_OK) {
             p->shape.cluster = bs.cluster;
             p->shape.slots = bs.slots;
@@ -432,6 +447,7 @@ int ftwa_plan(const ftwa_lattice *lat, double U, double t, double filling, const
             p->shape.variant = 2;
         }
     }
+shape_done:
     if (rc != FTWA_OK) {
         free_tables(p);
         delete p;
@@ -585,8 +601,20 @@ int ftwa_adjoint(ftwa_plan_t *p, uint64_t seed, int64_t M, int64_t n_steps, int3
 {
     if (!p || M < 1 || n_steps < 1 || ckpt_every < 1 || !dL_docc_dev) return FTWA_ERR_INVALID_ARGUMENT;
     if (n_steps % ckpt_every != 0 || ckpt_every % p->out_every != 0) return FTWA_ERR_INVALID_ARGUMENT;
-    return launch_adjoint(p, seed, M, n_steps, ckpt_every, dL_docc_dev, grad_U_dev, grad_t_dev, grad_n0_dev,
-                          static_cast<cudaStream_t>(stream));
+    return launch_adjoint(p, seed, M, n_steps, ckpt_every, dL_docc_dev, nullptr, nullptr, grad_U_dev, grad_t_dev,
+                          grad_n0_dev, static_cast<cudaStream_t>(stream));
+}
+
+int ftwa_adjoint_corr(ftwa_plan_t *p, uint64_t seed, int64_t M, int64_t n_steps, int32_t ckpt_every,
+                      const double *dL_docc_dev, const double *dL_dconn_dev, const double *occ_dev,
+                      double *grad_U_dev, double *grad_t_dev, double *grad_n0_dev, void *stream)
+{
+    if (!p || M < 1 || n_steps < 1 || ckpt_every < 1) return FTWA_ERR_INVALID_ARGUMENT;
+    if (!dL_docc_dev && !dL_dconn_dev) return FTWA_ERR_INVALID_ARGUMENT;
+    if (dL_dconn_dev && !occ_dev) return FTWA_ERR_INVALID_ARGUMENT;
+    if (n_steps % ckpt_every != 0 || ckpt_every % p->out_every != 0) return FTWA_ERR_INVALID_ARGUMENT;
+    return launch_adjoint(p, seed, M, n_steps, ckpt_every, dL_docc_dev, dL_dconn_dev, occ_dev, grad_U_dev,
+                          grad_t_dev, grad_n0_dev, static_cast<cudaStream_t>(stream));
 }
 
 int ftwa_status(ftwa_plan_t *p, void *stream)

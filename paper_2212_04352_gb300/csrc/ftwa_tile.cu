@@ -1,0 +1,1083 @@
+// Tiled persistent RK4 stepper for FP32 states (Eq. 6, on-site U).
+//
+// Same method and arithmetic as the banded stepper (Eq. 6 with classical
+// RK4; the stage state in shared memory, double-buffered; y0 and the stage
+// accumulator in tensor memory; a thread-block cluster per sample for large
+// lattices), with a layout chosen so that the inner loop is almost free of
+// integer work:
+//  - Shared memory is block-major: for each 32-column block b and spin s, the
+//    rows of this rank are stored at a fixed stride of 256 B (one complex
+//    FP32 value per lane), element (s, p, q) at Z(s, b) + 256 p + 8 lane(q).
+//    Row offsets inside a tile are therefore immediates of the load.
+//  - Each row stores the upper triangle plus a mirror band of bw entries
+//    below the diagonal (bw = lattice bandwidth), as in the banded stepper,
+//    so every read of Eq. 6 is a direct load.  Empty neighbour slots read
+//    the lane's own element with a zero hopping.
+//  - A tile is up to kR consecutive rows of one spin and one column block.
+//    A lane owns column q of the tile; the row-part gathers rho_pk,
+//    k in nb(q), are at fixed byte offsets from the lane's own element for
+//    every row of the rank (one table entry per block and lane), and the
+//    column-part reads rho_kq, k in nb(p), at per-row offsets (k - p) 256
+//    held with the row's hoppings in a per-rank table in shared memory.
+//  - On lattices whose site order has every site's neighbours among p - 1,
+//    p + 1 and at most one other site (honeycomb flakes numbered along
+//    rows), the column-part values of rows p -+ 1 are the lane's own values
+//    of the neighbouring rows of the tile, carried in registers.
+// Per element (p, q), p <= q, spin s (Eq. 6):
+//   k_pq = i [ sum_{k in nb(q)} t_qk rho_pk - sum_{k in nb(p)} t_pk rho_kq
+//              + U (Re rho_pp,sbar - Re rho_qq,sbar) rho_pq ].
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "ftwa_internal.h"
+#include "ptx.cuh"
+
+namespace ftwa {
+namespace tile {
+
+constexpr int kR = 8;                     // rows per tile
+constexpr int kThreadsT = 768;            // threads per CTA
+constexpr int kWarpsT = kThreadsT / 32;
+constexpr int kColsPerWarp = 80;          // tensor-memory columns per warp (6 warps per lane quadrant)
+constexpr int kMaxBlk = (FTWA_MAX_SITES + 31) / 32;
+constexpr int kRowBytes = 256;            // one row of a 32-column block
+
+struct TileHeader {
+    unsigned long long dead_bar;  // never completes (timeout test hook)
+    uint32_t tmem_base;
+    int abort;
+};
+
+extern __shared__ __align__(16) unsigned char tile_smem[];
+
+// Column-part data of one spin-row (one entry per spin-row, written from the
+// owning rank's point of view; each rank copies its rows into shared memory).
+struct __align__(16) RowEntry {
+    float mt[3];      // -t_pk of the three column-part slots (0: empty slot)
+    uint32_t flags;   // bit n: slot n is in another rank; bit 3 + n: that rank is the next one
+    int32_t dcol[3];  // local slot: (k - p) * 256 (0 for an empty slot); remote slot: k * 256
+    int32_t mir;      // Z(s, blk(p)) + 8 lane(p): element (q, p) is at mir + 256 q
+};
+
+// Tile descriptor: x = p0 | cnt << 9 | b << 13 | slot << 16 (p0 a spin-row);
+// y = flags below.
+enum : uint32_t {
+    kDiag = 1u,        // a row's diagonal element lies in the tile
+    kBand = 2u,        // some lane holds a mirror-band element (0 < q - p <= bw)
+    kPrevShift = 3,    // 2 bits: row p0 - 1 is 0 local, 1 absent (zero hopping), 2 in the previous rank
+    kNextShift = 5,    // 2 bits: row p0 + cnt is 0 local, 1 absent (zero hopping), 2 in the next rank
+    kRemote = 128u,    // some row of the tile reads a column-part slot of another rank
+};
+
+struct TileArgs {
+    int N, C, S, nblk, qoff, bw;
+    int slot_bytes, buf_bytes;       // one slot of one stage buffer; one stage buffer
+    int k_tiles;                     // tile entries per warp
+    float U, dt;
+    long long M, n_steps;
+    int out_every;
+    float2 *rho;                     // [M][2][N][N]
+    float *snap;                     // [n_out][M][2N] or null
+    int *status;
+    unsigned long long timeout_ns;
+    int force_timeout;
+    int row_begin[kMaxCluster + 1];  // spin-rows of each rank
+    int zoff[kMaxCluster][2][kMaxBlk];   // Z(s, b) of each rank (byte offset inside a slot)
+    const uint2 *tiles;              // [C][kWarpsT][k_tiles]
+    const int4 *koff;                // [C][nblk][32] row-part byte offsets of the three slots
+    const float2 *tq;                // [nblk][32][3] (t, t) of the row-part slots
+    const RowEntry *rows;            // [2N]
+    int rows_bytes;                  // shared-memory bytes of the largest rank's row table
+};
+
+// ---- address arithmetic shared by the kernel and the host layout check --------
+__host__ __device__ __forceinline__ int blk_of(int q, int qoff) { return (q - qoff) >> 5; }
+__host__ __device__ __forceinline__ int lane_of(int q, int qoff) { return (q - qoff) & 31; }
+// byte offset (inside a slot) of element (s, p, q) in a rank whose origins are z
+__host__ __device__ __forceinline__ int elem_off(const int (*z)[kMaxBlk], int s, int p, int q, int qoff)
+{
+    return z[s][blk_of(q, qoff)] + kRowBytes * p + 8 * lane_of(q, qoff);
+}
+
+// ---- device helpers ------------------------------------------------------------
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+__device__ __forceinline__ float2 ld_cluster(uint32_t a)
+{
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, float2 v)
+{
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+// tensor memory: a row pair's y0 and acc (8 words: y0 a, y0 b, acc a, acc b)
+__device__ __forceinline__ void tm_ld8(uint32_t ta, uint32_t (&w)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+                 : "r"(ta));
+}
+__device__ __forceinline__ void tm_wait8(uint32_t (&w)[8])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(w[0]), "+r"(w[1]), "+r"(w[2]), "+r"(w[3]), "+r"(w[4]), "+r"(w[5]), "+r"(w[6]), "+r"(w[7]));
+}
+__device__ __forceinline__ void tm_st4(uint32_t ta, float2 a, float2 b)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ta),
+                 "r"(__float_as_uint(a.x)), "r"(__float_as_uint(a.y)), "r"(__float_as_uint(b.x)),
+                 "r"(__float_as_uint(b.y)));
+}
+
+template <bool CLUSTER>
+__device__ __forceinline__ void stage_sync()
+{
+    if constexpr (CLUSTER) {
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    } else {
+        __syncthreads();
+    }
+}
+
+struct TileCtx {
+    uint32_t smem_s;          // shared::cta address of the dynamic shared memory
+    int buf0;                 // byte offset of stage buffer 0
+    int diag_off;             // byte offset of the diagonals [2 buffers][S][2N] (float)
+    int rows_off;             // byte offset of this rank's row table
+    int rb0, rb1;             // this rank's spin-rows
+    uint32_t diag_s;
+    uint32_t prev_c, next_c;  // shared::cluster address of smem in the previous / next rank
+    int rank;
+    const uint2 *tiles;
+    uint32_t t_state;
+    int lane;
+};
+
+// One RK4 stage over the rows of one tile.  Stage buffer CUR = STAGE & 1
+// holds the stage state; the next stage state goes to the other buffer.
+template <int STAGE, bool PM1, bool CLUSTER>
+__device__ __forceinline__ void tile_rows(const TileArgs &a, const TileCtx &c, uint2 td, int e_base, long long b_id,
+                                          bool snap_now, long long snap_row)
+{
+    constexpr int CUR = STAGE & 1;
+    const int N = a.N, twoN = 2 * N, lane = c.lane;
+    const int p0 = td.x & 511, cnt = (td.x >> 9) & 15, blk = (td.x >> 13) & 7, slot = (td.x >> 16) & 255;
+    const bool diag_t = (td.y & kDiag) != 0, band_t = (td.y & kBand) != 0;
+    const int s = p0 >= N ? 1 : 0;
+    const int pp0 = p0 - s * N;                       // site index of row 0 of the tile
+    const int q = a.qoff + 32 * blk + lane;
+    const int qc = q < 0 ? 0 : q;
+    const int slot_off = slot * a.slot_bytes;
+    const int cur_off = c.buf0 + CUR * a.buf_bytes + slot_off;
+    const int dnext = (CUR ? -1 : 1) * a.buf_bytes;   // next stage buffer minus this one
+    const int z = a.zoff[c.rank][s][blk];
+    const int own0 = cur_off + z + kRowBytes * pp0 + 8 * lane;     // element (p0, q)
+    const int4 ko = __ldg(&a.koff[(c.rank * a.nblk + blk) * 32 + lane]);
+    const float2 *tqp = a.tq + (blk * 32 + lane) * 3;
+    const float2 tq0 = __ldg(tqp), tq1 = __ldg(tqp + 1), tq2 = __ldg(tqp + 2);
+    const int dg_off = c.diag_off + 4 * ((CUR * a.S + slot) * twoN + (1 - s) * N);   // other spin's diagonal
+    auto lds = [&](int off) -> float2 { return *reinterpret_cast<const float2 *>(tile_smem + off); };
+    auto ldf = [&](int off) -> float { return *reinterpret_cast<const float *>(tile_smem + off); };
+    auto sts = [&](int off, float2 v) { *reinterpret_cast<float2 *>(tile_smem + off) = v; };
+    const float uq = a.U * ldf(dg_off + 4 * qc);
+    const float hdt = a.dt * 0.5f, sdt = a.dt * (1.0f / 6.0f);
+    const int rt0 = c.rows_off + (int)sizeof(RowEntry) * (p0 - c.rb0);
+
+    // carried column-part values of rows p - 1 and p (PM1)
+    float2 vprev = make_float2(0.f, 0.f), vcur = make_float2(0.f, 0.f);
+    const uint32_t nk = (td.y >> kNextShift) & 3;
+    if constexpr (PM1) {
+        const uint32_t pk = (td.y >> kPrevShift) & 3;
+        if (pk == 2) {
+            const int zp = a.zoff[c.rank - 1][s][blk];
+            vprev = ld_cluster(c.prev_c + (uint32_t)(cur_off + zp + kRowBytes * (pp0 - 1) + 8 * lane));
+        } else {
+            vprev = lds(pk == 0 ? own0 - kRowBytes : own0);   // absent: any finite value, zero hopping
+        }
+        vcur = lds(own0);
+    }
+
+    auto row = [&](int i, float2 &y0, float2 &acc) {
+        const int p = pp0 + i;
+        const int own = own0 + kRowBytes * i;
+        const RowEntry re = *reinterpret_cast<const RowEntry *>(tile_smem + rt0 + (int)sizeof(RowEntry) * i);
+        float2 ov;
+        float2 h = make_float2(0.f, 0.f);
+        // + sum_{k in nb(q)} t_qk rho_pk (row p)
+        h = ffma2(tq0, lds(own + ko.x), h);
+        h = ffma2(tq1, lds(own + ko.y), h);
+        h = ffma2(tq2, lds(own + ko.z), h);
+        // - sum_{k in nb(p)} t_pk rho_kq (column q)
+        if constexpr (PM1) {
+            ov = vcur;
+            float2 vnext;
+            if (i + 1 < cnt) {
+                vnext = lds(own + kRowBytes);
+            } else if (nk == 2) {
+                const int zn = a.zoff[c.rank + 1][s][blk];
+                vnext = ld_cluster(c.next_c + (uint32_t)(cur_off + zn + kRowBytes * (p + 1) + 8 * lane));
+            } else {
+                vnext = lds(nk == 0 ? own + kRowBytes : own);
+            }
+            float2 vf;
+            if (re.flags & 4u) {
+                const bool nx = (re.flags & 32u) != 0;
+                const int zo = a.zoff[nx ? c.rank + 1 : c.rank - 1][s][blk];
+                vf = ld_cluster((nx ? c.next_c : c.prev_c) + (uint32_t)(cur_off + zo + re.dcol[2] + 8 * lane));
+            } else {
+                vf = lds(own + re.dcol[2]);
+            }
+            h.x = fmaf(re.mt[0], vprev.x, h.x);
+            h.y = fmaf(re.mt[0], vprev.y, h.y);
+            h.x = fmaf(re.mt[1], vnext.x, h.x);
+            h.y = fmaf(re.mt[1], vnext.y, h.y);
+            h.x = fmaf(re.mt[2], vf.x, h.x);
+            h.y = fmaf(re.mt[2], vf.y, h.y);
+            vprev = vcur;
+            vcur = vnext;
+        } else {
+            ov = lds(own);
+#pragma unroll
+            for (int n = 0; n < 3; ++n) {
+                float2 v;
+                if (re.flags & (1u << n)) {
+                    const bool nx = (re.flags >> (3 + n)) & 1u;
+                    const int zo = a.zoff[nx ? c.rank + 1 : c.rank - 1][s][blk];
+                    v = ld_cluster((nx ? c.next_c : c.prev_c) + (uint32_t)(cur_off + zo + re.dcol[n] + 8 * lane));
+                } else {
+                    v = lds(own + re.dcol[n]);
+                }
+                h.x = fmaf(re.mt[n], v.x, h.x);
+                h.y = fmaf(re.mt[n], v.y, h.y);
+            }
+        }
+        // + U (Re rho_pp,sbar - Re rho_qq,sbar) rho_pq
+        const float coef = fmaf(a.U, ldf(dg_off + 4 * p), -uq);
+        h.x = fmaf(coef, ov.x, h.x);
+        h.y = fmaf(coef, ov.y, h.y);
+        // k = i h; the diagonal of Eq. 6 is real (the imaginary part is rounding residue)
+        const float kx = -h.y;
+        const float ky = (diag_t && q == p) ? 0.f : h.x;
+        float2 nx;
+        if constexpr (STAGE == 0) {
+            acc.x = kx;
+            acc.y = ky;
+            nx.x = fmaf(hdt, kx, y0.x);
+            nx.y = fmaf(hdt, ky, y0.y);
+        } else if constexpr (STAGE < 3) {
+            acc.x = fmaf(2.f, kx, acc.x);
+            acc.y = fmaf(2.f, ky, acc.y);
+            const float cc = STAGE == 1 ? hdt : a.dt;
+            nx.x = fmaf(cc, kx, y0.x);
+            nx.y = fmaf(cc, ky, y0.y);
+        } else {
+            nx.x = fmaf(sdt, acc.x + kx, y0.x);
+            nx.y = fmaf(sdt, acc.y + ky, y0.y);
+            y0 = nx;
+        }
+        if (!diag_t || q >= p) sts(own + dnext, nx);
+        if (band_t && q > p && q - p <= a.bw) {
+            // mirror entry (q, p) = conj(rho_pq) in row q (this rank or the next)
+            const float2 cj = make_float2(nx.x, -nx.y);
+            if (s * N + q < c.rb1) {
+                sts(cur_off + dnext + re.mir + kRowBytes * q, cj);
+            } else {
+                const int bp = blk_of(p, a.qoff);
+                const int mir_next = re.mir - a.zoff[c.rank][s][bp] + a.zoff[c.rank + 1][s][bp];
+                st_cluster(c.next_c + (uint32_t)(cur_off + dnext + mir_next + kRowBytes * q), cj);
+            }
+        }
+        if (diag_t && q == p) {
+            const int di = ((CUR ^ 1) * a.S + slot) * twoN + s * N + p;
+            if constexpr (CLUSTER) {
+                const uint32_t da = c.diag_s + (uint32_t)(4 * di);
+                for (int r = 0; r < a.C; ++r) {
+                    const uint32_t ra = map_rank(da, (uint32_t)r);
+                    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(nx.x) : "memory");
+                }
+            } else {
+                *reinterpret_cast<float *>(tile_smem + c.diag_off + 4 * di) = nx.x;
+            }
+            if (STAGE == 3 && snap_now) {
+                const long long m = b_id * a.S + slot;
+                if (m < a.M) a.snap[(snap_row * a.M + m) * twoN + s * N + p] = nx.x;
+            }
+        }
+    };
+
+    uint32_t w[8];
+    tm_ld8(c.t_state + (uint32_t)(8 * e_base), w);
+    for (int i = 0; i < cnt; i += 2) {
+        tm_wait8(w);
+        float2 y0a = make_float2(__uint_as_float(w[0]), __uint_as_float(w[1]));
+        float2 y0b = make_float2(__uint_as_float(w[2]), __uint_as_float(w[3]));
+        float2 acca = make_float2(__uint_as_float(w[4]), __uint_as_float(w[5]));
+        float2 accb = make_float2(__uint_as_float(w[6]), __uint_as_float(w[7]));
+        row(i, y0a, acca);
+        if (i + 1 < cnt) row(i + 1, y0b, accb);
+        const uint32_t ta = c.t_state + (uint32_t)(8 * (e_base + (i >> 1)));
+        if constexpr (STAGE < 3) tm_st4(ta + 4, acca, accb);
+        else tm_st4(ta, y0a, y0b);
+        if (i + 2 < cnt) tm_ld8(ta + 8, w);
+    }
+}
+
+template <int STAGE, bool PM1, bool CLUSTER>
+__device__ __forceinline__ void tile_stage(const TileArgs &a, const TileCtx &c, long long b_id, bool snap_now,
+                                        long long snap_row)
+{
+    int e = 0;   // row pairs of this warp done so far (tensor-memory column / 8)
+    for (int it = 0; it < a.k_tiles; ++it) {
+        const uint2 td = __ldg(&c.tiles[it]);
+        if (td.x == 0xFFFFFFFFu) break;
+        tile_rows<STAGE, PM1, CLUSTER>(a, c, td, e, b_id, snap_now, snap_row);
+        e += (((td.x >> 9) & 15) + 1) >> 1;
+    }
+}
+
+template <bool PM1, bool CLUSTER>
+__global__ void __launch_bounds__(kThreadsT, 1) tile_stepper(const __grid_constant__ TileArgs a)
+{
+    unsigned char *smem = tile_smem;
+    const int N = a.N, S = a.S, C = a.C, twoN = 2 * N;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = CLUSTER ? cluster_ctarank() : 0u;
+    const uint32_t cid = CLUSTER ? cluster_id_x() : blockIdx.x;
+    const uint32_t ncl = CLUSTER ? n_clusters_x() : gridDim.x;
+
+    // shared memory: header (64 B) | diagonals [2][S][2N] | row table | stage buffers 0, 1
+    TileHeader *h = reinterpret_cast<TileHeader *>(smem);
+    float *diag = reinterpret_cast<float *>(smem + 64);
+    const int diag_bytes = 16 * ((4 * 2 * S * twoN + 15) / 16);
+    TileCtx c;
+    c.smem_s = smem_addr(smem);
+    c.diag_off = 64;
+    c.rows_off = 64 + diag_bytes;
+    c.buf0 = 64 + diag_bytes + a.rows_bytes;
+    c.diag_s = smem_addr(diag);
+    c.rank = (int)rank;
+    c.rb0 = a.row_begin[rank];
+    c.rb1 = a.row_begin[rank + 1];
+    c.prev_c = 0;
+    c.next_c = 0;
+    if constexpr (CLUSTER) {
+        if (rank > 0) c.prev_c = map_rank(c.smem_s, rank - 1);
+        if ((int)rank + 1 < C) c.next_c = map_rank(c.smem_s, rank + 1);
+    }
+    c.tiles = a.tiles + ((size_t)rank * kWarpsT + warp) * a.k_tiles;
+    c.lane = lane;
+
+    if (threadIdx.x == 0) {
+        h->abort = 0;
+        mbar_init(smem_addr(&h->dead_bar), 1u);
+        fence_mbar_init_cluster();
+    }
+    // both stage buffers start zeroed (padding slots stay finite); this rank's row table
+    for (int i = threadIdx.x; i < (2 * a.buf_bytes) / 16; i += blockDim.x)
+        reinterpret_cast<float4 *>(smem + c.buf0)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = threadIdx.x; i < (c.rb1 - c.rb0) * (int)(sizeof(RowEntry) / 16); i += blockDim.x)
+        reinterpret_cast<uint4 *>(smem + c.rows_off)[i] = __ldg(reinterpret_cast<const uint4 *>(a.rows + c.rb0) + i);
+    if (warp == 0) {
+        tmem_alloc(smem_addr(&h->tmem_base), kTmemCols);
+        tmem_relinquish();
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if constexpr (CLUSTER) cluster_sync_hw();
+    c.t_state = h->tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(kColsPerWarp * (warp >> 2));
+
+    if (a.force_timeout) {
+        // test hook: a bounded wait on a barrier that nothing arrives at; every
+        // CTA gives up the same way and skips the integration
+        if (threadIdx.x == 0 && !mbar_wait_bounded(smem_addr(&h->dead_bar), 0u, a.timeout_ns)) {
+            h->abort = 1;
+            atomicCAS(a.status, 0, FTWA_ERR_DEVICE_TIMEOUT);
+        }
+        __syncthreads();
+    }
+
+    const int rb0 = a.row_begin[rank], rb1 = a.row_begin[rank + 1];
+    const long long n_batches = (a.M + S - 1) / S;
+    const bool run = h->abort == 0;
+    for (long long b_id = cid; run && b_id < n_batches; b_id += ncl) {
+        // ---- load rho(0): stored elements (upper part and mirror band) of own rows
+        for (int slot = 0; slot < S; ++slot) {
+            const long long m = b_id * S + slot;
+            const int slot_off = slot * a.slot_bytes;
+            for (int sr = rb0 + warp; sr < rb1; sr += kWarpsT) {
+                const int s = sr / N, p = sr % N, lo = p > a.bw ? p - a.bw : 0;
+                for (int k = lo + lane; k < N; k += 32) {
+                    float2 v = make_float2(0.f, 0.f);
+                    if (m < a.M) {
+                        if (k >= p) {
+                            v = a.rho[((m * 2 + s) * N + p) * (long long)N + k];
+                        } else {
+                            v = a.rho[((m * 2 + s) * N + k) * (long long)N + p];
+                            v.y = -v.y;
+                        }
+                    }
+                    if (k == p) {
+                        v.y = 0.f;
+                        if (a.snap && m < a.M) a.snap[m * twoN + s * N + p] = v.x;
+                        const int di = slot * twoN + s * N + p;   // stage buffer 0
+                        if constexpr (CLUSTER) {
+                            const uint32_t da = c.diag_s + (uint32_t)(4 * di);
+                            for (int r = 0; r < C; ++r) {
+                                const uint32_t ra = map_rank(da, (uint32_t)r);
+                                asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(v.x) : "memory");
+                            }
+                        } else {
+                            diag[di] = v.x;
+                        }
+                    }
+                    const int off = c.buf0 + slot_off + elem_off(a.zoff[rank], s, p, k, a.qoff);
+                    *reinterpret_cast<float2 *>(smem + off) = v;
+                }
+            }
+        }
+        // y0 of the computed elements into tensor memory (acc is written at stage 0)
+        {
+            int e = 0;
+            for (int it = 0; it < a.k_tiles; ++it) {
+                const uint2 td = __ldg(&c.tiles[it]);
+                if (td.x == 0xFFFFFFFFu) break;
+                const int p0 = td.x & 511, cnt = (td.x >> 9) & 15, blk = (td.x >> 13) & 7, slot = (td.x >> 16) & 255;
+                const int s = p0 >= N ? 1 : 0;
+                const int q = a.qoff + 32 * blk + lane;
+                const long long m = b_id * S + slot;
+                for (int i = 0; i < cnt; i += 2) {
+                    float2 v[2];
+                    for (int j = 0; j < 2; ++j) {
+                        const int p = p0 - s * N + i + j;
+                        v[j] = make_float2(0.f, 0.f);
+                        if (i + j < cnt && q >= p && q < N && m < a.M) {
+                            v[j] = a.rho[((m * 2 + s) * N + p) * (long long)N + q];
+                            if (q == p) v[j].y = 0.f;
+                        }
+                    }
+                    __syncwarp();
+                    tm_st4(c.t_state + (uint32_t)(8 * (e + (i >> 1))), v[0], v[1]);
+                }
+                e += (cnt + 1) >> 1;
+            }
+        }
+        tmem_wait_st();
+        stage_sync<CLUSTER>();
+
+        for (long long step = 0; step < a.n_steps; ++step) {
+            const bool snap_now = a.snap && ((step + 1) % a.out_every == 0);
+            const long long snap_row = (step + 1) / a.out_every;
+            tile_stage<0, PM1, CLUSTER>(a, c, b_id, snap_now, snap_row);
+            tmem_wait_st();
+            stage_sync<CLUSTER>();
+            tile_stage<1, PM1, CLUSTER>(a, c, b_id, snap_now, snap_row);
+            tmem_wait_st();
+            stage_sync<CLUSTER>();
+            tile_stage<2, PM1, CLUSTER>(a, c, b_id, snap_now, snap_row);
+            tmem_wait_st();
+            stage_sync<CLUSTER>();
+            tile_stage<3, PM1, CLUSTER>(a, c, b_id, snap_now, snap_row);
+            tmem_wait_st();
+            stage_sync<CLUSTER>();
+        }
+
+        // ---- write back rho(T) (full Hermitian matrix) from the y0 words
+        {
+            int e = 0;
+            for (int it = 0; it < a.k_tiles; ++it) {
+                const uint2 td = __ldg(&c.tiles[it]);
+                if (td.x == 0xFFFFFFFFu) break;
+                const int p0 = td.x & 511, cnt = (td.x >> 9) & 15, blk = (td.x >> 13) & 7, slot = (td.x >> 16) & 255;
+                const int s = p0 >= N ? 1 : 0;
+                const int q = a.qoff + 32 * blk + lane;
+                const long long m = b_id * S + slot;
+                for (int i = 0; i < cnt; i += 2) {
+                    uint32_t w[8];
+                    __syncwarp();
+                    tm_ld8(c.t_state + (uint32_t)(8 * (e + (i >> 1))), w);
+                    tm_wait8(w);
+                    for (int j = 0; j < 2 && i + j < cnt; ++j) {
+                        const int p = p0 - s * N + i + j;
+                        const float2 y = make_float2(__uint_as_float(w[2 * j]), __uint_as_float(w[2 * j + 1]));
+                        if (q >= p && q < N && m < a.M) {
+                            if (!(isfinite(y.x) && isfinite(y.y))) atomicCAS(a.status, 0, FTWA_ERR_NONFINITE);
+                            a.rho[((m * 2 + s) * N + p) * (long long)N + q] = y;
+                            if (p != q) a.rho[((m * 2 + s) * N + q) * (long long)N + p] = make_float2(y.x, -y.y);
+                        }
+                    }
+                }
+                e += (cnt + 1) >> 1;
+            }
+        }
+        __syncwarp();
+        // the next batch overwrites the stage buffers that peers read until here
+        stage_sync<CLUSTER>();
+    }
+
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (warp == 0) tmem_dealloc(h->tmem_base, kTmemCols);
+    if constexpr (CLUSTER) cluster_sync_hw();
+}
+
+// ---------------------------------------------------------------------------
+// Host side: work decomposition (pure host code, also used by the layout check)
+// ---------------------------------------------------------------------------
+struct Nbr {
+    int k[3];
+    double t[3];
+    int deg;
+};
+
+struct Layout {
+    int N = 0, bw = 0, nblk = 0, qoff = 0, C = 1, S = 1, pm1 = 0;
+    int slot_bytes = 0, buf_bytes = 0, smem_bytes = 0, k_tiles = 0, rows_bytes = 0;
+    int row_begin[kMaxCluster + 1] = {0};
+    int zoff[kMaxCluster][2][kMaxBlk] = {};
+    std::vector<uint2> tiles;                    // [C][kWarpsT][k_tiles]
+    std::vector<int4> koff;                      // [C][nblk][32]
+    std::vector<float2> tq;                      // [nblk][32][3]
+    std::vector<RowEntry> rows;                  // [2N]
+    std::vector<int> slices;                     // per rank
+};
+
+static void neighbours(const Plan *p, std::vector<Nbr> &nb)
+{
+    const int N = p->N;
+    nb.assign(N, Nbr{{0, 0, 0}, {0, 0, 0}, 0});
+    for (size_t b = 0; b < p->t_bond.size(); ++b) {
+        const int i = p->bonds[2 * b], j = p->bonds[2 * b + 1];
+        nb[i].k[nb[i].deg] = j;
+        nb[i].t[nb[i].deg++] = p->t_bond[b];
+        nb[j].k[nb[j].deg] = i;
+        nb[j].t[nb[j].deg++] = p->t_bond[b];
+    }
+}
+
+// every site's neighbours among p - 1, p + 1 and at most one other site
+static bool is_pm1(const std::vector<Nbr> &nb)
+{
+    const int N = (int)nb.size();
+    for (int p = 0; p < N; ++p) {
+        int far = 0;
+        for (int n = 0; n < nb[p].deg; ++n)
+            if (std::abs(nb[p].k[n] - p) != 1) ++far;
+        if (far > 1) return false;
+    }
+    return true;
+}
+
+// rank of spin-row sr
+static int owner(const Layout &L, int sr)
+{
+    int r = 0;
+    while (r + 1 < L.C && sr >= L.row_begin[r + 1]) ++r;
+    return r;
+}
+
+// Build the decomposition for C CTAs per sample and S slots (C == 1 only).
+// Returns false when it does not fit (shared memory, tensor memory, ranks
+// narrower than the bandwidth).
+static bool build_layout(const Plan *p, const std::vector<Nbr> &nb, bool pm1, int C, int S, Layout &L)
+{
+    const int N = p->N, bw = p->bandwidth;
+    L = Layout();
+    L.N = N;
+    L.bw = bw;
+    L.nblk = (N + 31) / 32;
+    L.qoff = N - 32 * L.nblk;
+    L.C = C;
+    L.S = S;
+    L.pm1 = pm1 ? 1 : 0;
+    const int nblk = L.nblk, qoff = L.qoff;
+    auto lastcol = [&](int b) { return qoff + 32 * b + 31; };
+    auto cslices = [&](int p_) { return nblk - blk_of(p_, qoff); };
+    if (C > kMaxCluster || (C > 1 && (C & 1))) return false;
+    // ---- ranks: C == 1 both spins; C >= 2 each spin split in C/2 ranks, balanced by computed slices
+    if (C == 1) {
+        L.row_begin[0] = 0;
+        L.row_begin[1] = 2 * N;
+    } else {
+        const int per = C / 2;
+        std::vector<int> cut(per + 1, 0);
+        double tot = 0;
+        for (int x = 0; x < N; ++x) tot += cslices(x);
+        int x = 0;
+        double acc = 0;
+        for (int r = 1; r < per; ++r) {
+            const double target = tot * r / per;
+            while (x < N && acc + 0.5 * cslices(x) < target) acc += cslices(x++);
+            cut[r] = x;
+        }
+        cut[per] = N;
+        for (int s = 0; s < 2; ++s)
+            for (int r = 0; r < per; ++r) L.row_begin[s * per + r] = s * N + cut[r];
+        L.row_begin[C] = 2 * N;
+        for (int r = 0; r < C; ++r) {
+            const int rows = L.row_begin[r + 1] - L.row_begin[r];
+            if (rows < 1) return false;
+            // column-part and mirror partners are at most bw rows away: they must
+            // lie in this rank or an adjacent rank of the same spin
+            if (per > 1 && rows < bw) return false;
+        }
+    }
+    // ---- regions: per rank, spin, block: rows [P0, min(P1, lastcol + bw + 1))
+    int slot_bytes = 0, max_rows = 0;
+    for (int r = 0; r < C; ++r) {
+        int off = 0;
+        max_rows = std::max(max_rows, L.row_begin[r + 1] - L.row_begin[r]);
+        for (int s = 0; s < 2; ++s) {
+            const int P0 = std::max(L.row_begin[r], s * N) - s * N;
+            const int P1 = std::min(L.row_begin[r + 1], s * N + N) - s * N;
+            if (P1 <= P0) continue;
+            for (int b = 0; b < nblk; ++b) {
+                const int hi = std::max(P0, std::min(P1, lastcol(b) + bw + 1));
+                const int rows = hi - P0;
+                L.zoff[r][s][b] = off - P0 * kRowBytes;
+                off += rows * kRowBytes;
+            }
+        }
+        slot_bytes = std::max(slot_bytes, off);
+    }
+    L.slot_bytes = slot_bytes;
+    L.buf_bytes = S * slot_bytes;
+    L.rows_bytes = max_rows * (int)sizeof(RowEntry);
+    const int diag_bytes = 16 * ((4 * 2 * S * 2 * N + 15) / 16);
+    L.smem_bytes = 64 + diag_bytes + L.rows_bytes + 2 * L.buf_bytes;
+    if (L.smem_bytes > 227 * 1024) return false;
+
+    // ---- column-part table (per spin-row, from the owner's point of view)
+    L.rows.assign((size_t)2 * N, RowEntry{});
+    for (int sr = 0; sr < 2 * N; ++sr) {
+        const int s = sr / N, pp = sr % N, r = owner(L, sr);
+        RowEntry e{};
+        int slot_k[3] = {pp, pp, pp};      // empty slot: the own row, zero hopping
+        double slot_t[3] = {0.0, 0.0, 0.0};
+        if (pm1) {
+            // slots: p - 1, p + 1, the far neighbour
+            for (int n = 0; n < nb[pp].deg; ++n) {
+                const int k = nb[pp].k[n];
+                const int sl = k == pp - 1 ? 0 : (k == pp + 1 ? 1 : 2);
+                slot_k[sl] = k;
+                slot_t[sl] = nb[pp].t[n];
+            }
+        } else {
+            for (int n = 0; n < nb[pp].deg; ++n) {
+                slot_k[n] = nb[pp].k[n];
+                slot_t[n] = nb[pp].t[n];
+            }
+        }
+        for (int n = 0; n < 3; ++n) {
+            e.mt[n] = -(float)slot_t[n];
+            if (pm1 && n < 2) continue;          // carried rows p -+ 1
+            const int k = slot_k[n];
+            const int ksr = s * N + k;
+            const bool remote = ksr < L.row_begin[r] || ksr >= L.row_begin[r + 1];
+            if (remote) {
+                const int o = owner(L, ksr);
+                if (std::abs(o - r) != 1 || o / std::max(C / 2, 1) != r / std::max(C / 2, 1)) return false;
+                e.flags |= 1u << n;
+                if (o == r + 1) e.flags |= 1u << (3 + n);
+                e.dcol[n] = kRowBytes * k;
+            } else {
+                e.dcol[n] = kRowBytes * (k - pp);
+            }
+        }
+        e.mir = L.zoff[r][s][blk_of(pp, qoff)] + 8 * lane_of(pp, qoff);
+        L.rows[sr] = e;
+    }
+    // ---- row-part offsets per rank, block, lane; hoppings per block, lane
+    L.koff.assign((size_t)C * nblk * 32, int4{0, 0, 0, 0});
+    L.tq.assign((size_t)nblk * 32 * 3, make_float2(0.f, 0.f));
+    for (int b = 0; b < nblk; ++b)
+        for (int ln = 0; ln < 32; ++ln) {
+            const int q = qoff + 32 * b + ln;
+            if (q < 0) continue;
+            for (int n = 0; n < nb[q].deg; ++n) {
+                const float t = (float)nb[q].t[n];
+                L.tq[(b * 32 + ln) * 3 + n] = make_float2(t, t);
+            }
+            for (int r = 0; r < C; ++r) {
+                const int s = L.row_begin[r] >= N ? 1 : 0;
+                int o[3] = {0, 0, 0};
+                for (int n = 0; n < nb[q].deg; ++n) {
+                    const int k = nb[q].k[n];
+                    o[n] = L.zoff[r][s][blk_of(k, qoff)] - L.zoff[r][s][b] + 8 * (lane_of(k, qoff) - ln);
+                }
+                L.koff[((size_t)r * nblk + b) * 32 + ln] = int4{o[0], o[1], o[2], 0};
+            }
+        }
+    if (C == 1 && N > 0) {
+        // both spins share one table: their regions have the same sizes
+        for (int b = 0; b < nblk; ++b)
+            if (L.zoff[0][1][b] - L.zoff[0][1][0] != L.zoff[0][0][b] - L.zoff[0][0][0]) return false;
+    }
+
+    // ---- tiles, assigned to warps longest first under the tensor-memory cap
+    const int pairs_cap = kColsPerWarp / 8;
+    std::vector<uint2> all_tiles;
+    int kt = 1;
+    std::vector<std::vector<uint2>> per_rank_warp((size_t)C * kWarpsT);
+    L.slices.assign(C, 0);
+    for (int r = 0; r < C; ++r) {
+        std::vector<std::pair<int, uint2>> tl;
+        for (int slot = 0; slot < S; ++slot)
+            for (int s = 0; s < 2; ++s) {
+                const int P0 = std::max(L.row_begin[r], s * N) - s * N;
+                const int P1 = std::min(L.row_begin[r + 1], s * N + N) - s * N;
+                if (P1 <= P0) continue;
+                for (int b = 0; b < nblk; ++b) {
+                    const int last = std::min(P1, lastcol(b) + 1);
+                    for (int x = P0; x < last;) {
+                        const int cnt = std::min(kR, last - x);
+                        uint2 td;
+                        td.x = (uint32_t)(s * N + x) | ((uint32_t)cnt << 9) | ((uint32_t)b << 13) | ((uint32_t)slot << 16);
+                        uint32_t f = 0;
+                        const int c0 = qoff + 32 * b;
+                        for (int i = 0; i < cnt; ++i) {
+                            const int pp = x + i;
+                            if (blk_of(pp, qoff) == b) f |= kDiag;
+                            if (pp + bw >= c0 && pp < lastcol(b)) f |= kBand;
+                            if (L.rows[s * N + pp].flags & 7u) f |= kRemote;
+                        }
+                        if (pm1) {
+                            const int prev = x - 1, next = x + cnt;
+                            uint32_t pk = 0, nk = 0;
+                            if (prev < P0) pk = prev < 0 ? 1u : 2u;
+                            if (next >= P1) nk = next >= N ? 1u : 2u;
+                            if (pk == 2 && r == 0) return false;
+                            if (nk == 2 && r + 1 >= C) return false;
+                            f |= pk << kPrevShift;
+                            f |= nk << kNextShift;
+                        }
+                        td.y = f;
+                        tl.push_back({cnt, td});
+                        L.slices[r] += cnt;
+                        x += cnt;
+                    }
+                }
+            }
+        std::stable_sort(tl.begin(), tl.end(), [](const auto &u, const auto &v) { return u.first > v.first; });
+        std::vector<int> load(kWarpsT, 0), pairs(kWarpsT, 0);
+        for (const auto &t : tl) {
+            int w = -1;
+            for (int x = 0; x < kWarpsT; ++x)
+                if (pairs[x] + (t.first + 1) / 2 <= pairs_cap && (w < 0 || load[x] < load[w])) w = x;
+            if (w < 0) return false;
+            load[w] += t.first;
+            pairs[w] += (t.first + 1) / 2;
+            per_rank_warp[(size_t)r * kWarpsT + w].push_back(t.second);
+        }
+        for (int x = 0; x < kWarpsT; ++x) kt = std::max<int>(kt, (int)per_rank_warp[(size_t)r * kWarpsT + x].size());
+    }
+    L.k_tiles = kt;
+    L.tiles.assign((size_t)C * kWarpsT * kt, uint2{0xFFFFFFFFu, 0u});
+    for (size_t rw = 0; rw < per_rank_warp.size(); ++rw)
+        for (size_t i = 0; i < per_rank_warp[rw].size(); ++i) L.tiles[rw * kt + i] = per_rank_warp[rw][i];
+    return true;
+}
+
+// Simulate every shared-memory address the kernel forms for one sample slot
+// and check it: reads of active lanes hit the intended element (or the zero
+// row for empty slots), every read stays inside the buffer of the rank it
+// addresses, every computed element is written exactly once per stage and
+// every mirror-band entry exactly once.  Returns the number of violations.
+static long long check_layout(const Layout &L, const std::vector<Nbr> &nb, char *msg, int msg_len)
+{
+    const int N = L.N, nblk = L.nblk, qoff = L.qoff, C = L.C;
+    long long bad = 0;
+    auto note = [&](const char *what, int r, int sr, int q) {
+        if (bad++ == 0 && msg) snprintf(msg, (size_t)msg_len, "%s (rank %d, row %d, column %d)", what, r, sr, q);
+    };
+    // logical element of every stored byte offset, per rank: key = s*N*N + p*N + q
+    std::vector<std::vector<int>> who(C, std::vector<int>((size_t)L.slot_bytes / 8 + 1, -1));
+    for (int r = 0; r < C; ++r)
+        for (int sr = L.row_begin[r]; sr < L.row_begin[r + 1]; ++sr) {
+            const int s = sr / N, p = sr % N, lo = p > L.bw ? p - L.bw : 0;
+            for (int q = lo; q < N; ++q) {
+                const int off = elem_off(L.zoff[r], s, p, q, qoff);
+                if (off < 0 || off + 8 > L.slot_bytes || (off & 7)) {
+                    note("stored element outside the slot", r, sr, q);
+                    continue;
+                }
+                if (who[r][off / 8] != -1) note("two elements share a slot", r, sr, q);
+                who[r][off / 8] = (s * N + p) * N + q;
+            }
+        }
+    auto read_ok = [&](int r, int off, int want, bool active, int sr, int q, const char *what) {
+        if (off < 0 || off + 8 > L.slot_bytes || (off & 7)) {
+            note(what, r, sr, q);
+            return;
+        }
+        if (!active) return;
+        if (who[r][off / 8] != want) note(what, r, sr, q);
+    };
+    std::vector<int> writes((size_t)2 * N * N, 0), mwrites((size_t)2 * N * N, 0);
+    for (int r = 0; r < C; ++r)
+        for (int w = 0; w < kWarpsT; ++w)
+            for (int it = 0; it < L.k_tiles; ++it) {
+                const uint2 td = L.tiles[((size_t)r * kWarpsT + w) * L.k_tiles + it];
+                if (td.x == 0xFFFFFFFFu) break;
+                const int p0 = td.x & 511, cnt = (td.x >> 9) & 15, b = (td.x >> 13) & 7, slot = (td.x >> 16) & 255;
+                if (slot != 0) continue;
+                const int s = p0 >= N ? 1 : 0, pp0 = p0 - s * N;
+                for (int ln = 0; ln < 32; ++ln) {
+                    const int q = qoff + 32 * b + ln;
+                    const int4 ko = L.koff[((size_t)r * nblk + b) * 32 + ln];
+                    const int own0 = L.zoff[r][s][b] + kRowBytes * pp0 + 8 * ln;
+                    for (int i = 0; i < cnt; ++i) {
+                        const int p = pp0 + i, sr = s * N + p;
+                        const bool act = q >= p && q < N && q >= 0;
+                        const int own = own0 + kRowBytes * i;
+                        read_ok(r, own, (s * N + p) * N + q, act, sr, q, "own read");
+                        const int kk[3] = {ko.x, ko.y, ko.z};
+                        for (int n = 0; n < 3; ++n) {
+                            const bool real = q >= 0 && n < nb[q].deg;
+                            read_ok(r, own + kk[n], real ? (s * N + p) * N + nb[q].k[n] : -3, act && real, sr, q,
+                                    "row-part read");
+                        }
+                        const RowEntry &e = L.rows[sr];
+                        for (int n = 0; n < 3; ++n) {
+                            if (L.pm1 && n < 2) {
+                                // carried rows p -+ 1: from the tile, or the boundary rows
+                                const int k = n == 0 ? p - 1 : p + 1;
+                                const bool in_tile = n == 0 ? i > 0 : i + 1 < cnt;
+                                if (in_tile || e.mt[n] == 0.f) continue;
+                                const uint32_t kind = (td.y >> (n == 0 ? kPrevShift : kNextShift)) & 3;
+                                if (kind == 2) {
+                                    const int o = n == 0 ? r - 1 : r + 1;
+                                    read_ok(o, elem_off(L.zoff[o], s, k, q, qoff), (s * N + k) * N + q, act, sr, q,
+                                            "boundary-row read (remote)");
+                                } else if (kind == 0) {
+                                    read_ok(r, own + (n == 0 ? -kRowBytes : kRowBytes), (s * N + k) * N + q, act, sr,
+                                            q, "boundary-row read");
+                                } else {
+                                    note("absent boundary row with a nonzero hopping", r, sr, q);
+                                }
+                                continue;
+                            }
+                            if (e.flags & (1u << n)) {
+                                const int o = (e.flags >> (3 + n)) & 1u ? r + 1 : r - 1;
+                                const int k = e.dcol[n] / kRowBytes;
+                                read_ok(o, L.zoff[o][s][b] + e.dcol[n] + 8 * ln, (s * N + k) * N + q, act, sr, q,
+                                        "column-part read (remote)");
+                            } else {
+                                const int k = p + e.dcol[n] / kRowBytes;
+                                read_ok(r, own + e.dcol[n], (s * N + k) * N + q, act, sr, q, "column-part read");
+                            }
+                        }
+                        if (act) {
+                            writes[(size_t)(s * N + p) * N + q]++;
+                            if (q > p && q - p <= L.bw) {
+                                const int qsr = s * N + q;
+                                const int o = qsr < L.row_begin[r + 1] ? r : r + 1;
+                                const int bp = blk_of(p, qoff);
+                                const int mir_next = o < C ? e.mir - L.zoff[r][s][bp] + L.zoff[o][s][bp] : 0;
+                                const int off = (o == r ? e.mir : mir_next) + kRowBytes * q;
+                                if (o >= C) {
+                                    note("mirror row beyond the last rank", r, sr, q);
+                                } else {
+                                    read_ok(o, off, (s * N + q) * N + p, true, sr, q, "mirror store");
+                                    mwrites[(size_t)(s * N + q) * N + p]++;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+    for (int s = 0; s < 2; ++s)
+        for (int p = 0; p < N; ++p)
+            for (int q = 0; q < N; ++q) {
+                const size_t k = (size_t)(s * N + p) * N + q;
+                if (q >= p && writes[k] != 1) note("computed element not written exactly once", 0, s * N + p, q);
+                if (q < p && q >= p - L.bw && mwrites[k] != 1) note("mirror entry not written exactly once", 0, s * N + p, q);
+                if ((q < p && writes[k]) || (q >= p && mwrites[k])) note("write outside its triangle", 0, s * N + p, q);
+            }
+    return bad;
+}
+
+// Choose C (1, 2, 4, 8) and S: the smallest cluster that fits, with as many
+// slots as useful for C == 1.
+static bool choose_layout(const Plan *p, int64_t M, const std::vector<Nbr> &nb, bool pm1, Layout &out)
+{
+    const int sm = p->sm_count > 0 ? p->sm_count : 1;
+    for (int C = 1; C <= kMaxCluster; C *= 2) {
+        if (p->cluster_override && C != p->cluster_override) continue;
+        int want = 1;
+        if (C == 1) want = (int)std::max<long long>(1, std::min<long long>((M + sm - 1) / sm, 255));
+        Layout best;
+        bool ok = false;
+        for (int S = 1; S <= want; ++S) {
+            Layout L;
+            if (!build_layout(p, nb, pm1, C, S, L)) break;
+            best = L;
+            ok = true;
+        }
+        if (ok) {
+            out = best;
+            return true;
+        }
+    }
+    return false;
+}
+
+}  // namespace tile
+
+// FP32 plans with the on-site U (no drive or long-range field): the tiled
+// stepper, when a shape fits.
+bool tile_supported(const Plan *p)
+{
+    return p->precision == FTWA_FP32 && !p->drive && !p->longrange && !p->hop_drive && p->N <= FTWA_MAX_SITES &&
+           p->N >= 2;
+}
+
+int launch_tile(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cudaStream_t s)
+{
+    using namespace tile;
+    if (!tile_supported(p)) return FTWA_ERR_UNSUPPORTED;
+    std::vector<Nbr> nb;
+    neighbours(p, nb);
+    const bool pm1 = is_pm1(nb);
+    Layout L;
+    if (!choose_layout(p, M, nb, pm1, L)) return FTWA_ERR_UNSUPPORTED;
+    const int sm = p->sm_count > 0 ? p->sm_count : 1;
+    const long long batches = (M + L.S - 1) / L.S;
+    int grid = (int)std::min<long long>(std::max<long long>(batches, 1), std::max(1, sm / L.C)) * L.C;
+    auto kern = L.C > 1 ? (pm1 ? tile_stepper<true, true> : tile_stepper<false, true>)
+                        : (pm1 ? tile_stepper<true, false> : tile_stepper<false, false>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem_bytes);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(kThreadsT, 1, 1);
+    cfg.dynamicSmemBytes = L.smem_bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = L.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = L.C > 1 ? 1 : 0;
+    if (L.C > 1) {
+        int n_clusters = 0;
+        e = cudaOccupancyMaxActiveClusters(&n_clusters, kern, &cfg);
+        if (e != cudaSuccess) return set_cuda_error(e);
+        if (n_clusters < 1) return FTWA_ERR_UNSUPPORTED;
+        grid = std::min(grid, n_clusters * L.C);
+        cfg.gridDim = dim3(grid, 1, 1);
+    }
+    // tables: rows | tiles | koff | tq in one plan-owned device buffer (16-byte aligned parts)
+    const size_t b_rows = L.rows.size() * sizeof(RowEntry);
+    const size_t b_tiles = ((L.tiles.size() * sizeof(uint2) + 15) / 16) * 16;
+    const size_t b_koff = L.koff.size() * sizeof(int4);
+    const size_t b_tq = L.tq.size() * sizeof(float2);
+    const size_t bytes = b_rows + b_tiles + b_koff + b_tq;
+    if (p->tile_bytes < bytes) {
+        cudaFree(p->d_tile);
+        p->d_tile = nullptr;
+        p->tile_bytes = 0;
+        e = cudaMalloc(&p->d_tile, bytes);
+        if (e != cudaSuccess) return set_cuda_error(e);
+        p->tile_bytes = bytes;
+    }
+    std::vector<unsigned char> host(bytes, 0);
+    std::memcpy(host.data(), L.rows.data(), b_rows);
+    std::memcpy(host.data() + b_rows, L.tiles.data(), L.tiles.size() * sizeof(uint2));
+    std::memcpy(host.data() + b_rows + b_tiles, L.koff.data(), b_koff);
+    std::memcpy(host.data() + b_rows + b_tiles + b_koff, L.tq.data(), b_tq);
+    if (p->tile_host != host) {
+        // a changed table is uploaded (never during stream capture: batch
+        // creation prepares every plan first)
+        p->tile_host = host;
+        e = cudaMemcpyAsync(p->d_tile, p->tile_host.data(), bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            p->tile_host.clear();
+            return set_cuda_error(e);
+        }
+    }
+    p->shape.cluster = L.C;
+    p->shape.slots = L.S;
+    p->shape.units_per_warp = 0;
+    for (int r = 0; r < L.C; ++r) p->shape.units_per_warp = std::max(p->shape.units_per_warp, L.slices[r]);
+    p->shape.units_per_warp = (p->shape.units_per_warp + kWarpsT - 1) / kWarpsT;
+    p->shape.smem_bytes = L.smem_bytes;
+    p->shape.grid = grid;
+    p->shape.variant = 3;
+    if (M == 0 || p->dry_run) return FTWA_OK;
+
+    TileArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.N = L.N;
+    a.C = L.C;
+    a.S = L.S;
+    a.nblk = L.nblk;
+    a.qoff = L.qoff;
+    a.bw = L.bw;
+    a.slot_bytes = L.slot_bytes;
+    a.buf_bytes = L.buf_bytes;
+    a.k_tiles = L.k_tiles;
+    a.U = (float)p->U;
+    a.dt = (float)p->dt;
+    a.M = M;
+    a.n_steps = n_steps;
+    a.out_every = p->out_every;
+    a.rho = reinterpret_cast<float2 *>(rho);
+    a.snap = reinterpret_cast<float *>(snap);
+    a.status = p->d_status;
+    a.timeout_ns = p->timeout_ns;
+    a.force_timeout = p->force_timeout;
+    for (int i = 0; i <= kMaxCluster; ++i) a.row_begin[i] = L.row_begin[std::min(i, L.C)];
+    std::memcpy(a.zoff, L.zoff, sizeof(a.zoff));
+    unsigned char *base = static_cast<unsigned char *>(p->d_tile);
+    a.rows = reinterpret_cast<const RowEntry *>(base);
+    a.rows_bytes = L.rows_bytes;
+    a.tiles = reinterpret_cast<const uint2 *>(base + b_rows);
+    a.koff = reinterpret_cast<const int4 *>(base + b_rows + b_tiles);
+    a.tq = reinterpret_cast<const float2 *>(base + b_rows + b_tiles + b_koff);
+    e = cudaLaunchKernelEx(&cfg, kern, a);
+    return set_cuda_error(e);
+}
+
+}  // namespace ftwa
+
+// Host-only consistency check of the tiled stepper's work decomposition for a
+// lattice (no device needed); see include/ftwa.h.
+extern "C" int ftwa_debug_tile_check(int32_t n_sites, int32_t n_bonds, const int32_t *bonds, const double *t_bond,
+                                     int32_t cluster, int32_t slots, int64_t *violations, char *msg, int32_t msg_len)
+{
+    using namespace ftwa;
+    using namespace ftwa::tile;
+    if (n_sites < 2 || n_sites > FTWA_MAX_SITES || n_bonds < 0 || (!bonds && n_bonds) || !violations)
+        return FTWA_ERR_INVALID_ARGUMENT;
+    if (msg && msg_len > 0) msg[0] = 0;
+    Plan p;
+    p.N = n_sites;
+    p.precision = FTWA_FP32;
+    p.bonds.assign(bonds, bonds + 2 * (size_t)n_bonds);
+    p.t_bond.assign((size_t)n_bonds, 1.0);
+    if (t_bond)
+        for (int b = 0; b < n_bonds; ++b) p.t_bond[b] = t_bond[b];
+    std::vector<int> deg(n_sites, 0);
+    p.bandwidth = 1;
+    for (int b = 0; b < n_bonds; ++b) {
+        const int i = bonds[2 * b], j = bonds[2 * b + 1];
+        if (i < 0 || j >= n_sites || i >= j) return FTWA_ERR_INVALID_ARGUMENT;
+        if (++deg[i] > 3 || ++deg[j] > 3) return FTWA_ERR_UNSUPPORTED;
+        p.bandwidth = std::max(p.bandwidth, j - i);
+    }
+    std::vector<Nbr> nb;
+    neighbours(&p, nb);
+    Layout L;
+    if (!build_layout(&p, nb, is_pm1(nb), cluster, slots, L)) return FTWA_ERR_UNSUPPORTED;
+    *violations = check_layout(L, nb, msg, msg_len);
+    return FTWA_OK;
+}

@@ -167,3 +167,53 @@ def test_adjoint_matches_oracle_adjoint(ftwa, lat_name, U, ckpt):
         assert abs(got[0][0] - want[0]) <= tol * scale
         assert np.abs(got[1] - want[1]).max() <= tol * scale
         assert np.abs(got[2] - want[2]).max() <= tol * scale
+
+
+@pytest.mark.parametrize("lat_name,U,ckpt", [("chain10", 1.6, 10), ("periodic8", 2.5, 30), ("flake24", 1.0, 15)])
+def test_adjoint_corr_matches_oracle_adjoint(ftwa, lat_name, U, ckpt):
+    """Correlation losses (ftwa_adjoint_corr): the GPU adjoint for a random
+    linear loss sum g <n> + sum G C (G not symmetric, C the connected
+    correlator of Eq. 5) against the oracle's discrete RK4 adjoint (pinned to
+    finite differences at 1e-8): FP64 to 1e-10 of the largest gradient entry,
+    FP32 to 2e-3.  The forward means come from the GPU's own moments."""
+    from oracle import adjoint as OA
+    lat = {"chain10": W.hexagon_chain(2), "periodic8": W.periodic_honeycomb(),
+           "flake24": W.hexagonal_flake(2)}[lat_name]
+    n0u, n0d = W.neel_state(lat)
+    nu, nd = W.softened(n0u), W.softened(n0d)
+    N, seed, M, steps, every = lat.n_sites, 10, 5, 30, 5
+    rng = np.random.default_rng(4)
+    T = steps // every + 1
+    g = rng.standard_normal((T, 2 * N))
+    G = rng.standard_normal((T, 2 * N, 2 * N))
+    snap, _ = oracle.run(lat, U, nu, nd, seed, 0, M, 0.01, steps, every)
+    want = OA.adjoint(lat, U, nu, nd, seed, M, 0.01, steps, every, g, gC=G, mu=snap.mean(axis=1))
+    scale = max(abs(want[0]), np.abs(want[1]).max(), np.abs(want[2]).max())
+    for precision, tol in ((0, 1e-10), (1, 2e-3)):
+        with ftwa.Plan(lat, U, n_up=nu, n_dn=nd, precision=precision, out_every=every) as P:
+            X = P.evolve(P.sample(seed, M), steps)
+            occ, _, _ = P.moments(X, g2=False)
+            got = [x.cpu().numpy() for x in P.adjoint(seed, M, steps, ckpt, torch.from_numpy(g).cuda(),
+                                                      dL_dconn=torch.from_numpy(G).cuda(), occ=occ)]
+            # the correlation term alone (no occupation cotangent) is accepted too
+            P.adjoint(seed, M, steps, ckpt, None, dL_dconn=torch.from_numpy(G).cuda(), occ=occ)
+            assert P.status() == 0
+        assert abs(got[0][0] - want[0]) <= tol * scale
+        assert np.abs(got[1] - want[1]).max() <= tol * scale
+        assert np.abs(got[2] - want[2]).max() <= tol * scale
+
+
+def test_adjoint_corr_rejects_missing_means(ftwa):
+    from paper_2212_04352_gb300 import _lib as L
+    import ctypes
+    lat = W.periodic_honeycomb()
+    nu, nd = W.softened(W.neel_state(lat)[0]), W.softened(W.neel_state(lat)[1])
+    G = torch.zeros((5, 16, 16), dtype=torch.float64, device="cuda")
+    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=0, out_every=10) as P:
+        p = ctypes.c_void_p
+        rc = ftwa.load().ftwa_adjoint_corr(P._h, 1, 2, 40, 20, None, p(G.data_ptr()), None, None, None, None, None)
+        assert rc == L.FTWA_ERR_INVALID_ARGUMENT
+        rc = ftwa.load().ftwa_adjoint_corr(P._h, 1, 2, 40, 20, None, None, None, None, None, None, None)
+        assert rc == L.FTWA_ERR_INVALID_ARGUMENT
+        with pytest.raises(ValueError):
+            P.adjoint(1, 2, 40, 20, None, dL_dconn=G)

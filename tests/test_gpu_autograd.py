@@ -134,3 +134,51 @@ def test_errors(ftwa):
         occ.sum().backward()
     with pytest.raises(ftwa.FtwaError):          # occupation outside [0, 1]
         ftwa.occupations(lat, 1.6, lat.t_bond, n0 + 1.0, SEED, M, STEPS)
+
+
+def test_correlations_autograd_matches_finite_differences(ftwa):
+    """correlations(): a nonlinear loss of the occupations, the connected
+    correlator and g2 (Eq. 10, formed in torch from occ and conn) differentiated
+    by the RK4 adjoint (ftwa_adjoint_corr) against central differences of the
+    wrapped forward (FP64, h = 1e-5, same seed): dL/dU, every dL/dt_b and
+    every dL/dn0 to 1e-6 of the largest entry.  Occupations 0.2 / 0.8: g2
+    divides by <n_k><n_l>, and near-empty sites make the loss so curved that
+    central differences at h = 1e-5 are off by 1e-3."""
+    lat, _ = _setup()
+    nu, nd = W.neel_state(lat)
+    n0 = np.stack([W.softened(nu, 0.2), W.softened(nd, 0.2)])
+    tb0 = np.array(lat.t_bond, dtype=np.float64)
+    rng = np.random.default_rng(8)
+    T, K = STEPS // EVERY + 1, 2 * lat.n_sites
+    w_c = torch.from_numpy(rng.standard_normal((T, K, K))).cuda()
+    w_g = torch.from_numpy(rng.standard_normal((T, K, K)) * 0.01).cuda()
+
+    def loss(U, tb, n):
+        occ, conn = ftwa.correlations(lat, U, tb, n, SEED, M, STEPS, out_every=EVERY, ckpt_every=CKPT)
+        nn = occ[:, :, None] * occ[:, None, :]
+        g2 = (conn + nn) / nn
+        return (occ ** 2).sum() + (w_c * conn).sum() + (w_c * conn ** 2).sum() + (w_g * g2).sum()
+
+    U = torch.tensor(1.6, dtype=torch.float64, requires_grad=True)
+    tb = torch.tensor(tb0, requires_grad=True)
+    n = torch.tensor(n0, requires_grad=True)
+    L = loss(U, tb, n)
+    L.backward()
+    h = 1e-5
+    with torch.no_grad():
+        def f(du=0.0, dt=None, dn=None):
+            return float(loss(torch.tensor(1.6 + du, dtype=torch.float64),
+                              torch.tensor(tb0 + (0 if dt is None else dt)),
+                              torch.tensor(n0 + (0 if dn is None else dn))))
+        fdU = (f(du=h) - f(du=-h)) / (2 * h)
+        fdt = np.array([(f(dt=h * e) - f(dt=-h * e)) / (2 * h) for e in np.eye(lat.n_bonds)])
+        fdn = np.zeros_like(n0)
+        for s in range(2):
+            for i in range(lat.n_sites):
+                e = np.zeros_like(n0)
+                e[s, i] = h
+                fdn[s, i] = (f(dn=e) - f(dn=-e)) / (2 * h)
+    scale = max(abs(fdU), np.abs(fdt).max(), np.abs(fdn).max())
+    assert abs(U.grad.item() - fdU) <= 1e-6 * scale
+    assert np.abs(tb.grad.numpy() - fdt).max() <= 1e-6 * scale
+    assert np.abs(n.grad.numpy() - fdn).max() <= 1e-6 * scale

@@ -151,7 +151,18 @@ def test_evolve_198_sites_fp64(ftwa, variant):
     assert np.max(np.abs(X.cpu().numpy() - snap_o)) <= 1e-10
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+def _tile_fits(lat, cluster):
+    """Whether the tiled stepper (variant 3) has a decomposition for this
+    lattice and cluster size (host-side check, no launch)."""
+    import ctypes
+    from paper_2212_04352_gb300 import _lib as L
+    b = np.ascontiguousarray(lat.bonds, dtype=np.int32)
+    v = ctypes.c_int64()
+    return L.load().ftwa_debug_tile_check(lat.n_sites, len(b), b.ctypes.data, None, cluster, 1, ctypes.byref(v),
+                                          None, 0) == 0
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("lat_name", ["periodic8", "brick198"])
 def test_evolve_fp32_short(ftwa, lat_name, variant):
     lat = W.periodic_honeycomb() if lat_name == "periodic8" else W.brick_wall_flake()
@@ -169,14 +180,19 @@ def test_evolve_fp32_short(ftwa, lat_name, variant):
         assert _rel(fin[m], fin_o[m]) <= 1e-4
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("cluster", [1, 2, 4, 8])
-@pytest.mark.parametrize("lat_name", ["chain7", "brick35", "flake54"])
+@pytest.mark.parametrize("lat_name", ["chain7", "brick35", "flake54", "flake96", "brick198"])
 def test_evolve_fp32_shapes(ftwa, lat_name, cluster, variant):
-    """FP32 steppers (1: banded, 2: packed triangle) on odd and even lattice
-    sizes (ragged first column block of the banded layout) and every cluster
-    split; ragged M."""
-    lat = {"chain7": W.chain(7), "brick35": W.brick_wall_flake(5, 7), "flake54": W.hexagonal_flake(3)}[lat_name]
+    """FP32 steppers (1: banded, 2: packed triangle, 3: tiled) on odd and
+    even lattice sizes (ragged first column block), lattices with and without
+    the p -+ 1 neighbour order, and every cluster split that fits; ragged M."""
+    lat = {"chain7": W.chain(7), "brick35": W.brick_wall_flake(5, 7), "flake54": W.hexagonal_flake(3),
+           "flake96": W.hexagonal_flake(4), "brick198": W.brick_wall_flake()}[lat_name]
+    if lat.n_sites > 60 and variant != 3:
+        pytest.skip("large lattices: tiled stepper only (the others are covered above)")
+    if variant == 3 and not _tile_fits(lat, cluster):
+        pytest.skip("no tiled decomposition for this cluster size")
     nu, nd = W.neel_state(lat)
     M, steps = 5, 100
     rho0 = _oracle_states(lat, nu, nd, 21, M)
@@ -235,8 +251,8 @@ def test_timeout_hook_returns_status(ftwa):
     FTWA_ERR_DEVICE_TIMEOUT; the context stays usable afterwards."""
     lat = W.hexagonal_flake(3)
     nu, nd = W.neel_state(lat)
-    for cluster, variant in [(1, 1), (2, 1), (1, 2), (2, 2)]:
-        with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=0, cluster=cluster, timeout_us=2000,
+    for cluster, variant, prec in [(1, 1, 0), (2, 1, 0), (1, 2, 0), (2, 2, 0), (1, 3, 1), (4, 3, 1)]:
+        with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=prec, cluster=cluster, timeout_us=2000,
                        variant=variant) as P:
             rho = P.sample(1, 2)
             r0 = rho.clone()

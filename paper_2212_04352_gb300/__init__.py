@@ -40,7 +40,7 @@ class Plan:
     """Owner of one ftwa_plan_t (lattice tables, launch shape, status word)."""
 
     def __init__(self, lattice, U, t=1.0, filling=0.0, n_up=None, n_dn=None, precision=FTWA_FP64,
-                 dt=0.01, out_every=10, cluster=0, timeout_us=0, variant=0):
+                 dt=0.01, out_every=10, cluster=0, timeout_us=0, variant=0, threads=0):
         lib = load()
         self.N = int(lattice.n_sites)
         self.n_bonds = int(lattice.n_bonds)
@@ -54,7 +54,7 @@ class Plan:
             self._nu = np.ascontiguousarray(n_up, dtype=np.float64)
             self._nd = np.ascontiguousarray(n_dn, dtype=np.float64)
             init = _lib.InitState(self._nu.ctypes.data, self._nd.ctypes.data)
-        opts = _lib.Options(int(precision), float(dt), int(out_every), int(cluster), 0, 0, int(timeout_us),
+        opts = _lib.Options(int(precision), float(dt), int(out_every), int(cluster), int(threads), 0, int(timeout_us),
                             int(variant))
         h = ctypes.c_void_p()
         check(lib.ftwa_plan(ctypes.byref(lat), float(U), float(t), float(filling),

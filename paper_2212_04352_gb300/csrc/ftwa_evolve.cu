@@ -1437,6 +1437,7 @@ static int band_launch(Plan *p, BandShape &sh, void *rho, int64_t M, int64_t n_s
     p->shape.smem_bytes = sh.smem_bytes;
     p->shape.grid = sh.grid;
     p->shape.variant = 1;
+    p->shape.threads = kThreads;
     if (M == 0 || p->dry_run) return FTWA_OK;
     BandArgs<T> a{};
     a.nbr = p->d_nbr;
@@ -1553,10 +1554,10 @@ int launch_evolve(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cu
         return p->precision == FTWA_FP64 ? band_dispatch<double>(p, bs, rho, M, n_steps, snap, s)
                                          : band_dispatch<float>(p, bs, rho, M, n_steps, snap, s);
     }
-    // automatic choice: the banded stepper for FP32; for FP64 (DFMA-bound on
-    // this part) the packed-triangle stepper, which does fewer flops per
-    // element.  The tiled stepper runs when asked for (or chosen by the autotuner).
-    if (p->variant_override == 3) {
+    // automatic choice: the tiled stepper for FP32 (the banded one when no
+    // tiled shape fits); for FP64 (DFMA-bound on this part) the packed-triangle
+    // stepper, which does fewer flops per element
+    if (p->variant_override == 3 || (p->variant_override == 0 && tile_supported(p))) {
         const int rc = launch_tile(p, rho, M, n_steps, snap, s);
         if (rc != FTWA_ERR_UNSUPPORTED || p->variant_override == 3) return rc;
     }

@@ -29,6 +29,7 @@ struct StepperShape {
     int row_begin[kMaxCluster + 1] = {0};  // spin-row partition over ranks
     int grid = 0;           // CTAs launched
     int variant = 0;        // 1 = banded stepper, 2 = general packed-triangle stepper, 3 = tiled stepper
+    int threads = kThreads; // threads per CTA
 };
 
 // Launch shape of the banded stepper.

@@ -266,7 +266,9 @@ int ftwa_plan(const ftwa_lattice *lat, double U, double t, double filling, const
     if (o.cluster_override < 0 || o.cluster_override > kMaxCluster ||
         (o.cluster_override & (o.cluster_override - 1)) != 0)
         return FTWA_ERR_INVALID_ARGUMENT;
-    if (o.threads_override != 0 && o.threads_override != kThreads) return FTWA_ERR_UNSUPPORTED;
+    // 768 threads for every stepper; the tiled stepper also runs with 512
+    if (o.threads_override != 0 && o.threads_override != kThreads && !(o.threads_override == 512 && o.variant == 3))
+        return FTWA_ERR_UNSUPPORTED;
     if (o.variant < 0 || o.variant > 3) return FTWA_ERR_INVALID_ARGUMENT;
 
     ftwa_plan_t *p = new (std::nothrow) ftwa_plan_t();
@@ -424,7 +426,7 @@ int ftwa_plan(const ftwa_lattice *lat, double U, double t, double filling, const
     {
         BandShape bs;
         const bool try_band = p->variant_override == 1 || (p->variant_override == 0 && p->precision == FTWA_FP32);
-        if (p->variant_override == 3) {
+        if (p->variant_override == 3 || (p->variant_override == 0 && tile_supported(p))) {
             // shape of the tiled stepper for one sample per cluster (tables are
             // built and uploaded by the first evolve)
             p->dry_run = true;
@@ -439,6 +441,7 @@ int ftwa_plan(const ftwa_lattice *lat, double U, double t, double filling, const
             p->shape.smem_bytes = bs.smem_bytes;
             p->shape.grid = bs.grid;
             p->shape.variant = 1;
+            p->shape.threads = kThreads;
             rc = FTWA_OK;
         } else if (p->variant_override == 1) {
             rc = FTWA_ERR_UNSUPPORTED;
@@ -475,7 +478,7 @@ int ftwa_get_info(const ftwa_plan_t *p, ftwa_plan_info *info)
     info->n_bonds = p->B;
     info->precision = p->precision;
     info->cluster = p->shape.cluster;
-    info->threads = kThreads;
+    info->threads = p->shape.threads;
     info->samples_per_cta = p->shape.slots;
     info->smem_bytes = p->shape.smem_bytes;
     info->tmem_cols = kTmemCols;

@@ -40,9 +40,10 @@ namespace ftwa {
 namespace tile {
 
 constexpr int kR = 8;                     // rows per tile
-constexpr int kThreadsT = 768;            // threads per CTA
-constexpr int kWarpsT = kThreadsT / 32;
-constexpr int kColsPerWarp = 80;          // tensor-memory columns per warp (6 warps per lane quadrant)
+constexpr int kMaxWarpsT = 24;            // warps per CTA: 16 (512 threads) or 24 (768)
+// tensor-memory columns per warp: warps w, w + 4, ... share lane quadrant w % 4
+// and split the 512 columns (multiples of 8 for the 8-column row-pair blocks)
+__host__ __device__ constexpr int cols_per_warp(int warps) { return (512 / (warps / 4)) / 8 * 8; }
 constexpr int kMaxBlk = (FTWA_MAX_SITES + 31) / 32;
 constexpr int kRowBytes = 256;            // one row of a 32-column block
 
@@ -71,10 +72,11 @@ enum : uint32_t {
     kPrevShift = 3,    // 2 bits: row p0 - 1 is 0 local, 1 absent (zero hopping), 2 in the previous rank
     kNextShift = 5,    // 2 bits: row p0 + cnt is 0 local, 1 absent (zero hopping), 2 in the next rank
     kRemote = 128u,    // some row of the tile reads a column-part slot of another rank
+    kRemoteMir = 256u, // some mirror-band row of the tile may belong to the next rank
 };
 
 struct TileArgs {
-    int N, C, S, nblk, qoff, bw;
+    int N, C, S, nblk, qoff, bw, warps;
     int slot_bytes, buf_bytes;       // one slot of one stage buffer; one stage buffer
     int k_tiles;                     // tile entries per warp
     float U, dt;
@@ -87,7 +89,7 @@ struct TileArgs {
     int force_timeout;
     int row_begin[kMaxCluster + 1];  // spin-rows of each rank
     int zoff[kMaxCluster][2][kMaxBlk];   // Z(s, b) of each rank (byte offset inside a slot)
-    const uint2 *tiles;              // [C][kWarpsT][k_tiles]
+    const uint2 *tiles;              // [C][warps][k_tiles]
     const int4 *koff;                // [C][nblk][32] row-part byte offsets of the three slots
     const float2 *tq;                // [nblk][32][3] (t, t) of the row-part slots
     const RowEntry *rows;            // [2N]
@@ -161,6 +163,10 @@ struct TileCtx {
 
 // One RK4 stage over the rows of one tile.  Stage buffer CUR = STAGE & 1
 // holds the stage state; the next stage state goes to the other buffer.
+// Everything that depends only on the lane (column) or only on the tile is
+// formed once per tile; the rare cases (the diagonal, the mirror band, rows
+// of another rank) are warp-uniform branches or per-lane predicates on
+// values formed per tile.
 template <int STAGE, bool PM1, bool CLUSTER>
 __device__ __forceinline__ void tile_rows(const TileArgs &a, const TileCtx &c, uint2 td, int e_base, long long b_id,
                                           bool snap_now, long long snap_row)
@@ -168,16 +174,16 @@ __device__ __forceinline__ void tile_rows(const TileArgs &a, const TileCtx &c, u
     constexpr int CUR = STAGE & 1;
     const int N = a.N, twoN = 2 * N, lane = c.lane;
     const int p0 = td.x & 511, cnt = (td.x >> 9) & 15, blk = (td.x >> 13) & 7, slot = (td.x >> 16) & 255;
-    const bool diag_t = (td.y & kDiag) != 0, band_t = (td.y & kBand) != 0;
+    const bool diag_t = (td.y & kDiag) != 0, band_t = (td.y & kBand) != 0, rmir_t = (td.y & kRemoteMir) != 0;
     const int s = p0 >= N ? 1 : 0;
     const int pp0 = p0 - s * N;                       // site index of row 0 of the tile
-    const int q = a.qoff + 32 * blk + lane;
+    const int c0 = a.qoff + 32 * blk;
+    const int q = c0 + lane;
     const int qc = q < 0 ? 0 : q;
     const int slot_off = slot * a.slot_bytes;
     const int cur_off = c.buf0 + CUR * a.buf_bytes + slot_off;
     const int dnext = (CUR ? -1 : 1) * a.buf_bytes;   // next stage buffer minus this one
-    const int z = a.zoff[c.rank][s][blk];
-    const int own0 = cur_off + z + kRowBytes * pp0 + 8 * lane;     // element (p0, q)
+    const int own0 = cur_off + a.zoff[c.rank][s][blk] + kRowBytes * pp0 + 8 * lane;   // element (p0, q)
     const int4 ko = __ldg(&a.koff[(c.rank * a.nblk + blk) * 32 + lane]);
     const float2 *tqp = a.tq + (blk * 32 + lane) * 3;
     const float2 tq0 = __ldg(tqp), tq1 = __ldg(tqp + 1), tq2 = __ldg(tqp + 2);
@@ -188,18 +194,25 @@ __device__ __forceinline__ void tile_rows(const TileArgs &a, const TileCtx &c, u
     const float uq = a.U * ldf(dg_off + 4 * qc);
     const float hdt = a.dt * 0.5f, sdt = a.dt * (1.0f / 6.0f);
     const int rt0 = c.rows_off + (int)sizeof(RowEntry) * (p0 - c.rb0);
+    // cluster-space addresses of (row 0, column q) in the previous / next rank's current buffer
+    uint32_t base_prev = 0, base_next = 0;
+    if constexpr (CLUSTER) {
+        if (c.rank > 0) base_prev = c.prev_c + (uint32_t)(cur_off + a.zoff[c.rank - 1][s][blk] + 8 * lane);
+        if (c.rank + 1 < a.C) base_next = c.next_c + (uint32_t)(cur_off + a.zoff[c.rank + 1][s][blk] + 8 * lane);
+    }
+    // mirror band: row q of this rank, or of the next one
+    const bool mir_local = s * N + q < c.rb1;
+    const int mir_lane = kRowBytes * q + cur_off + dnext;
+    float dnew = 0.f;                                 // this lane's new diagonal value (q == p)
 
-    // carried column-part values of rows p - 1 and p (PM1)
-    float2 vprev = make_float2(0.f, 0.f), vcur = make_float2(0.f, 0.f);
-    const uint32_t nk = (td.y >> kNextShift) & 3;
+    // carried column-part values (PM1): rows p0 - 1 and p0 + cnt of the tile
+    float2 vprev = make_float2(0.f, 0.f), vcur = make_float2(0.f, 0.f), vlast = make_float2(0.f, 0.f);
     if constexpr (PM1) {
-        const uint32_t pk = (td.y >> kPrevShift) & 3;
-        if (pk == 2) {
-            const int zp = a.zoff[c.rank - 1][s][blk];
-            vprev = ld_cluster(c.prev_c + (uint32_t)(cur_off + zp + kRowBytes * (pp0 - 1) + 8 * lane));
-        } else {
-            vprev = lds(pk == 0 ? own0 - kRowBytes : own0);   // absent: any finite value, zero hopping
-        }
+        const uint32_t pk = (td.y >> kPrevShift) & 3, nk = (td.y >> kNextShift) & 3;
+        if (CLUSTER && pk == 2) vprev = ld_cluster(base_prev + (uint32_t)(kRowBytes * (pp0 - 1)));
+        else vprev = lds(pk == 0 ? own0 - kRowBytes : own0);          // absent: a finite value, zero hopping
+        if (CLUSTER && nk == 2) vlast = ld_cluster(base_next + (uint32_t)(kRowBytes * (pp0 + cnt)));
+        else vlast = lds(nk == 0 ? own0 + kRowBytes * cnt : own0);
         vcur = lds(own0);
     }
 
@@ -216,23 +229,12 @@ __device__ __forceinline__ void tile_rows(const TileArgs &a, const TileCtx &c, u
         // - sum_{k in nb(p)} t_pk rho_kq (column q)
         if constexpr (PM1) {
             ov = vcur;
-            float2 vnext;
-            if (i + 1 < cnt) {
-                vnext = lds(own + kRowBytes);
-            } else if (nk == 2) {
-                const int zn = a.zoff[c.rank + 1][s][blk];
-                vnext = ld_cluster(c.next_c + (uint32_t)(cur_off + zn + kRowBytes * (p + 1) + 8 * lane));
-            } else {
-                vnext = lds(nk == 0 ? own + kRowBytes : own);
-            }
+            const bool in_tile = i + 1 < cnt;
+            const float2 vn = lds(in_tile ? own + kRowBytes : own);
+            const float2 vnext = in_tile ? vn : vlast;
             float2 vf;
-            if (re.flags & 4u) {
-                const bool nx = (re.flags & 32u) != 0;
-                const int zo = a.zoff[nx ? c.rank + 1 : c.rank - 1][s][blk];
-                vf = ld_cluster((nx ? c.next_c : c.prev_c) + (uint32_t)(cur_off + zo + re.dcol[2] + 8 * lane));
-            } else {
-                vf = lds(own + re.dcol[2]);
-            }
+            if (CLUSTER && (re.flags & 4u)) vf = ld_cluster(((re.flags & 32u) ? base_next : base_prev) + (uint32_t)re.dcol[2]);
+            else vf = lds(own + re.dcol[2]);
             h.x = fmaf(re.mt[0], vprev.x, h.x);
             h.y = fmaf(re.mt[0], vprev.y, h.y);
             h.x = fmaf(re.mt[1], vnext.x, h.x);
@@ -246,13 +248,10 @@ __device__ __forceinline__ void tile_rows(const TileArgs &a, const TileCtx &c, u
 #pragma unroll
             for (int n = 0; n < 3; ++n) {
                 float2 v;
-                if (re.flags & (1u << n)) {
-                    const bool nx = (re.flags >> (3 + n)) & 1u;
-                    const int zo = a.zoff[nx ? c.rank + 1 : c.rank - 1][s][blk];
-                    v = ld_cluster((nx ? c.next_c : c.prev_c) + (uint32_t)(cur_off + zo + re.dcol[n] + 8 * lane));
-                } else {
+                if (CLUSTER && (re.flags & (1u << n)))
+                    v = ld_cluster((((re.flags >> (3 + n)) & 1u) ? base_next : base_prev) + (uint32_t)re.dcol[n]);
+                else
                     v = lds(own + re.dcol[n]);
-                }
                 h.x = fmaf(re.mt[n], v.x, h.x);
                 h.y = fmaf(re.mt[n], v.y, h.y);
             }
@@ -263,7 +262,7 @@ __device__ __forceinline__ void tile_rows(const TileArgs &a, const TileCtx &c, u
         h.y = fmaf(coef, ov.y, h.y);
         // k = i h; the diagonal of Eq. 6 is real (the imaginary part is rounding residue)
         const float kx = -h.y;
-        const float ky = (diag_t && q == p) ? 0.f : h.x;
+        const float ky = q == p ? 0.f : h.x;
         float2 nx;
         if constexpr (STAGE == 0) {
             acc.x = kx;
@@ -281,32 +280,22 @@ __device__ __forceinline__ void tile_rows(const TileArgs &a, const TileCtx &c, u
             nx.y = fmaf(sdt, acc.y + ky, y0.y);
             y0 = nx;
         }
-        if (!diag_t || q >= p) sts(own + dnext, nx);
-        if (band_t && q > p && q - p <= a.bw) {
-            // mirror entry (q, p) = conj(rho_pq) in row q (this rank or the next)
+        if (q >= p) sts(own + dnext, nx);
+        if (q == p) dnew = nx.x;
+        if (band_t) {
+            // mirror entry (q, p) = conj(rho_pq) in row q, for 0 < q - p <= bw
+            const bool mb = (unsigned)(q - p - 1) < (unsigned)a.bw;
             const float2 cj = make_float2(nx.x, -nx.y);
-            if (s * N + q < c.rb1) {
-                sts(cur_off + dnext + re.mir + kRowBytes * q, cj);
-            } else {
-                const int bp = blk_of(p, a.qoff);
-                const int mir_next = re.mir - a.zoff[c.rank][s][bp] + a.zoff[c.rank + 1][s][bp];
-                st_cluster(c.next_c + (uint32_t)(cur_off + dnext + mir_next + kRowBytes * q), cj);
-            }
-        }
-        if (diag_t && q == p) {
-            const int di = ((CUR ^ 1) * a.S + slot) * twoN + s * N + p;
-            if constexpr (CLUSTER) {
-                const uint32_t da = c.diag_s + (uint32_t)(4 * di);
-                for (int r = 0; r < a.C; ++r) {
-                    const uint32_t ra = map_rank(da, (uint32_t)r);
-                    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(nx.x) : "memory");
+            if (!rmir_t) {
+                if (mb) sts(re.mir + mir_lane, cj);
+            } else if (mb) {
+                if (mir_local) {
+                    sts(re.mir + mir_lane, cj);
+                } else {
+                    const int bp = blk_of(p, a.qoff);
+                    const int mn = re.mir - a.zoff[c.rank][s][bp] + a.zoff[c.rank + 1][s][bp];
+                    st_cluster(c.next_c + (uint32_t)(mn + mir_lane), cj);
                 }
-            } else {
-                *reinterpret_cast<float *>(tile_smem + c.diag_off + 4 * di) = nx.x;
-            }
-            if (STAGE == 3 && snap_now) {
-                const long long m = b_id * a.S + slot;
-                if (m < a.M) a.snap[(snap_row * a.M + m) * twoN + s * N + p] = nx.x;
             }
         }
     };
@@ -326,6 +315,24 @@ __device__ __forceinline__ void tile_rows(const TileArgs &a, const TileCtx &c, u
         else tm_st4(ta, y0a, y0b);
         if (i + 2 < cnt) tm_ld8(ta + 8, w);
     }
+    if (diag_t && q >= pp0 && q < pp0 + cnt) {
+        // the lanes holding a row's diagonal publish its new value to every
+        // rank's diagonal table, and to the snapshot
+        const int di = ((CUR ^ 1) * a.S + slot) * twoN + s * N + q;
+        if constexpr (CLUSTER) {
+            const uint32_t da = c.diag_s + (uint32_t)(4 * di);
+            for (int r = 0; r < a.C; ++r) {
+                const uint32_t ra = map_rank(da, (uint32_t)r);
+                asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(dnew) : "memory");
+            }
+        } else {
+            *reinterpret_cast<float *>(tile_smem + c.diag_off + 4 * di) = dnew;
+        }
+        if (STAGE == 3 && snap_now) {
+            const long long m = b_id * a.S + slot;
+            if (m < a.M) a.snap[(snap_row * a.M + m) * twoN + s * N + q] = dnew;
+        }
+    }
 }
 
 template <int STAGE, bool PM1, bool CLUSTER>
@@ -341,8 +348,8 @@ __device__ __forceinline__ void tile_stage(const TileArgs &a, const TileCtx &c, 
     }
 }
 
-template <bool PM1, bool CLUSTER>
-__global__ void __launch_bounds__(kThreadsT, 1) tile_stepper(const __grid_constant__ TileArgs a)
+template <bool PM1, bool CLUSTER, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) tile_stepper(const __grid_constant__ TileArgs a)
 {
     unsigned char *smem = tile_smem;
     const int N = a.N, S = a.S, C = a.C, twoN = 2 * N;
@@ -370,7 +377,8 @@ __global__ void __launch_bounds__(kThreadsT, 1) tile_stepper(const __grid_consta
         if (rank > 0) c.prev_c = map_rank(c.smem_s, rank - 1);
         if ((int)rank + 1 < C) c.next_c = map_rank(c.smem_s, rank + 1);
     }
-    c.tiles = a.tiles + ((size_t)rank * kWarpsT + warp) * a.k_tiles;
+    constexpr int WARPS = THREADS / 32;
+    c.tiles = a.tiles + ((size_t)rank * WARPS + warp) * a.k_tiles;
     c.lane = lane;
 
     if (threadIdx.x == 0) {
@@ -391,7 +399,7 @@ __global__ void __launch_bounds__(kThreadsT, 1) tile_stepper(const __grid_consta
     __syncthreads();
     tmem_fence_after();
     if constexpr (CLUSTER) cluster_sync_hw();
-    c.t_state = h->tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(kColsPerWarp * (warp >> 2));
+    c.t_state = h->tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(cols_per_warp(WARPS) * (warp >> 2));
 
     if (a.force_timeout) {
         // test hook: a bounded wait on a barrier that nothing arrives at; every
@@ -411,7 +419,7 @@ __global__ void __launch_bounds__(kThreadsT, 1) tile_stepper(const __grid_consta
         for (int slot = 0; slot < S; ++slot) {
             const long long m = b_id * S + slot;
             const int slot_off = slot * a.slot_bytes;
-            for (int sr = rb0 + warp; sr < rb1; sr += kWarpsT) {
+            for (int sr = rb0 + warp; sr < rb1; sr += WARPS) {
                 const int s = sr / N, p = sr % N, lo = p > a.bw ? p - a.bw : 0;
                 for (int k = lo + lane; k < N; k += 32) {
                     float2 v = make_float2(0.f, 0.f);
@@ -542,10 +550,13 @@ struct Layout {
     int slot_bytes = 0, buf_bytes = 0, smem_bytes = 0, k_tiles = 0, rows_bytes = 0;
     int row_begin[kMaxCluster + 1] = {0};
     int zoff[kMaxCluster][2][kMaxBlk] = {};
-    std::vector<uint2> tiles;                    // [C][kWarpsT][k_tiles]
+    int warps = 24;                              // warps per CTA
+    std::vector<uint2> tiles;                    // [C][warps][k_tiles]
     std::vector<int4> koff;                      // [C][nblk][32]
     std::vector<float2> tq;                      // [nblk][32][3]
     std::vector<RowEntry> rows;                  // [2N]
+    std::vector<int> rp_k;                       // [nblk][32][3] column read by each row-part slot
+    std::vector<char> rp_real;                   // [nblk][32][3] the slot is a bond (else zero hopping)
     std::vector<int> slices;                     // per rank
 };
 
@@ -586,10 +597,12 @@ static int owner(const Layout &L, int sr)
 // Build the decomposition for C CTAs per sample and S slots (C == 1 only).
 // Returns false when it does not fit (shared memory, tensor memory, ranks
 // narrower than the bandwidth).
-static bool build_layout(const Plan *p, const std::vector<Nbr> &nb, bool pm1, int C, int S, Layout &L)
+static bool build_layout(const Plan *p, const std::vector<Nbr> &nb, bool pm1, int C, int S, int warps, Layout &L)
 {
     const int N = p->N, bw = p->bandwidth;
     L = Layout();
+    L.warps = warps;
+    const int kWarpsT = warps;
     L.N = N;
     L.bw = bw;
     L.nblk = (N + 31) / 32;
@@ -694,27 +707,81 @@ static bool build_layout(const Plan *p, const std::vector<Nbr> &nb, bool pm1, in
         e.mir = L.zoff[r][s][blk_of(pp, qoff)] + 8 * lane_of(pp, qoff);
         L.rows[sr] = e;
     }
-    // ---- row-part offsets per rank, block, lane; hoppings per block, lane
-    L.koff.assign((size_t)C * nblk * 32, int4{0, 0, 0, 0});
+    // ---- row-part slots per column q: the column read (k) and its hopping.
+    // PM1 lattices: slots q - 1, q + 1, far, and a missing neighbour reads a
+    // stored decoy column with zero hopping, chosen so that each slot's
+    // 16-lane half-warp gather hits 16 distinct shared-memory bank pairs
+    // (the bank pair of column k is (k - qoff) mod 16 in this layout).
+    // Other lattices: the neighbour list, empty slots read the own element.
+    L.rp_k.assign((size_t)nblk * 32 * 3, 0);
+    L.rp_real.assign((size_t)nblk * 32 * 3, 0);
     L.tq.assign((size_t)nblk * 32 * 3, make_float2(0.f, 0.f));
+    auto bank = [&](int k) { return ((k - qoff) % 16 + 16) % 16; };
     for (int b = 0; b < nblk; ++b)
-        for (int ln = 0; ln < 32; ++ln) {
-            const int q = qoff + 32 * b + ln;
-            if (q < 0) continue;
-            for (int n = 0; n < nb[q].deg; ++n) {
-                const float t = (float)nb[q].t[n];
-                L.tq[(b * 32 + ln) * 3 + n] = make_float2(t, t);
+        for (int h = 0; h < 2; ++h) {
+            bool used[3][16] = {};
+            std::vector<int> pending[3];
+            for (int ln = 16 * h; ln < 16 * h + 16; ++ln) {
+                const int q = qoff + 32 * b + ln;
+                int *rk = &L.rp_k[(size_t)(b * 32 + ln) * 3];
+                char *re_ = &L.rp_real[(size_t)(b * 32 + ln) * 3];
+                float2 *tq = &L.tq[(size_t)(b * 32 + ln) * 3];
+                const int qq = q < 0 ? 0 : q;
+                for (int n = 0; n < 3; ++n) rk[n] = qq;
+                if (q < 0) continue;
+                if (pm1) {
+                    for (int n = 0; n < nb[q].deg; ++n) {
+                        const int k = nb[q].k[n];
+                        const int sl = k == q - 1 ? 0 : (k == q + 1 ? 1 : 2);
+                        rk[sl] = k;
+                        re_[sl] = 1;
+                        tq[sl] = make_float2((float)nb[q].t[n], (float)nb[q].t[n]);
+                    }
+                    if (!re_[0] && q >= 1) rk[0] = q - 1;
+                    if (!re_[1] && q <= N - 2) rk[1] = q + 1;
+                    for (int sl = 0; sl < 3; ++sl) {
+                        if (re_[sl] || sl < 2) used[sl][bank(rk[sl])] = true;
+                        else pending[sl].push_back(ln);
+                    }
+                } else {
+                    for (int n = 0; n < nb[q].deg; ++n) {
+                        rk[n] = nb[q].k[n];
+                        re_[n] = 1;
+                        tq[n] = make_float2((float)nb[q].t[n], (float)nb[q].t[n]);
+                    }
+                }
             }
-            for (int r = 0; r < C; ++r) {
-                const int s = L.row_begin[r] >= N ? 1 : 0;
-                int o[3] = {0, 0, 0};
-                for (int n = 0; n < nb[q].deg; ++n) {
-                    const int k = nb[q].k[n];
+            for (int ln : pending[2]) {
+                const int q = qoff + 32 * b + ln;
+                int best = q;
+                for (int d = 1; d <= bw; ++d) {
+                    for (int sg = 1; sg >= -1; sg -= 2) {
+                        const int k = q + sg * d;
+                        if (k < 0 || k >= N || k < q - bw) continue;
+                        if (!used[2][bank(k)]) {
+                            best = k;
+                            d = bw + 1;
+                            break;
+                        }
+                    }
+                }
+                L.rp_k[(size_t)(b * 32 + ln) * 3 + 2] = best;
+                used[2][bank(best)] = true;
+            }
+        }
+    L.koff.assign((size_t)C * nblk * 32, int4{0, 0, 0, 0});
+    for (int r = 0; r < C; ++r) {
+        const int s = L.row_begin[r] >= N ? 1 : 0;
+        for (int b = 0; b < nblk; ++b)
+            for (int ln = 0; ln < 32; ++ln) {
+                int o[3];
+                for (int n = 0; n < 3; ++n) {
+                    const int k = L.rp_k[(size_t)(b * 32 + ln) * 3 + n];
                     o[n] = L.zoff[r][s][blk_of(k, qoff)] - L.zoff[r][s][b] + 8 * (lane_of(k, qoff) - ln);
                 }
                 L.koff[((size_t)r * nblk + b) * 32 + ln] = int4{o[0], o[1], o[2], 0};
             }
-        }
+    }
     if (C == 1 && N > 0) {
         // both spins share one table: their regions have the same sizes
         for (int b = 0; b < nblk; ++b)
@@ -722,7 +789,7 @@ static bool build_layout(const Plan *p, const std::vector<Nbr> &nb, bool pm1, in
     }
 
     // ---- tiles, assigned to warps longest first under the tensor-memory cap
-    const int pairs_cap = kColsPerWarp / 8;
+    const int pairs_cap = cols_per_warp(warps) / 8;
     std::vector<uint2> all_tiles;
     int kt = 1;
     std::vector<std::vector<uint2>> per_rank_warp((size_t)C * kWarpsT);
@@ -747,6 +814,7 @@ static bool build_layout(const Plan *p, const std::vector<Nbr> &nb, bool pm1, in
                             if (blk_of(pp, qoff) == b) f |= kDiag;
                             if (pp + bw >= c0 && pp < lastcol(b)) f |= kBand;
                             if (L.rows[s * N + pp].flags & 7u) f |= kRemote;
+                            if (pp + bw >= c0 && pp < lastcol(b) && s * N + pp + bw >= L.row_begin[r + 1]) f |= kRemoteMir;
                         }
                         if (pm1) {
                             const int prev = x - 1, next = x + cnt;
@@ -820,15 +888,20 @@ static long long check_layout(const Layout &L, const std::vector<Nbr> &nb, char 
         if (!active) return;
         if (who[r][off / 8] != want) note(what, r, sr, q);
     };
-    std::vector<int> writes((size_t)2 * N * N, 0), mwrites((size_t)2 * N * N, 0);
+    std::vector<int> writes((size_t)2 * N * N, 0), mwrites((size_t)2 * N * N, 0), dwrites((size_t)2 * N, 0);
     for (int r = 0; r < C; ++r)
-        for (int w = 0; w < kWarpsT; ++w)
+        for (int w = 0; w < L.warps; ++w)
             for (int it = 0; it < L.k_tiles; ++it) {
-                const uint2 td = L.tiles[((size_t)r * kWarpsT + w) * L.k_tiles + it];
+                const uint2 td = L.tiles[((size_t)r * L.warps + w) * L.k_tiles + it];
                 if (td.x == 0xFFFFFFFFu) break;
                 const int p0 = td.x & 511, cnt = (td.x >> 9) & 15, b = (td.x >> 13) & 7, slot = (td.x >> 16) & 255;
                 if (slot != 0) continue;
                 const int s = p0 >= N ? 1 : 0, pp0 = p0 - s * N;
+                // diagonal-table writes (once per row of a tile holding the row's diagonal)
+                for (int i = 0; i < cnt; ++i) {
+                    const int c0 = qoff + 32 * b, p = pp0 + i;
+                    if ((td.y & kDiag) && (unsigned)(p - c0) < 32u) dwrites[(size_t)s * N + p]++;
+                }
                 for (int ln = 0; ln < 32; ++ln) {
                     const int q = qoff + 32 * b + ln;
                     const int4 ko = L.koff[((size_t)r * nblk + b) * 32 + ln];
@@ -840,9 +913,14 @@ static long long check_layout(const Layout &L, const std::vector<Nbr> &nb, char 
                         read_ok(r, own, (s * N + p) * N + q, act, sr, q, "own read");
                         const int kk[3] = {ko.x, ko.y, ko.z};
                         for (int n = 0; n < 3; ++n) {
-                            const bool real = q >= 0 && n < nb[q].deg;
-                            read_ok(r, own + kk[n], real ? (s * N + p) * N + nb[q].k[n] : -3, act && real, sr, q,
-                                    "row-part read");
+                            const size_t ix = (size_t)(b * 32 + ln) * 3 + n;
+                            const bool real = L.rp_real[ix] != 0;
+                            const int k = L.rp_k[ix];
+                            // a decoy of an active lane must still read a stored element of row p
+                            const bool stored = k >= (p > L.bw ? p - L.bw : 0);
+                            read_ok(r, own + kk[n], (s * N + p) * N + k, act && (real || stored), sr, q,
+                                    real ? "row-part read" : "row-part decoy read");
+                            if (act && !real && !stored) note("row-part decoy outside the stored band", r, sr, q);
                         }
                         const RowEntry &e = L.rows[sr];
                         for (int n = 0; n < 3; ++n) {
@@ -893,6 +971,8 @@ static long long check_layout(const Layout &L, const std::vector<Nbr> &nb, char 
                     }
                 }
             }
+    for (int sr = 0; sr < 2 * N; ++sr)
+        if (dwrites[sr] != 1) note("diagonal not published exactly once", 0, sr, sr % N);
     for (int s = 0; s < 2; ++s)
         for (int p = 0; p < N; ++p)
             for (int q = 0; q < N; ++q) {
@@ -909,6 +989,7 @@ static long long check_layout(const Layout &L, const std::vector<Nbr> &nb, char 
 static bool choose_layout(const Plan *p, int64_t M, const std::vector<Nbr> &nb, bool pm1, Layout &out)
 {
     const int sm = p->sm_count > 0 ? p->sm_count : 1;
+    const int warps = p->threads_override == 512 ? 16 : 24;
     for (int C = 1; C <= kMaxCluster; C *= 2) {
         if (p->cluster_override && C != p->cluster_override) continue;
         int want = 1;
@@ -917,7 +998,7 @@ static bool choose_layout(const Plan *p, int64_t M, const std::vector<Nbr> &nb, 
         bool ok = false;
         for (int S = 1; S <= want; ++S) {
             Layout L;
-            if (!build_layout(p, nb, pm1, C, S, L)) break;
+            if (!build_layout(p, nb, pm1, C, S, warps, L)) break;
             best = L;
             ok = true;
         }
@@ -951,13 +1032,18 @@ int launch_tile(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cuda
     const int sm = p->sm_count > 0 ? p->sm_count : 1;
     const long long batches = (M + L.S - 1) / L.S;
     int grid = (int)std::min<long long>(std::max<long long>(batches, 1), std::max(1, sm / L.C)) * L.C;
-    auto kern = L.C > 1 ? (pm1 ? tile_stepper<true, true> : tile_stepper<false, true>)
-                        : (pm1 ? tile_stepper<true, false> : tile_stepper<false, false>);
+    void (*kern)(TileArgs);
+    if (L.warps == 16)
+        kern = L.C > 1 ? (pm1 ? tile_stepper<true, true, 512> : tile_stepper<false, true, 512>)
+                       : (pm1 ? tile_stepper<true, false, 512> : tile_stepper<false, false, 512>);
+    else
+        kern = L.C > 1 ? (pm1 ? tile_stepper<true, true, 768> : tile_stepper<false, true, 768>)
+                       : (pm1 ? tile_stepper<true, false, 768> : tile_stepper<false, false, 768>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem_bytes);
     if (e != cudaSuccess) return set_cuda_error(e);
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid, 1, 1);
-    cfg.blockDim = dim3(kThreadsT, 1, 1);
+    cfg.blockDim = dim3(32 * L.warps, 1, 1);
     cfg.dynamicSmemBytes = L.smem_bytes;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -1008,7 +1094,8 @@ int launch_tile(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cuda
     p->shape.slots = L.S;
     p->shape.units_per_warp = 0;
     for (int r = 0; r < L.C; ++r) p->shape.units_per_warp = std::max(p->shape.units_per_warp, L.slices[r]);
-    p->shape.units_per_warp = (p->shape.units_per_warp + kWarpsT - 1) / kWarpsT;
+    p->shape.units_per_warp = (p->shape.units_per_warp + L.warps - 1) / L.warps;
+    p->shape.threads = 32 * L.warps;
     p->shape.smem_bytes = L.smem_bytes;
     p->shape.grid = grid;
     p->shape.variant = 3;
@@ -1022,6 +1109,7 @@ int launch_tile(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cuda
     a.nblk = L.nblk;
     a.qoff = L.qoff;
     a.bw = L.bw;
+    a.warps = L.warps;
     a.slot_bytes = L.slot_bytes;
     a.buf_bytes = L.buf_bytes;
     a.k_tiles = L.k_tiles;
@@ -1076,8 +1164,14 @@ extern "C" int ftwa_debug_tile_check(int32_t n_sites, int32_t n_bonds, const int
     }
     std::vector<Nbr> nb;
     neighbours(&p, nb);
-    Layout L;
-    if (!build_layout(&p, nb, is_pm1(nb), cluster, slots, L)) return FTWA_ERR_UNSUPPORTED;
-    *violations = check_layout(L, nb, msg, msg_len);
-    return FTWA_OK;
+    // both CTA sizes the stepper launches with
+    *violations = 0;
+    bool any = false;
+    for (int warps : {16, 24}) {
+        Layout L;
+        if (!build_layout(&p, nb, is_pm1(nb), cluster, slots, warps, L)) continue;
+        any = true;
+        *violations += check_layout(L, nb, msg, msg_len);
+    }
+    return any ? FTWA_OK : FTWA_ERR_UNSUPPORTED;
 }

@@ -349,3 +349,30 @@ def test_gram_bf16x3_error_below_tenth_of_sampling_error(ftwa):
     d = torch.sqrt(torch.diagonal(c64, dim1=1, dim2=2))
     stat = d[:, :, None] * d[:, None, :] / M ** 0.5
     assert ((c16 - c64).abs() / stat).max().item() < 0.1
+
+
+@pytest.mark.parametrize("threads", [512, 768])
+@pytest.mark.parametrize("cluster", [1, 2, 4])
+@pytest.mark.parametrize("lat_name", ["brick35", "flake54", "brick198"])
+def test_evolve_fp32_tiled_threads(ftwa, lat_name, cluster, threads):
+    """The tiled stepper with 16 or 24 warps per CTA (different tile
+    assignments and tensor-memory splits): the oracle's trajectory to 1e-4
+    after 100 FP32 steps; output Hermitian."""
+    lat = {"brick35": W.brick_wall_flake(5, 7), "flake54": W.hexagonal_flake(3), "brick198": W.brick_wall_flake()}[lat_name]
+    if not _tile_fits(lat, cluster):
+        pytest.skip("no tiled decomposition for this cluster size")
+    nu, nd = W.neel_state(lat)
+    M, steps = 3, 100
+    rho0 = _oracle_states(lat, nu, nd, 23, M)
+    fin_o = np.stack([oracle.evolve(lat, 1.6, rho0[m], 0.01, steps)[0] for m in range(M)])
+    with ftwa.Plan(lat, 1.6, n_up=nu, n_dn=nd, precision=1, cluster=cluster, variant=3, threads=threads) as P:
+        inf = P.info()
+        assert inf["variant"] == 3 and inf["threads"] == threads and inf["cluster"] == cluster
+        rho = torch.from_numpy(rho0.astype(np.complex64)).cuda()
+        P.evolve(rho, steps, snap=None)
+        assert P.status() == 0
+        fin = rho.cpu().numpy().astype(np.complex128)
+    for m in range(M):
+        assert _rel(fin[m], fin_o[m]) <= 1e-4
+        for sp in range(2):
+            assert np.array_equal(fin[m, sp], fin[m, sp].conj().T)

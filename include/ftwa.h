@@ -343,6 +343,26 @@ int ftwa_autotune(ftwa_plan_t *plan, int64_t M, int32_t probe_steps, void *strea
 typedef struct ftwa_batch ftwa_batch_t;
 int ftwa_batch_create(ftwa_plan_t *const *plans, int32_t n, void *const *rho_dev, const int64_t *M, int64_t n_steps,
                       void *const *snap_dev, ftwa_batch_t **out);
+/* One persistent kernel for a batch of heterogeneous problems: plans[i]
+ * (FP32, on-site U, lattices of different sizes, any U) advances M[i] samples
+ * in rho_dev[i] by n_steps RK4 steps of Eq. 6 (snapshots into snap_dev[i] as
+ * for ftwa_evolve, if snap_dev and snap_dev[i] are not NULL).  Every
+ * problem's samples are cut into batches of S_i samples (S_i as large as the
+ * problem's tiled decomposition fits on chip for the batch's cluster size);
+ * the (problem, batch) work items are ordered by cost, largest first, and the
+ * launch's clusters (all co-resident clusters of the device) draw them from a
+ * queue in device memory until it is empty.  The launch is captured in a CUDA
+ * graph (the queue head's reset, then the kernel) replayed by
+ * ftwa_batch_launch.  The cluster size is the smallest every problem fits;
+ * with tune != 0 the cluster size (that and twice it) and the CTA size (512,
+ * 768 threads) are picked by timing a probe of each on scratch states
+ * (synchronous).  The batch owns copies of every table it needs; plans and
+ * buffers must outlive it.  Errors: FTWA_ERR_INVALID_ARGUMENT,
+ * FTWA_ERR_UNSUPPORTED (more than 24 problems, a plan that is not FP32 or has
+ * a drive or long-range field, no decomposition on chip),
+ * FTWA_ERR_OUT_OF_MEMORY, FTWA_ERR_CUDA. */
+int ftwa_batch_create_persistent(ftwa_plan_t *const *plans, int32_t n, void *const *rho_dev, const int64_t *M,
+                                 int64_t n_steps, void *const *snap_dev, int32_t tune, ftwa_batch_t **out);
 /* Replay the batch's graph on `stream`. */
 int ftwa_batch_launch(ftwa_batch_t *batch, void *stream);
 /* Release a batch (NULL is accepted). */

@@ -472,9 +472,15 @@ class ED:
 
 
 class Batch:
-    """One CUDA graph advancing several plans' samples (ftwa_batch_*)."""
+    """One CUDA graph advancing several plans' samples (ftwa_batch_*).
 
-    def __init__(self, plans, rhos, n_steps, snaps=None):
+    persistent=False: the graph's branches are the plans' own persistent
+    steppers (ftwa_batch_create).  persistent=True: one persistent kernel
+    drawing (problem, sample batch) items from a cost-ordered queue
+    (ftwa_batch_create_persistent; FP32 plans); tune=True times the cluster
+    and CTA sizes on a probe first."""
+
+    def __init__(self, plans, rhos, n_steps, snaps=None, persistent=False, tune=False):
         n = len(plans)
         self._plans = list(plans)          # keep the plans and buffers alive
         self._rhos = list(rhos)
@@ -487,7 +493,11 @@ class Batch:
         if snaps is not None:
             hs = (P * n)(*[0 if x is None else x.data_ptr() for x in snaps])
         h = P()
-        check(load().ftwa_batch_create(hp, n, hr, hm, int(n_steps), hs, ctypes.byref(h)), "ftwa_batch_create")
+        if persistent:
+            check(load().ftwa_batch_create_persistent(hp, n, hr, hm, int(n_steps), hs, 1 if tune else 0,
+                                                      ctypes.byref(h)), "ftwa_batch_create_persistent")
+        else:
+            check(load().ftwa_batch_create(hp, n, hr, hm, int(n_steps), hs, ctypes.byref(h)), "ftwa_batch_create")
         self._h = h
 
     def launch(self, stream=None):

@@ -27,6 +27,7 @@ EXPORTS = ("ftwa_plan", "ftwa_destroy", "ftwa_get_info", "ftwa_sample", "ftwa_se
            "ftwa_evolve", "ftwa_evolve_at", "ftwa_set_drive", "ftwa_set_hopping_drive", "ftwa_set_interaction",
            "ftwa_ed_plan", "ftwa_ed_destroy", "ftwa_ed_info", "ftwa_ed_evolve",
            "ftwa_moments", "ftwa_moments_noalloc", "ftwa_adjoint", "ftwa_adjoint_corr", "ftwa_autotune", "ftwa_batch_create",
+           "ftwa_batch_create_persistent",
            "ftwa_batch_launch", "ftwa_batch_destroy", "ftwa_status", "ftwa_debug_force_timeout",
            "ftwa_debug_tile_check", "ftwa_measure_peak", "ftwa_error_string",
            "ftwa_version")
@@ -96,6 +97,7 @@ def load(path: str = LIB_PATH):
     lib.ftwa_adjoint_corr.argtypes = [P, u64, i64, i64, i32, P, P, P, P, P, P, P]
     lib.ftwa_autotune.argtypes = [P, i64, i32, P]
     lib.ftwa_batch_create.argtypes = [P, i32, P, P, i64, P, ctypes.POINTER(P)]
+    lib.ftwa_batch_create_persistent.argtypes = [P, i32, P, P, i64, P, i32, ctypes.POINTER(P)]
     lib.ftwa_batch_launch.argtypes = [P, P]
     lib.ftwa_batch_destroy.argtypes = [P]
     lib.ftwa_batch_destroy.restype = None
@@ -108,7 +110,8 @@ def load(path: str = LIB_PATH):
     lib.ftwa_error_string.restype = ctypes.c_char_p
     lib.ftwa_version.restype = ctypes.c_int
     for name in ("ftwa_plan", "ftwa_get_info", "ftwa_sample", "ftwa_philox", "ftwa_evolve", "ftwa_moments",
-                 "ftwa_moments_noalloc", "ftwa_autotune", "ftwa_batch_create", "ftwa_batch_launch",
+                 "ftwa_moments_noalloc", "ftwa_autotune", "ftwa_batch_create", "ftwa_batch_create_persistent",
+                 "ftwa_batch_launch",
                  "ftwa_adjoint", "ftwa_adjoint_corr", "ftwa_status", "ftwa_debug_force_timeout",
                  "ftwa_debug_tile_check", "ftwa_measure_peak"):
         getattr(lib, name).restype = ctypes.c_int

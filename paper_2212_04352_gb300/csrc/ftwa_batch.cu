@@ -14,12 +14,6 @@
 
 #include "ftwa_internal.h"
 
-struct ftwa_batch {
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    int n = 0;
-};
-
 using namespace ftwa;
 
 extern "C" {
@@ -176,6 +170,7 @@ void ftwa_batch_destroy(ftwa_batch_t *b)
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->d_owned) cudaFree(b->d_owned);
     delete b;
 }
 

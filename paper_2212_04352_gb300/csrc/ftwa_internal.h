@@ -129,3 +129,13 @@ int launch_adjoint(Plan *p, uint64_t seed, int64_t M, int64_t n_steps, int32_t c
 
 // The opaque handle of the C ABI is the plan itself.
 struct ftwa_plan : public ftwa::Plan {};
+
+// A batched launch: one CUDA graph (kernel branches of several plans, or one
+// persistent kernel over a work queue of all plans' samples) and the device
+// memory the batch owns (work queue, tables).
+struct ftwa_batch {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int n = 0;
+    void *d_owned = nullptr;
+};

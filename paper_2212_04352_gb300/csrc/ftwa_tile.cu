@@ -33,6 +33,8 @@
 #include <cstring>
 #include <vector>
 
+#include <new>
+
 #include "ftwa_internal.h"
 #include "ptx.cuh"
 
@@ -51,6 +53,7 @@ struct TileHeader {
     unsigned long long dead_bar;  // never completes (timeout test hook)
     uint32_t tmem_base;
     int abort;
+    int item;                     // batched launch: the cluster's current work item
 };
 
 extern __shared__ __align__(16) unsigned char tile_smem[];
@@ -76,7 +79,7 @@ enum : uint32_t {
 };
 
 struct TileArgs {
-    int N, C, S, nblk, qoff, bw, warps;
+    int N, C, S, nblk, qoff, bw, warps, pm1;
     int slot_bytes, buf_bytes;       // one slot of one stage buffer; one stage buffer
     int k_tiles;                     // tile entries per warp
     float U, dt;
@@ -348,11 +351,153 @@ __device__ __forceinline__ void tile_stage(const TileArgs &a, const TileCtx &c, 
     }
 }
 
+// Per-problem set-up of a CTA: shared-memory offsets of the problem's
+// diagonal table, row table and stage buffers; both stage buffers zeroed
+// (padding slots stay finite) and this rank's row table copied in.  Ends
+// with a CTA barrier.
+template <int WARPS>
+__device__ __forceinline__ void tile_setup(const TileArgs &a, TileCtx &c, int warp)
+{
+    const int twoN = 2 * a.N;
+    const int diag_bytes = 16 * ((4 * 2 * a.S * twoN + 15) / 16);
+    c.diag_off = 64;
+    c.rows_off = 64 + diag_bytes;
+    c.buf0 = 64 + diag_bytes + a.rows_bytes;
+    c.rb0 = a.row_begin[c.rank];
+    c.rb1 = a.row_begin[c.rank + 1];
+    c.tiles = a.tiles + ((size_t)c.rank * WARPS + warp) * a.k_tiles;
+    for (int i = threadIdx.x; i < (2 * a.buf_bytes) / 16; i += blockDim.x)
+        reinterpret_cast<float4 *>(tile_smem + c.buf0)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = threadIdx.x; i < (c.rb1 - c.rb0) * (int)(sizeof(RowEntry) / 16); i += blockDim.x)
+        reinterpret_cast<uint4 *>(tile_smem + c.rows_off)[i] = __ldg(reinterpret_cast<const uint4 *>(a.rows + c.rb0) + i);
+    __syncthreads();
+}
+
+// One batch of S samples: load rho(0), n_steps RK4 steps, write rho(T) back.
+// Starts and ends at a barrier of the cluster (or CTA).
+template <bool PM1, bool CLUSTER, int WARPS>
+__device__ __forceinline__ void tile_batch(const TileArgs &a, const TileCtx &c, int warp, long long b_id)
+{
+    const int N = a.N, S = a.S, twoN = 2 * N, lane = c.lane;
+    // ---- load rho(0): stored elements (upper part and mirror band) of own rows
+    for (int slot = 0; slot < S; ++slot) {
+        const long long m = b_id * S + slot;
+        const int slot_off = slot * a.slot_bytes;
+        for (int sr = c.rb0 + warp; sr < c.rb1; sr += WARPS) {
+            const int s = sr / N, p = sr % N, lo = p > a.bw ? p - a.bw : 0;
+            for (int k = lo + lane; k < N; k += 32) {
+                float2 v = make_float2(0.f, 0.f);
+                if (m < a.M) {
+                    if (k >= p) {
+                        v = a.rho[((m * 2 + s) * N + p) * (long long)N + k];
+                    } else {
+                        v = a.rho[((m * 2 + s) * N + k) * (long long)N + p];
+                        v.y = -v.y;
+                    }
+                }
+                if (k == p) {
+                    v.y = 0.f;
+                    if (a.snap && m < a.M) a.snap[m * twoN + s * N + p] = v.x;
+                    const int di = slot * twoN + s * N + p;   // stage buffer 0
+                    if constexpr (CLUSTER) {
+                        const uint32_t da = c.diag_s + (uint32_t)(4 * di);
+                        for (int r = 0; r < a.C; ++r) {
+                            const uint32_t ra = map_rank(da, (uint32_t)r);
+                            asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(v.x) : "memory");
+                        }
+                    } else {
+                        *reinterpret_cast<float *>(tile_smem + c.diag_off + 4 * di) = v.x;
+                    }
+                }
+                const int off = c.buf0 + slot_off + elem_off(a.zoff[c.rank], s, p, k, a.qoff);
+                *reinterpret_cast<float2 *>(tile_smem + off) = v;
+            }
+        }
+    }
+    // y0 of the computed elements into tensor memory (acc is written at stage 0)
+    {
+        int e = 0;
+        for (int it = 0; it < a.k_tiles; ++it) {
+            const uint2 td = __ldg(&c.tiles[it]);
+            if (td.x == 0xFFFFFFFFu) break;
+            const int p0 = td.x & 511, cnt = (td.x >> 9) & 15, blk = (td.x >> 13) & 7, slot = (td.x >> 16) & 255;
+            const int s = p0 >= N ? 1 : 0;
+            const int q = a.qoff + 32 * blk + lane;
+            const long long m = b_id * S + slot;
+            for (int i = 0; i < cnt; i += 2) {
+                float2 v[2];
+                for (int j = 0; j < 2; ++j) {
+                    const int p = p0 - s * N + i + j;
+                    v[j] = make_float2(0.f, 0.f);
+                    if (i + j < cnt && q >= p && q < N && m < a.M) {
+                        v[j] = a.rho[((m * 2 + s) * N + p) * (long long)N + q];
+                        if (q == p) v[j].y = 0.f;
+                    }
+                }
+                __syncwarp();
+                tm_st4(c.t_state + (uint32_t)(8 * (e + (i >> 1))), v[0], v[1]);
+            }
+            e += (cnt + 1) >> 1;
+        }
+    }
+    tmem_wait_st();
+    stage_sync<CLUSTER>();
+
+    for (long long step = 0; step < a.n_steps; ++step) {
+        const bool snap_now = a.snap && ((step + 1) % a.out_every == 0);
+        const long long snap_row = (step + 1) / a.out_every;
+        tile_stage<0, PM1, CLUSTER>(a, c, b_id, snap_now, snap_row);
+        tmem_wait_st();
+        stage_sync<CLUSTER>();
+        tile_stage<1, PM1, CLUSTER>(a, c, b_id, snap_now, snap_row);
+        tmem_wait_st();
+        stage_sync<CLUSTER>();
+        tile_stage<2, PM1, CLUSTER>(a, c, b_id, snap_now, snap_row);
+        tmem_wait_st();
+        stage_sync<CLUSTER>();
+        tile_stage<3, PM1, CLUSTER>(a, c, b_id, snap_now, snap_row);
+        tmem_wait_st();
+        stage_sync<CLUSTER>();
+    }
+
+    // ---- write back rho(T) (full Hermitian matrix) from the y0 words
+    {
+        int e = 0;
+        for (int it = 0; it < a.k_tiles; ++it) {
+            const uint2 td = __ldg(&c.tiles[it]);
+            if (td.x == 0xFFFFFFFFu) break;
+            const int p0 = td.x & 511, cnt = (td.x >> 9) & 15, blk = (td.x >> 13) & 7, slot = (td.x >> 16) & 255;
+            const int s = p0 >= N ? 1 : 0;
+            const int q = a.qoff + 32 * blk + lane;
+            const long long m = b_id * S + slot;
+            for (int i = 0; i < cnt; i += 2) {
+                uint32_t w[8];
+                __syncwarp();
+                tm_ld8(c.t_state + (uint32_t)(8 * (e + (i >> 1))), w);
+                tm_wait8(w);
+                for (int j = 0; j < 2 && i + j < cnt; ++j) {
+                    const int p = p0 - s * N + i + j;
+                    const float2 y = make_float2(__uint_as_float(w[2 * j]), __uint_as_float(w[2 * j + 1]));
+                    if (q >= p && q < N && m < a.M) {
+                        if (!(isfinite(y.x) && isfinite(y.y))) atomicCAS(a.status, 0, FTWA_ERR_NONFINITE);
+                        a.rho[((m * 2 + s) * N + p) * (long long)N + q] = y;
+                        if (p != q) a.rho[((m * 2 + s) * N + q) * (long long)N + p] = make_float2(y.x, -y.y);
+                    }
+                }
+            }
+            e += (cnt + 1) >> 1;
+        }
+    }
+    __syncwarp();
+    // the next batch overwrites the stage buffers that peers read until here
+    stage_sync<CLUSTER>();
+}
+
 template <bool PM1, bool CLUSTER, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1) tile_stepper(const __grid_constant__ TileArgs a)
 {
+    constexpr int WARPS = THREADS / 32;
     unsigned char *smem = tile_smem;
-    const int N = a.N, S = a.S, C = a.C, twoN = 2 * N;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = CLUSTER ? cluster_ctarank() : 0u;
     const uint32_t cid = CLUSTER ? cluster_id_x() : blockIdx.x;
@@ -360,37 +505,23 @@ __global__ void __launch_bounds__(THREADS, 1) tile_stepper(const __grid_constant
 
     // shared memory: header (64 B) | diagonals [2][S][2N] | row table | stage buffers 0, 1
     TileHeader *h = reinterpret_cast<TileHeader *>(smem);
-    float *diag = reinterpret_cast<float *>(smem + 64);
-    const int diag_bytes = 16 * ((4 * 2 * S * twoN + 15) / 16);
     TileCtx c;
     c.smem_s = smem_addr(smem);
-    c.diag_off = 64;
-    c.rows_off = 64 + diag_bytes;
-    c.buf0 = 64 + diag_bytes + a.rows_bytes;
-    c.diag_s = smem_addr(diag);
+    c.diag_s = smem_addr(smem + 64);
     c.rank = (int)rank;
-    c.rb0 = a.row_begin[rank];
-    c.rb1 = a.row_begin[rank + 1];
+    c.lane = lane;
     c.prev_c = 0;
     c.next_c = 0;
     if constexpr (CLUSTER) {
         if (rank > 0) c.prev_c = map_rank(c.smem_s, rank - 1);
-        if ((int)rank + 1 < C) c.next_c = map_rank(c.smem_s, rank + 1);
+        if ((int)rank + 1 < a.C) c.next_c = map_rank(c.smem_s, rank + 1);
     }
-    constexpr int WARPS = THREADS / 32;
-    c.tiles = a.tiles + ((size_t)rank * WARPS + warp) * a.k_tiles;
-    c.lane = lane;
-
     if (threadIdx.x == 0) {
         h->abort = 0;
         mbar_init(smem_addr(&h->dead_bar), 1u);
         fence_mbar_init_cluster();
     }
-    // both stage buffers start zeroed (padding slots stay finite); this rank's row table
-    for (int i = threadIdx.x; i < (2 * a.buf_bytes) / 16; i += blockDim.x)
-        reinterpret_cast<float4 *>(smem + c.buf0)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int i = threadIdx.x; i < (c.rb1 - c.rb0) * (int)(sizeof(RowEntry) / 16); i += blockDim.x)
-        reinterpret_cast<uint4 *>(smem + c.rows_off)[i] = __ldg(reinterpret_cast<const uint4 *>(a.rows + c.rb0) + i);
+    tile_setup<WARPS>(a, c, warp);
     if (warp == 0) {
         tmem_alloc(smem_addr(&h->tmem_base), kTmemCols);
         tmem_relinquish();
@@ -411,129 +542,83 @@ __global__ void __launch_bounds__(THREADS, 1) tile_stepper(const __grid_constant
         __syncthreads();
     }
 
-    const int rb0 = a.row_begin[rank], rb1 = a.row_begin[rank + 1];
-    const long long n_batches = (a.M + S - 1) / S;
+    const long long n_batches = (a.M + a.S - 1) / a.S;
     const bool run = h->abort == 0;
-    for (long long b_id = cid; run && b_id < n_batches; b_id += ncl) {
-        // ---- load rho(0): stored elements (upper part and mirror band) of own rows
-        for (int slot = 0; slot < S; ++slot) {
-            const long long m = b_id * S + slot;
-            const int slot_off = slot * a.slot_bytes;
-            for (int sr = rb0 + warp; sr < rb1; sr += WARPS) {
-                const int s = sr / N, p = sr % N, lo = p > a.bw ? p - a.bw : 0;
-                for (int k = lo + lane; k < N; k += 32) {
-                    float2 v = make_float2(0.f, 0.f);
-                    if (m < a.M) {
-                        if (k >= p) {
-                            v = a.rho[((m * 2 + s) * N + p) * (long long)N + k];
-                        } else {
-                            v = a.rho[((m * 2 + s) * N + k) * (long long)N + p];
-                            v.y = -v.y;
-                        }
-                    }
-                    if (k == p) {
-                        v.y = 0.f;
-                        if (a.snap && m < a.M) a.snap[m * twoN + s * N + p] = v.x;
-                        const int di = slot * twoN + s * N + p;   // stage buffer 0
-                        if constexpr (CLUSTER) {
-                            const uint32_t da = c.diag_s + (uint32_t)(4 * di);
-                            for (int r = 0; r < C; ++r) {
-                                const uint32_t ra = map_rank(da, (uint32_t)r);
-                                asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(v.x) : "memory");
-                            }
-                        } else {
-                            diag[di] = v.x;
-                        }
-                    }
-                    const int off = c.buf0 + slot_off + elem_off(a.zoff[rank], s, p, k, a.qoff);
-                    *reinterpret_cast<float2 *>(smem + off) = v;
-                }
-            }
-        }
-        // y0 of the computed elements into tensor memory (acc is written at stage 0)
-        {
-            int e = 0;
-            for (int it = 0; it < a.k_tiles; ++it) {
-                const uint2 td = __ldg(&c.tiles[it]);
-                if (td.x == 0xFFFFFFFFu) break;
-                const int p0 = td.x & 511, cnt = (td.x >> 9) & 15, blk = (td.x >> 13) & 7, slot = (td.x >> 16) & 255;
-                const int s = p0 >= N ? 1 : 0;
-                const int q = a.qoff + 32 * blk + lane;
-                const long long m = b_id * S + slot;
-                for (int i = 0; i < cnt; i += 2) {
-                    float2 v[2];
-                    for (int j = 0; j < 2; ++j) {
-                        const int p = p0 - s * N + i + j;
-                        v[j] = make_float2(0.f, 0.f);
-                        if (i + j < cnt && q >= p && q < N && m < a.M) {
-                            v[j] = a.rho[((m * 2 + s) * N + p) * (long long)N + q];
-                            if (q == p) v[j].y = 0.f;
-                        }
-                    }
-                    __syncwarp();
-                    tm_st4(c.t_state + (uint32_t)(8 * (e + (i >> 1))), v[0], v[1]);
-                }
-                e += (cnt + 1) >> 1;
-            }
-        }
-        tmem_wait_st();
-        stage_sync<CLUSTER>();
-
-        for (long long step = 0; step < a.n_steps; ++step) {
-            const bool snap_now = a.snap && ((step + 1) % a.out_every == 0);
-            const long long snap_row = (step + 1) / a.out_every;
-            tile_stage<0, PM1, CLUSTER>(a, c, b_id, snap_now, snap_row);
-            tmem_wait_st();
-            stage_sync<CLUSTER>();
-            tile_stage<1, PM1, CLUSTER>(a, c, b_id, snap_now, snap_row);
-            tmem_wait_st();
-            stage_sync<CLUSTER>();
-            tile_stage<2, PM1, CLUSTER>(a, c, b_id, snap_now, snap_row);
-            tmem_wait_st();
-            stage_sync<CLUSTER>();
-            tile_stage<3, PM1, CLUSTER>(a, c, b_id, snap_now, snap_row);
-            tmem_wait_st();
-            stage_sync<CLUSTER>();
-        }
-
-        // ---- write back rho(T) (full Hermitian matrix) from the y0 words
-        {
-            int e = 0;
-            for (int it = 0; it < a.k_tiles; ++it) {
-                const uint2 td = __ldg(&c.tiles[it]);
-                if (td.x == 0xFFFFFFFFu) break;
-                const int p0 = td.x & 511, cnt = (td.x >> 9) & 15, blk = (td.x >> 13) & 7, slot = (td.x >> 16) & 255;
-                const int s = p0 >= N ? 1 : 0;
-                const int q = a.qoff + 32 * blk + lane;
-                const long long m = b_id * S + slot;
-                for (int i = 0; i < cnt; i += 2) {
-                    uint32_t w[8];
-                    __syncwarp();
-                    tm_ld8(c.t_state + (uint32_t)(8 * (e + (i >> 1))), w);
-                    tm_wait8(w);
-                    for (int j = 0; j < 2 && i + j < cnt; ++j) {
-                        const int p = p0 - s * N + i + j;
-                        const float2 y = make_float2(__uint_as_float(w[2 * j]), __uint_as_float(w[2 * j + 1]));
-                        if (q >= p && q < N && m < a.M) {
-                            if (!(isfinite(y.x) && isfinite(y.y))) atomicCAS(a.status, 0, FTWA_ERR_NONFINITE);
-                            a.rho[((m * 2 + s) * N + p) * (long long)N + q] = y;
-                            if (p != q) a.rho[((m * 2 + s) * N + q) * (long long)N + p] = make_float2(y.x, -y.y);
-                        }
-                    }
-                }
-                e += (cnt + 1) >> 1;
-            }
-        }
-        __syncwarp();
-        // the next batch overwrites the stage buffers that peers read until here
-        stage_sync<CLUSTER>();
-    }
+    for (long long b_id = cid; run && b_id < n_batches; b_id += ncl) tile_batch<PM1, CLUSTER, WARPS>(a, c, warp, b_id);
 
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
     if (warp == 0) tmem_dealloc(h->tmem_base, kTmemCols);
     if constexpr (CLUSTER) cluster_sync_hw();
+}
+
+// Problems of a persistent batched launch (kernel parameter space).
+constexpr int kMaxBatch = 24;
+struct BatchArgs {
+    int n_items, C;
+    const int2 *items;   // [n_items]: (problem, batch of S samples), largest cost first
+    int *counter;        // work-queue head, zeroed before every launch
+    TileArgs prob[kMaxBatch];
+};
+
+// One persistent cluster-launched kernel over a queue of (problem, sample
+// batch) work items of problems of different lattices and U: each cluster
+// takes the next item (its rank 0 draws it and hands it to the cluster's
+// CTAs), sets the problem up when it changes, and integrates the batch.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) tile_batch_stepper(const __grid_constant__ BatchArgs B)
+{
+    constexpr int WARPS = THREADS / 32;
+    unsigned char *smem = tile_smem;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    TileHeader *h = reinterpret_cast<TileHeader *>(smem);
+    TileCtx c;
+    c.smem_s = smem_addr(smem);
+    c.diag_s = smem_addr(smem + 64);
+    c.rank = (int)rank;
+    c.lane = lane;
+    c.prev_c = rank > 0 ? map_rank(c.smem_s, rank - 1) : 0u;
+    c.next_c = (int)rank + 1 < B.C ? map_rank(c.smem_s, rank + 1) : 0u;
+    if (warp == 0) {
+        tmem_alloc(smem_addr(&h->tmem_base), kTmemCols);
+        tmem_relinquish();
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    cluster_sync_hw();
+    c.t_state = h->tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(cols_per_warp(WARPS) * (warp >> 2));
+
+    int cur = -1;
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) {
+            const int it = atomicAdd(B.counter, 1);
+            const uint32_t ia = smem_addr(&h->item);
+            for (int r = 0; r < B.C; ++r) {
+                const uint32_t ra = map_rank(ia, (uint32_t)r);
+                asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(ra), "r"(it) : "memory");
+            }
+        }
+        stage_sync<true>();
+        const int it = *reinterpret_cast<volatile int *>(&h->item);
+        if (it >= B.n_items) break;
+        const int2 w = __ldg(&B.items[it]);
+        const TileArgs &a = B.prob[w.x];
+        if (w.x != cur) {
+            tile_setup<WARPS>(a, c, warp);
+            cur = w.x;
+        }
+        if (a.pm1) tile_batch<true, true, WARPS>(a, c, warp, w.y);
+        else tile_batch<false, true, WARPS>(a, c, warp, w.y);
+    }
+
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (warp == 0) tmem_dealloc(h->tmem_base, kTmemCols);
+    cluster_sync_hw();
 }
 
 // ---------------------------------------------------------------------------
@@ -986,14 +1071,19 @@ static long long check_layout(const Layout &L, const std::vector<Nbr> &nb, char 
 
 // Choose C (1, 2, 4, 8) and S: the smallest cluster that fits, with as many
 // slots as useful for C == 1.
-static bool choose_layout(const Plan *p, int64_t M, const std::vector<Nbr> &nb, bool pm1, Layout &out)
+// C_force / warps_force (0: the plan's overrides or defaults); multi_slot:
+// several samples per cluster also for C > 1 (batched launches).
+static bool choose_layout(const Plan *p, int64_t M, const std::vector<Nbr> &nb, bool pm1, Layout &out,
+                          int C_force = 0, int warps_force = 0, bool multi_slot = false)
 {
     const int sm = p->sm_count > 0 ? p->sm_count : 1;
-    const int warps = p->threads_override == 512 ? 16 : 24;
+    const int warps = warps_force ? warps_force : (p->threads_override == 512 ? 16 : 24);
     for (int C = 1; C <= kMaxCluster; C *= 2) {
-        if (p->cluster_override && C != p->cluster_override) continue;
+        if (C_force && C != C_force) continue;
+        if (!C_force && p->cluster_override && C != p->cluster_override) continue;
         int want = 1;
-        if (C == 1) want = (int)std::max<long long>(1, std::min<long long>((M + sm - 1) / sm, 255));
+        if (C == 1 || multi_slot)
+            want = (int)std::max<long long>(1, std::min<long long>((M + sm / C - 1) / std::max(1, sm / C), 255));
         Layout best;
         bool ok = false;
         for (int S = 1; S <= want; ++S) {
@@ -1008,6 +1098,58 @@ static bool choose_layout(const Plan *p, int64_t M, const std::vector<Nbr> &nb, 
         }
     }
     return false;
+}
+
+// Tables of a layout in one device-ready byte image: rows | tiles | koff | tq
+// (16-byte aligned parts); offsets returned for the argument pointers.
+struct TablePack {
+    std::vector<unsigned char> bytes;
+    size_t o_tiles = 0, o_koff = 0, o_tq = 0;
+};
+static void pack_tables(const Layout &L, TablePack &t)
+{
+    const size_t b_rows = L.rows.size() * sizeof(RowEntry);
+    const size_t b_tiles = ((L.tiles.size() * sizeof(uint2) + 15) / 16) * 16;
+    const size_t b_koff = L.koff.size() * sizeof(int4);
+    const size_t b_tq = ((L.tq.size() * sizeof(float2) + 15) / 16) * 16;
+    t.bytes.assign(b_rows + b_tiles + b_koff + b_tq, 0);
+    t.o_tiles = b_rows;
+    t.o_koff = b_rows + b_tiles;
+    t.o_tq = b_rows + b_tiles + b_koff;
+    std::memcpy(t.bytes.data(), L.rows.data(), b_rows);
+    std::memcpy(t.bytes.data() + t.o_tiles, L.tiles.data(), L.tiles.size() * sizeof(uint2));
+    std::memcpy(t.bytes.data() + t.o_koff, L.koff.data(), b_koff);
+    std::memcpy(t.bytes.data() + t.o_tq, L.tq.data(), L.tq.size() * sizeof(float2));
+}
+
+// Kernel arguments of a layout whose tables are at device address `base`.
+static void fill_args(const Plan *p, const Layout &L, const TablePack &t, const unsigned char *base, TileArgs &a)
+{
+    std::memset(&a, 0, sizeof(a));
+    a.N = L.N;
+    a.C = L.C;
+    a.S = L.S;
+    a.nblk = L.nblk;
+    a.qoff = L.qoff;
+    a.bw = L.bw;
+    a.warps = L.warps;
+    a.pm1 = L.pm1;
+    a.slot_bytes = L.slot_bytes;
+    a.buf_bytes = L.buf_bytes;
+    a.k_tiles = L.k_tiles;
+    a.U = (float)p->U;
+    a.dt = (float)p->dt;
+    a.out_every = p->out_every;
+    a.status = p->d_status;
+    a.timeout_ns = p->timeout_ns;
+    a.force_timeout = p->force_timeout;
+    for (int i = 0; i <= kMaxCluster; ++i) a.row_begin[i] = L.row_begin[std::min(i, L.C)];
+    std::memcpy(a.zoff, L.zoff, sizeof(a.zoff));
+    a.rows = reinterpret_cast<const RowEntry *>(base);
+    a.rows_bytes = L.rows_bytes;
+    a.tiles = reinterpret_cast<const uint2 *>(base + t.o_tiles);
+    a.koff = reinterpret_cast<const int4 *>(base + t.o_koff);
+    a.tq = reinterpret_cast<const float2 *>(base + t.o_tq);
 }
 
 }  // namespace tile
@@ -1061,12 +1203,11 @@ int launch_tile(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cuda
         grid = std::min(grid, n_clusters * L.C);
         cfg.gridDim = dim3(grid, 1, 1);
     }
-    // tables: rows | tiles | koff | tq in one plan-owned device buffer (16-byte aligned parts)
-    const size_t b_rows = L.rows.size() * sizeof(RowEntry);
-    const size_t b_tiles = ((L.tiles.size() * sizeof(uint2) + 15) / 16) * 16;
-    const size_t b_koff = L.koff.size() * sizeof(int4);
-    const size_t b_tq = L.tq.size() * sizeof(float2);
-    const size_t bytes = b_rows + b_tiles + b_koff + b_tq;
+    // tables in one plan-owned device buffer, uploaded when they change (never
+    // during stream capture: batch creation prepares every plan first)
+    TablePack tp;
+    pack_tables(L, tp);
+    const size_t bytes = tp.bytes.size();
     if (p->tile_bytes < bytes) {
         cudaFree(p->d_tile);
         p->d_tile = nullptr;
@@ -1075,15 +1216,8 @@ int launch_tile(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cuda
         if (e != cudaSuccess) return set_cuda_error(e);
         p->tile_bytes = bytes;
     }
-    std::vector<unsigned char> host(bytes, 0);
-    std::memcpy(host.data(), L.rows.data(), b_rows);
-    std::memcpy(host.data() + b_rows, L.tiles.data(), L.tiles.size() * sizeof(uint2));
-    std::memcpy(host.data() + b_rows + b_tiles, L.koff.data(), b_koff);
-    std::memcpy(host.data() + b_rows + b_tiles + b_koff, L.tq.data(), b_tq);
-    if (p->tile_host != host) {
-        // a changed table is uploaded (never during stream capture: batch
-        // creation prepares every plan first)
-        p->tile_host = host;
+    if (p->tile_host != tp.bytes) {
+        p->tile_host = tp.bytes;
         e = cudaMemcpyAsync(p->d_tile, p->tile_host.data(), bytes, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) {
             p->tile_host.clear();
@@ -1102,35 +1236,11 @@ int launch_tile(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cuda
     if (M == 0 || p->dry_run) return FTWA_OK;
 
     TileArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.N = L.N;
-    a.C = L.C;
-    a.S = L.S;
-    a.nblk = L.nblk;
-    a.qoff = L.qoff;
-    a.bw = L.bw;
-    a.warps = L.warps;
-    a.slot_bytes = L.slot_bytes;
-    a.buf_bytes = L.buf_bytes;
-    a.k_tiles = L.k_tiles;
-    a.U = (float)p->U;
-    a.dt = (float)p->dt;
+    fill_args(p, L, tp, static_cast<unsigned char *>(p->d_tile), a);
     a.M = M;
     a.n_steps = n_steps;
-    a.out_every = p->out_every;
     a.rho = reinterpret_cast<float2 *>(rho);
     a.snap = reinterpret_cast<float *>(snap);
-    a.status = p->d_status;
-    a.timeout_ns = p->timeout_ns;
-    a.force_timeout = p->force_timeout;
-    for (int i = 0; i <= kMaxCluster; ++i) a.row_begin[i] = L.row_begin[std::min(i, L.C)];
-    std::memcpy(a.zoff, L.zoff, sizeof(a.zoff));
-    unsigned char *base = static_cast<unsigned char *>(p->d_tile);
-    a.rows = reinterpret_cast<const RowEntry *>(base);
-    a.rows_bytes = L.rows_bytes;
-    a.tiles = reinterpret_cast<const uint2 *>(base + b_rows);
-    a.koff = reinterpret_cast<const int4 *>(base + b_rows + b_tiles);
-    a.tq = reinterpret_cast<const float2 *>(base + b_rows + b_tiles + b_koff);
     e = cudaLaunchKernelEx(&cfg, kern, a);
     return set_cuda_error(e);
 }
@@ -1174,4 +1284,260 @@ extern "C" int ftwa_debug_tile_check(int32_t n_sites, int32_t n_bonds, const int
         *violations += check_layout(L, nb, msg, msg_len);
     }
     return any ? FTWA_OK : FTWA_ERR_UNSUPPORTED;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent batched launch over several plans (lattices of different sizes,
+// several U): one cluster-launched kernel whose clusters draw (problem, sample
+// batch) items from a queue ordered by cost, largest first.
+// ---------------------------------------------------------------------------
+namespace ftwa {
+namespace tile {
+
+struct BatchConfig {
+    int C = 0, warps = 0, smem = 0, grid = 0;
+    std::vector<Layout> L;
+    std::vector<TablePack> tp;
+    std::vector<int2> items;
+};
+
+static bool batch_config(Plan *const *plans, int n, const int64_t *M, const std::vector<std::vector<Nbr>> &nb,
+                         const std::vector<char> &pm1, int C, int warps, BatchConfig &bc)
+{
+    bc = BatchConfig();
+    bc.C = C;
+    bc.warps = warps;
+    bc.L.resize(n);
+    bc.tp.resize(n);
+    std::vector<std::pair<long long, int2>> its;
+    for (int i = 0; i < n; ++i) {
+        if (!choose_layout(plans[i], std::max<int64_t>(M[i], 1), nb[i], pm1[i] != 0, bc.L[i], C, warps, true))
+            return false;
+        bc.smem = std::max(bc.smem, bc.L[i].smem_bytes);
+        pack_tables(bc.L[i], bc.tp[i]);
+        const int S = bc.L[i].S, N = plans[i]->N;
+        const long long batches = (M[i] + S - 1) / S;
+        for (long long j = 0; j < batches; ++j) its.push_back({(long long)S * N * (N + 1), int2{i, (int)j}});
+    }
+    std::stable_sort(its.begin(), its.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    for (auto &x : its) bc.items.push_back(x.second);
+    return bc.smem <= 227 * 1024;
+}
+
+// Upload a configuration (tables, queue, counter) into one device buffer and
+// write the kernel arguments; *mem receives the buffer (owned by the caller).
+static int batch_upload(Plan *const *plans, int n, const BatchConfig &bc, void *const *rho, const int64_t *M,
+                        int64_t n_steps, void *const *snap, BatchArgs &B, void **mem, cudaStream_t s)
+{
+    size_t off = 0;
+    std::vector<size_t> tab_off(n);
+    for (int i = 0; i < n; ++i) {
+        tab_off[i] = off;
+        off += ((bc.tp[i].bytes.size() + 255) / 256) * 256;
+    }
+    const size_t items_off = off;
+    off += ((bc.items.size() * sizeof(int2) + 255) / 256) * 256;
+    const size_t counter_off = off;
+    off += 256;
+    void *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, off);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    unsigned char *base = static_cast<unsigned char *>(d);
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(base + tab_off[i], bc.tp[i].bytes.data(), bc.tp[i].bytes.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !bc.items.empty())
+        e = cudaMemcpyAsync(base + items_off, bc.items.data(), bc.items.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // host images are freed with the configuration
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return set_cuda_error(e);
+    }
+    std::memset(&B, 0, sizeof(B));
+    B.n_items = (int)bc.items.size();
+    B.C = bc.C;
+    B.items = reinterpret_cast<const int2 *>(base + items_off);
+    B.counter = reinterpret_cast<int *>(base + counter_off);
+    for (int i = 0; i < n; ++i) {
+        fill_args(plans[i], bc.L[i], bc.tp[i], base + tab_off[i], B.prob[i]);
+        B.prob[i].M = M[i];
+        B.prob[i].n_steps = n_steps;
+        B.prob[i].rho = reinterpret_cast<float2 *>(rho[i]);
+        B.prob[i].snap = snap ? reinterpret_cast<float *>(snap[i]) : nullptr;
+        B.prob[i].force_timeout = 0;
+    }
+    *mem = d;
+    return FTWA_OK;
+}
+
+static void (*batch_kernel(int warps))(BatchArgs)
+{
+    return warps == 16 ? tile_batch_stepper<512> : tile_batch_stepper<768>;
+}
+
+// launch configuration of a batch (grid: every co-resident cluster)
+static int batch_launch_cfg(const BatchConfig &bc, cudaLaunchConfig_t &cfg, cudaLaunchAttribute *attr,
+                            cudaStream_t s)
+{
+    auto kern = batch_kernel(bc.warps);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bc.smem);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    cfg = cudaLaunchConfig_t{};
+    cfg.blockDim = dim3(32 * bc.warps, 1, 1);
+    cfg.dynamicSmemBytes = bc.smem;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = bc.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(bc.C, 1, 1);
+    int n_clusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&n_clusters, kern, &cfg);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    if (n_clusters < 1) return FTWA_ERR_UNSUPPORTED;
+    cfg.gridDim = dim3(n_clusters * bc.C, 1, 1);
+    return FTWA_OK;
+}
+
+}  // namespace tile
+}  // namespace ftwa
+
+extern "C" int ftwa_batch_create_persistent(ftwa_plan_t *const *plans, int32_t n, void *const *rho_dev,
+                                            const int64_t *M, int64_t n_steps, void *const *snap_dev, int32_t tune,
+                                            ftwa_batch_t **out)
+{
+    using namespace ftwa;
+    using namespace ftwa::tile;
+    if (!out || !plans || !rho_dev || !M || n < 1 || n > kMaxBatch || n_steps < 0) return FTWA_ERR_INVALID_ARGUMENT;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!plans[i] || M[i] < 0 || (M[i] > 0 && !rho_dev[i])) return FTWA_ERR_INVALID_ARGUMENT;
+        if (!tile_supported(plans[i]) || plans[i]->device != plans[0]->device) return FTWA_ERR_UNSUPPORTED;
+    }
+    std::vector<Plan *> P(plans, plans + n);
+    std::vector<std::vector<Nbr>> nb(n);
+    std::vector<char> pm1(n);
+    for (int i = 0; i < n; ++i) {
+        neighbours(P[i], nb[i]);
+        pm1[i] = is_pm1(nb[i]) ? 1 : 0;
+    }
+    // the smallest cluster size every problem fits
+    int C_min = 0;
+    for (int C = 1; C <= kMaxCluster && !C_min; C *= 2) {
+        BatchConfig bc;
+        if (batch_config(P.data(), n, M, nb, pm1, C, 24, bc)) C_min = C;
+    }
+    if (!C_min) return FTWA_ERR_UNSUPPORTED;
+    std::vector<std::pair<int, int>> cands = {{C_min, 24}};
+    if (tune) {
+        cands.push_back({C_min, 16});
+        if (2 * C_min <= kMaxCluster) {
+            cands.push_back({2 * C_min, 24});
+            cands.push_back({2 * C_min, 16});
+        }
+    }
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return FTWA_ERR_CUDA;
+    int rc = FTWA_OK;
+    int best = 0;
+    if (cands.size() > 1) {
+        // autotune: time each candidate on a probe (scratch states of up to 64
+        // batches per problem, a few steps)
+        std::vector<int64_t> Mp(n);
+        std::vector<void *> rp(n, nullptr);
+        float best_ms = -1.f;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (size_t c = 0; c < cands.size() && rc == FTWA_OK; ++c) {
+            BatchConfig bc;
+            if (!batch_config(P.data(), n, M, nb, pm1, cands[c].first, cands[c].second, bc)) continue;
+            for (int i = 0; i < n && rc == FTWA_OK; ++i) {
+                Mp[i] = std::min<int64_t>(M[i], 64LL * bc.L[i].S);
+                cudaFree(rp[i]);
+                rp[i] = nullptr;
+                if (Mp[i] == 0) continue;
+                if (cudaMalloc(&rp[i], (size_t)Mp[i] * 2 * P[i]->N * P[i]->N * 8) != cudaSuccess) rc = FTWA_ERR_OUT_OF_MEMORY;
+                else rc = launch_sample(P[i], 12345, 0, Mp[i], rp[i], s);
+            }
+            if (rc != FTWA_OK) break;
+            BatchConfig bp;
+            if (!batch_config(P.data(), n, Mp.data(), nb, pm1, cands[c].first, cands[c].second, bp)) continue;
+            BatchArgs B;
+            void *mem = nullptr;
+            rc = batch_upload(P.data(), n, bp, rp.data(), Mp.data(), std::min<int64_t>(n_steps, 10), nullptr, B, &mem, s);
+            if (rc != FTWA_OK) break;
+            cudaLaunchConfig_t cfg;
+            cudaLaunchAttribute attr[1];
+            int r2 = batch_launch_cfg(bp, cfg, attr, s);
+            if (r2 == FTWA_OK) {
+                cudaMemsetAsync(B.counter, 0, sizeof(int), s);
+                cudaEventRecord(e0, s);
+                cudaError_t e = cudaLaunchKernelEx(&cfg, batch_kernel(bp.warps), B);
+                cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) rc = set_cuda_error(e);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rc == FTWA_OK && (best_ms < 0.f || ms < best_ms)) {
+                    best_ms = ms;
+                    best = (int)c;
+                }
+            } else if (r2 != FTWA_ERR_UNSUPPORTED) {
+                rc = r2;
+            }
+            cudaFree(mem);
+        }
+        for (int i = 0; i < n; ++i) cudaFree(rp[i]);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    BatchConfig bc;
+    BatchArgs B;
+    void *mem = nullptr;
+    if (rc == FTWA_OK && !batch_config(P.data(), n, M, nb, pm1, cands[best].first, cands[best].second, bc))
+        rc = FTWA_ERR_UNSUPPORTED;
+    if (rc == FTWA_OK) rc = batch_upload(P.data(), n, bc, rho_dev, M, n_steps, snap_dev, B, &mem, s);
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    if (rc == FTWA_OK) rc = batch_launch_cfg(bc, cfg, attr, s);
+    ftwa_batch *b = nullptr;
+    if (rc == FTWA_OK) {
+        b = new (std::nothrow) ftwa_batch();
+        if (!b) rc = FTWA_ERR_OUT_OF_MEMORY;
+    }
+    if (rc == FTWA_OK) {
+        // one graph: zero the queue head, then the persistent kernel
+        b->n = n;
+        b->d_owned = mem;
+        mem = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = cudaMemsetAsync(B.counter, 0, sizeof(int), s);
+            cfg.stream = s;
+            if (e1 == cudaSuccess) e1 = cudaLaunchKernelEx(&cfg, batch_kernel(bc.warps), B);
+            e = cudaStreamEndCapture(s, &b->graph);
+            if (e == cudaSuccess) e = e1;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        if (e != cudaSuccess) rc = set_cuda_error(e);
+        // plan info: the batch's shape
+        for (int i = 0; i < n && rc == FTWA_OK; ++i) {
+            P[i]->shape.cluster = bc.C;
+            P[i]->shape.slots = bc.L[i].S;
+            P[i]->shape.threads = 32 * bc.warps;
+            P[i]->shape.smem_bytes = bc.smem;
+            P[i]->shape.grid = (int)cfg.gridDim.x;
+            P[i]->shape.variant = 3;
+        }
+    }
+    cudaStreamDestroy(s);
+    if (mem) cudaFree(mem);
+    if (rc != FTWA_OK) {
+        if (b) ftwa_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return FTWA_OK;
 }

@@ -60,8 +60,6 @@ def test_tile_layout_every_cluster_size(lib, name):
     fitted = 0
     for cluster in (1, 2, 4, 8):
         for slots in (1, 3):
-            if cluster > 1 and slots > 1:
-                continue
             rc, bad, msg = _check(lib, lat, cluster, slots)
             if rc == L.FTWA_ERR_UNSUPPORTED:
                 continue

@@ -506,7 +506,7 @@ def bench_batched(F, args):
     out = {"workload": f"flakes 24/54/96/150/198 sites x U in {Us}, M={M} each, FP32, {steps} RK4 steps",
            "problems": len(plans), "value": total / (ms / 1000.0), "unit": UNIT, "ms": ms,
            "launch": "one persistent kernel, cost-ordered work queue, CUDA graph",
-           "persistent_shape": {"cluster": pshape["cluster"], "threads": pshape["threads"]},
+           "persistent_shape": {"cluster_of_198_sites": pshape["cluster"], "threads": pshape["threads"]},
            "autotune_s": tune_p, "graph_launches": 1,
            "per_problem_graph": {"value": total / (ms_graph / 1000.0), "ms": ms_graph, "shapes": shapes,
                                  "autotune_s": tune_s},

@@ -158,7 +158,8 @@ struct TileCtx {
     int rb0, rb1;             // this rank's spin-rows
     uint32_t diag_s;
     uint32_t prev_c, next_c;  // shared::cluster address of smem in the previous / next rank
-    int rank;
+    int rank;                 // rank inside the problem's group of a.C CTAs
+    uint32_t rank_base;       // cluster rank of that group's first CTA
     const uint2 *tiles;
     uint32_t t_state;
     int lane;
@@ -325,7 +326,7 @@ __device__ __forceinline__ void tile_rows(const TileArgs &a, const TileCtx &c, u
         if constexpr (CLUSTER) {
             const uint32_t da = c.diag_s + (uint32_t)(4 * di);
             for (int r = 0; r < a.C; ++r) {
-                const uint32_t ra = map_rank(da, (uint32_t)r);
+                const uint32_t ra = map_rank(da, c.rank_base + (uint32_t)r);
                 asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(dnew) : "memory");
             }
         } else {
@@ -402,7 +403,7 @@ __device__ __forceinline__ void tile_batch(const TileArgs &a, const TileCtx &c, 
                     if constexpr (CLUSTER) {
                         const uint32_t da = c.diag_s + (uint32_t)(4 * di);
                         for (int r = 0; r < a.C; ++r) {
-                            const uint32_t ra = map_rank(da, (uint32_t)r);
+                            const uint32_t ra = map_rank(da, c.rank_base + (uint32_t)r);
                             asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(v.x) : "memory");
                         }
                     } else {
@@ -509,6 +510,7 @@ __global__ void __launch_bounds__(THREADS, 1) tile_stepper(const __grid_constant
     c.smem_s = smem_addr(smem);
     c.diag_s = smem_addr(smem + 64);
     c.rank = (int)rank;
+    c.rank_base = 0;
     c.lane = lane;
     c.prev_c = 0;
     c.next_c = 0;
@@ -577,7 +579,6 @@ __global__ void __launch_bounds__(THREADS, 1) tile_batch_stepper(const __grid_co
     TileCtx c;
     c.smem_s = smem_addr(smem);
     c.diag_s = smem_addr(smem + 64);
-    c.rank = (int)rank;
     c.lane = lane;
     c.prev_c = rank > 0 ? map_rank(c.smem_s, rank - 1) : 0u;
     c.next_c = (int)rank + 1 < B.C ? map_rank(c.smem_s, rank + 1) : 0u;
@@ -606,12 +607,23 @@ __global__ void __launch_bounds__(THREADS, 1) tile_batch_stepper(const __grid_co
         if (it >= B.n_items) break;
         const int2 w = __ldg(&B.items[it]);
         const TileArgs &a = B.prob[w.x];
+        // a problem decomposed over a.C CTAs runs B.C / a.C batches of the
+        // item side by side, one per group of a.C CTAs of the cluster
+        const int groups = B.C / a.C;
+        c.rank = (int)rank % a.C;
+        c.rank_base = rank - (uint32_t)c.rank;
+        const long long b_id = (long long)w.y * groups + (int)rank / a.C;
         if (w.x != cur) {
             tile_setup<WARPS>(a, c, warp);
             cur = w.x;
         }
-        if (a.pm1) tile_batch<true, true, WARPS>(a, c, warp, w.y);
-        else tile_batch<false, true, WARPS>(a, c, warp, w.y);
+        if (a.C == 1) {
+            if (a.pm1) tile_batch<true, false, WARPS>(a, c, warp, b_id);
+            else tile_batch<false, false, WARPS>(a, c, warp, b_id);
+        } else {
+            if (a.pm1) tile_batch<true, true, WARPS>(a, c, warp, b_id);
+            else tile_batch<false, true, WARPS>(a, c, warp, b_id);
+        }
     }
 
     tmem_fence_before();
@@ -1311,13 +1323,18 @@ static bool batch_config(Plan *const *plans, int n, const int64_t *M, const std:
     bc.tp.resize(n);
     std::vector<std::pair<long long, int2>> its;
     for (int i = 0; i < n; ++i) {
-        if (!choose_layout(plans[i], std::max<int64_t>(M[i], 1), nb[i], pm1[i] != 0, bc.L[i], C, warps, true))
-            return false;
+        // the smallest group of CTAs (a divisor of C) the problem fits on; the
+        // cluster's C / Ci groups then integrate batches of it side by side
+        bool ok = false;
+        for (int Ci = 1; Ci <= C && !ok; Ci *= 2)
+            ok = choose_layout(plans[i], std::max<int64_t>(M[i], 1), nb[i], pm1[i] != 0, bc.L[i], Ci, warps, true);
+        if (!ok) return false;
         bc.smem = std::max(bc.smem, bc.L[i].smem_bytes);
         pack_tables(bc.L[i], bc.tp[i]);
-        const int S = bc.L[i].S, N = plans[i]->N;
+        const int S = bc.L[i].S, N = plans[i]->N, Ci = bc.L[i].C, groups = C / Ci;
         const long long batches = (M[i] + S - 1) / S;
-        for (long long j = 0; j < batches; ++j) its.push_back({(long long)S * N * (N + 1), int2{i, (int)j}});
+        const long long items = (batches + groups - 1) / groups;
+        for (long long j = 0; j < items; ++j) its.push_back({(long long)S * N * (N + 1) / Ci, int2{i, (int)j}});
     }
     std::stable_sort(its.begin(), its.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
     for (auto &x : its) bc.items.push_back(x.second);
@@ -1524,7 +1541,7 @@ extern "C" int ftwa_batch_create_persistent(ftwa_plan_t *const *plans, int32_t n
         if (e != cudaSuccess) rc = set_cuda_error(e);
         // plan info: the batch's shape
         for (int i = 0; i < n && rc == FTWA_OK; ++i) {
-            P[i]->shape.cluster = bc.C;
+            P[i]->shape.cluster = bc.L[i].C;
             P[i]->shape.slots = bc.L[i].S;
             P[i]->shape.threads = 32 * bc.warps;
             P[i]->shape.smem_bytes = bc.smem;

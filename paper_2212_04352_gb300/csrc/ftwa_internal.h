@@ -73,6 +73,9 @@ struct Plan {
     void *d_tile = nullptr;           // tiled stepper tables (tiles, row-part offsets, hoppings)
     size_t tile_bytes = 0;
     std::vector<unsigned char> tile_host;   // copy of the tables last uploaded
+    std::vector<int> tile_rp_k;             // tiled stepper: row-part slot columns (lattice only;
+    std::vector<char> tile_rp_real;         //   searched once, empty until the first use)
+    std::vector<float> tile_rp_t;
     uint32_t *d_items = nullptr;      // banded stepper work items
     size_t items_bytes = 0;
     std::vector<uint32_t> items_host; // copy of the table last uploaded

@@ -5,10 +5,14 @@
 // accumulator in tensor memory; a thread-block cluster per sample for large
 // lattices), with a layout chosen so that the inner loop is almost free of
 // integer work:
-//  - Shared memory is block-major: for each 32-column block b and spin s, the
-//    rows of this rank are stored at a fixed stride of 256 B (one complex
-//    FP32 value per lane), element (s, p, q) at Z(s, b) + 256 p + 8 lane(q).
-//    Row offsets inside a tile are therefore immediates of the load.
+//  - Shared memory is block-major: for each 31-column block b and spin s, the
+//    rows of this rank are stored at a fixed stride of 248 B (one complex
+//    FP32 value per lane, lanes 0..30; lane 31 idles), element (s, p, q) at
+//    Z(s, b) + 248 p + 8 lane(q).  Row offsets inside a tile are therefore
+//    immediates of the load, and since 248 B is 31 bank pairs, the elements
+//    of one column in 16 consecutive rows (the mirror-band stores of a row)
+//    fall in 16 distinct bank pairs.  Regions, slots and stage buffers start
+//    on 128-byte boundaries, so a row's bank pattern is the lane's.
 //  - Each row stores the upper triangle plus a mirror band of bw entries
 //    below the diagonal (bw = lattice bandwidth), as in the banded stepper,
 //    so every read of Eq. 6 is a direct load.  Empty neighbour slots read
@@ -17,7 +21,7 @@
 //    A lane owns column q of the tile; the row-part gathers rho_pk,
 //    k in nb(q), are at fixed byte offsets from the lane's own element for
 //    every row of the rank (one table entry per block and lane), and the
-//    column-part reads rho_kq, k in nb(p), at per-row offsets (k - p) 256
+//    column-part reads rho_kq, k in nb(p), at per-row offsets (k - p) 248
 //    held with the row's hoppings in a per-rank table in shared memory.
 //  - On lattices whose site order has every site's neighbours among p - 1,
 //    p + 1 and at most one other site (honeycomb flakes numbered along
@@ -29,6 +33,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -46,8 +51,11 @@ constexpr int kMaxWarpsT = 24;            // warps per CTA: 16 (512 threads) or 
 // tensor-memory columns per warp: warps w, w + 4, ... share lane quadrant w % 4
 // and split the 512 columns (multiples of 8 for the 8-column row-pair blocks)
 __host__ __device__ constexpr int cols_per_warp(int warps) { return (512 / (warps / 4)) / 8 * 8; }
-constexpr int kMaxBlk = (FTWA_MAX_SITES + 31) / 32;
-constexpr int kRowBytes = 256;            // one row of a 32-column block
+constexpr int kW = 31;                    // columns per block (lanes 0..30; lane 31 idle)
+constexpr int kMaxBlk = (FTWA_MAX_SITES + kW - 1) / kW;
+constexpr int kRowBytes = 8 * kW;         // one row of a block: 248 B, so consecutive rows of a
+                                          // column fall in distinct bank pairs
+constexpr int kIdleQ = -(1 << 20);        // column of the idle lane: fails every element predicate
 
 struct TileHeader {
     unsigned long long dead_bar;  // never completes (timeout test hook)
@@ -63,11 +71,22 @@ extern __shared__ __align__(16) unsigned char tile_smem[];
 struct __align__(16) RowEntry {
     float mt[3];      // -t_pk of the three column-part slots (0: empty slot)
     uint32_t flags;   // bit n: slot n is in another rank; bit 3 + n: that rank is the next one
-    int32_t dcol[3];  // local slot: (k - p) * 256 (0 for an empty slot); remote slot: k * 256
-    int32_t mir;      // Z(s, blk(p)) + 8 lane(p): element (q, p) is at mir + 256 q
+    int32_t dcol[3];  // local slot: (k - p) * 248 (0 for an empty slot); remote slot: k * 248
+    int32_t mir;      // Z(s, blk(p)) + 8 lane(p): element (q, p) is at mir + 248 q
 };
 
-// Tile descriptor: x = p0 | cnt << 9 | b << 13 | slot << 16 (p0 a spin-row);
+// Lattices with carried rows p -+ 1: the same 32 bytes per spin-row, with the
+// hoppings as (h, h) pairs for packed FMAs.
+struct __align__(16) RowPm1 {
+    float m0[2];      // -t of row p - 1 (0: absent)
+    float m1[2];      // -t of row p + 1
+    float m2[2];      // -t of the far neighbour k (0: none)
+    int32_t far;      // local: (k - p) * 248; another rank: k * 248 | 1, | 2 when it is the next rank
+    int32_t mir;      // as RowEntry::mir
+};
+static_assert(sizeof(RowPm1) == sizeof(RowEntry), "row tables share one slot size");
+
+// Tile descriptor: x = p0 | cnt << 9 | b << 13 | slot << 17 (p0 a spin-row);
 // y = flags below.
 enum : uint32_t {
     kDiag = 1u,        // a row's diagonal element lies in the tile
@@ -76,6 +95,9 @@ enum : uint32_t {
     kNextShift = 5,    // 2 bits: row p0 + cnt is 0 local, 1 absent (zero hopping), 2 in the next rank
     kRemote = 128u,    // some row of the tile reads a column-part slot of another rank
     kRemoteMir = 256u, // some mirror-band row of the tile may belong to the next rank
+    kFull = 512u,      // carried-row lattice, kR rows, no kRemoteMir, far slots of at most one
+                       // other rank: the unrolled path
+    kFarNext = 1024u,  // kFull tile whose remote far slots are in the next rank
 };
 
 struct TileArgs {
@@ -100,8 +122,16 @@ struct TileArgs {
 };
 
 // ---- address arithmetic shared by the kernel and the host layout check --------
-__host__ __device__ __forceinline__ int blk_of(int q, int qoff) { return (q - qoff) >> 5; }
-__host__ __device__ __forceinline__ int lane_of(int q, int qoff) { return (q - qoff) & 31; }
+__host__ __device__ __forceinline__ int blk_of(int q, int qoff) { return (q - qoff) / kW; }
+__host__ __device__ __forceinline__ int lane_of(int q, int qoff) { return (q - qoff) % kW; }
+__host__ __device__ __forceinline__ int td_p0(uint32_t x) { return x & 511; }
+__host__ __device__ __forceinline__ int td_cnt(uint32_t x) { return (x >> 9) & 15; }
+__host__ __device__ __forceinline__ int td_blk(uint32_t x) { return (x >> 13) & 15; }
+__host__ __device__ __forceinline__ int td_slot(uint32_t x) { return (x >> 17) & 255; }
+__host__ __device__ __forceinline__ uint32_t td_make(int p0, int cnt, int b, int slot)
+{
+    return (uint32_t)p0 | ((uint32_t)cnt << 9) | ((uint32_t)b << 13) | ((uint32_t)slot << 17);
+}
 // byte offset (inside a slot) of element (s, p, q) in a rank whose origins are z
 __host__ __device__ __forceinline__ int elem_off(const int (*z)[kMaxBlk], int s, int p, int q, int qoff)
 {
@@ -139,6 +169,13 @@ __device__ __forceinline__ void tm_st4(uint32_t ta, float2 a, float2 b)
                  "r"(__float_as_uint(a.x)), "r"(__float_as_uint(a.y)), "r"(__float_as_uint(b.x)),
                  "r"(__float_as_uint(b.y)));
 }
+// y0 of a row pair and a zeroed accumulator (all 8 words)
+__device__ __forceinline__ void tm_st8z(uint32_t ta, float2 a, float2 b)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(ta),
+                 "r"(__float_as_uint(a.x)), "r"(__float_as_uint(a.y)), "r"(__float_as_uint(b.x)),
+                 "r"(__float_as_uint(b.y)), "r"(0u), "r"(0u), "r"(0u), "r"(0u));
+}
 
 template <bool CLUSTER>
 __device__ __forceinline__ void stage_sync()
@@ -165,44 +202,94 @@ struct TileCtx {
     int lane;
 };
 
-// One RK4 stage over the rows of one tile.  Stage buffer CUR = STAGE & 1
-// holds the stage state; the next stage state goes to the other buffer.
-// Everything that depends only on the lane (column) or only on the tile is
-// formed once per tile; the rare cases (the diagonal, the mirror band, rows
-// of another rank) are warp-uniform branches or per-lane predicates on
-// values formed per tile.
-template <int STAGE, bool PM1, bool CLUSTER>
-__device__ __forceinline__ void tile_rows(const TileArgs &a, const TileCtx &c, uint2 td, int e_base, long long b_id,
-                                          bool snap_now, long long snap_row)
+// The lanes holding a row's diagonal publish its new value to every rank's
+// diagonal table (and, after the final stage, to the snapshot).
+template <bool FINAL, bool CLUSTER>
+__device__ __forceinline__ void publish_diag(const TileArgs &a, const TileCtx &c, bool mine, int cur, int slot, int s,
+                                             int q, float dnew, long long b_id, bool snap_now, long long snap_row)
 {
-    constexpr int CUR = STAGE & 1;
+    if (!mine) return;
+    const int twoN = 2 * a.N;
+    const int di = ((cur ^ 1) * a.S + slot) * twoN + s * a.N + q;
+    if constexpr (CLUSTER) {
+        const uint32_t da = c.diag_s + (uint32_t)(4 * di);
+        for (int r = 0; r < a.C; ++r) {
+            const uint32_t ra = map_rank(da, c.rank_base + (uint32_t)r);
+            asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(dnew) : "memory");
+        }
+    } else {
+        *reinterpret_cast<float *>(tile_smem + c.diag_off + 4 * di) = dnew;
+    }
+    if (FINAL && snap_now) {
+        const long long m = b_id * a.S + slot;
+        if (m < a.M) a.snap[(snap_row * a.M + m) * twoN + s * a.N + q] = dnew;
+    }
+}
+
+// One RK4 stage over the rows of one tile.  Stage buffer sc.cur holds the
+// stage state; the next stage state goes to the other buffer.  Stages 0-2
+// share one code path: the stage accumulator starts each step at zero (the
+// final stage stores zeros), acc += b k and the next stage state is
+// y0 + cc k, with (b, cc) = (1, dt/2), (2, dt/2), (2, dt); the final stage
+// forms y0 + dt/6 (acc + k).  Everything that depends only on the lane
+// (column) or only on the tile is formed once per tile; the rare cases (the
+// diagonal, the mirror band, rows of another rank) are warp-uniform branches
+// or per-lane predicates on values formed per tile.
+struct StageC {
+    int cur;     // stage buffer holding the stage state
+    float b;     // weight of k in the accumulator
+    float cc;    // next stage state: y0 + cc k
+};
+
+__device__ __forceinline__ float4 lds128(int off) { return *reinterpret_cast<const float4 *>(tile_smem + off); }
+
+// far column-part value: a shared-memory load of this CTA or, where `rem` is
+// set, a distributed shared-memory load of a peer (both predicated, no branch)
+__device__ __forceinline__ float2 ld_far(uint32_t local_addr, uint32_t remote_addr, uint32_t rem)
+{
+    float2 v;
+    asm volatile(
+        "{\n\t.reg .pred pr;\n\tsetp.ne.u32 pr, %3, 0;\n\t"
+        "@pr ld.shared::cluster.v2.f32 {%0, %1}, [%4];\n\t"
+        "@!pr ld.shared.v2.f32 {%0, %1}, [%2];\n\t}"
+        : "=f"(v.x), "=f"(v.y)
+        : "r"(local_addr), "r"(rem), "r"(remote_addr));
+    return v;
+}
+
+template <bool FINAL, bool PM1, bool CLUSTER>
+__device__ __forceinline__ void tile_rows(const TileArgs &a, const TileCtx &c, const StageC &sc, uint2 td, int e_base,
+                                          long long b_id, bool snap_now, long long snap_row)
+{
+    const int cur = FINAL ? 1 : sc.cur;
     const int N = a.N, twoN = 2 * N, lane = c.lane;
-    const int p0 = td.x & 511, cnt = (td.x >> 9) & 15, blk = (td.x >> 13) & 7, slot = (td.x >> 16) & 255;
+    const int p0 = td_p0(td.x), cnt = td_cnt(td.x), blk = td_blk(td.x), slot = td_slot(td.x);
     const bool diag_t = (td.y & kDiag) != 0, band_t = (td.y & kBand) != 0, rmir_t = (td.y & kRemoteMir) != 0;
     const int s = p0 >= N ? 1 : 0;
     const int pp0 = p0 - s * N;                       // site index of row 0 of the tile
-    const int c0 = a.qoff + 32 * blk;
-    const int q = c0 + lane;
+    const int la = lane < kW ? lane : kW - 1;           // the idle lane shadows lane 30's addresses
+    const int c0 = a.qoff + kW * blk;
+    const int q = lane < kW ? c0 + lane : kIdleQ;
     const int qc = q < 0 ? 0 : q;
     const int slot_off = slot * a.slot_bytes;
-    const int cur_off = c.buf0 + CUR * a.buf_bytes + slot_off;
-    const int dnext = (CUR ? -1 : 1) * a.buf_bytes;   // next stage buffer minus this one
-    const int own0 = cur_off + a.zoff[c.rank][s][blk] + kRowBytes * pp0 + 8 * lane;   // element (p0, q)
+    const int cur_off = c.buf0 + cur * a.buf_bytes + slot_off;
+    const int dnext = (cur ? -1 : 1) * a.buf_bytes;   // next stage buffer minus this one
+    const int own0 = cur_off + a.zoff[c.rank][s][blk] + kRowBytes * pp0 + 8 * la;   // element (p0, q)
     const int4 ko = __ldg(&a.koff[(c.rank * a.nblk + blk) * 32 + lane]);
     const float2 *tqp = a.tq + (blk * 32 + lane) * 3;
     const float2 tq0 = __ldg(tqp), tq1 = __ldg(tqp + 1), tq2 = __ldg(tqp + 2);
-    const int dg_off = c.diag_off + 4 * ((CUR * a.S + slot) * twoN + (1 - s) * N);   // other spin's diagonal
+    const int dg_off = c.diag_off + 4 * ((cur * a.S + slot) * twoN + (1 - s) * N);   // other spin's diagonal
     auto lds = [&](int off) -> float2 { return *reinterpret_cast<const float2 *>(tile_smem + off); };
     auto ldf = [&](int off) -> float { return *reinterpret_cast<const float *>(tile_smem + off); };
     auto sts = [&](int off, float2 v) { *reinterpret_cast<float2 *>(tile_smem + off) = v; };
     const float uq = a.U * ldf(dg_off + 4 * qc);
-    const float hdt = a.dt * 0.5f, sdt = a.dt * (1.0f / 6.0f);
+    const float sdt = a.dt * (1.0f / 6.0f);
     const int rt0 = c.rows_off + (int)sizeof(RowEntry) * (p0 - c.rb0);
     // cluster-space addresses of (row 0, column q) in the previous / next rank's current buffer
     uint32_t base_prev = 0, base_next = 0;
     if constexpr (CLUSTER) {
-        if (c.rank > 0) base_prev = c.prev_c + (uint32_t)(cur_off + a.zoff[c.rank - 1][s][blk] + 8 * lane);
-        if (c.rank + 1 < a.C) base_next = c.next_c + (uint32_t)(cur_off + a.zoff[c.rank + 1][s][blk] + 8 * lane);
+        if (c.rank > 0) base_prev = c.prev_c + (uint32_t)(cur_off + a.zoff[c.rank - 1][s][blk] + 8 * la);
+        if (c.rank + 1 < a.C) base_next = c.next_c + (uint32_t)(cur_off + a.zoff[c.rank + 1][s][blk] + 8 * la);
     }
     // mirror band: row q of this rank, or of the next one
     const bool mir_local = s * N + q < c.rb1;
@@ -223,31 +310,34 @@ __device__ __forceinline__ void tile_rows(const TileArgs &a, const TileCtx &c, u
     auto row = [&](int i, float2 &y0, float2 &acc) {
         const int p = pp0 + i;
         const int own = own0 + kRowBytes * i;
-        const RowEntry re = *reinterpret_cast<const RowEntry *>(tile_smem + rt0 + (int)sizeof(RowEntry) * i);
         float2 ov;
         float2 h = make_float2(0.f, 0.f);
+        int mir;
         // + sum_{k in nb(q)} t_qk rho_pk (row p)
         h = ffma2(tq0, lds(own + ko.x), h);
         h = ffma2(tq1, lds(own + ko.y), h);
         h = ffma2(tq2, lds(own + ko.z), h);
         // - sum_{k in nb(p)} t_pk rho_kq (column q)
         if constexpr (PM1) {
+            const float4 m01 = lds128(rt0 + (int)sizeof(RowPm1) * i);
+            const float4 m2f = lds128(rt0 + (int)sizeof(RowPm1) * i + 16);
+            const int far = __float_as_int(m2f.z);
+            mir = __float_as_int(m2f.w);
             ov = vcur;
             const bool in_tile = i + 1 < cnt;
             const float2 vn = lds(in_tile ? own + kRowBytes : own);
             const float2 vnext = in_tile ? vn : vlast;
             float2 vf;
-            if (CLUSTER && (re.flags & 4u)) vf = ld_cluster(((re.flags & 32u) ? base_next : base_prev) + (uint32_t)re.dcol[2]);
-            else vf = lds(own + re.dcol[2]);
-            h.x = fmaf(re.mt[0], vprev.x, h.x);
-            h.y = fmaf(re.mt[0], vprev.y, h.y);
-            h.x = fmaf(re.mt[1], vnext.x, h.x);
-            h.y = fmaf(re.mt[1], vnext.y, h.y);
-            h.x = fmaf(re.mt[2], vf.x, h.x);
-            h.y = fmaf(re.mt[2], vf.y, h.y);
+            if (CLUSTER && (far & 1)) vf = ld_cluster(((far & 2) ? base_next : base_prev) + (uint32_t)(far & ~3));
+            else vf = lds(own + far);
+            h = ffma2(make_float2(m01.x, m01.y), vprev, h);
+            h = ffma2(make_float2(m01.z, m01.w), vnext, h);
+            h = ffma2(make_float2(m2f.x, m2f.y), vf, h);
             vprev = vcur;
             vcur = vnext;
         } else {
+            const RowEntry re = *reinterpret_cast<const RowEntry *>(tile_smem + rt0 + (int)sizeof(RowEntry) * i);
+            mir = re.mir;
             ov = lds(own);
 #pragma unroll
             for (int n = 0; n < 3; ++n) {
@@ -268,17 +358,11 @@ __device__ __forceinline__ void tile_rows(const TileArgs &a, const TileCtx &c, u
         const float kx = -h.y;
         const float ky = q == p ? 0.f : h.x;
         float2 nx;
-        if constexpr (STAGE == 0) {
-            acc.x = kx;
-            acc.y = ky;
-            nx.x = fmaf(hdt, kx, y0.x);
-            nx.y = fmaf(hdt, ky, y0.y);
-        } else if constexpr (STAGE < 3) {
-            acc.x = fmaf(2.f, kx, acc.x);
-            acc.y = fmaf(2.f, ky, acc.y);
-            const float cc = STAGE == 1 ? hdt : a.dt;
-            nx.x = fmaf(cc, kx, y0.x);
-            nx.y = fmaf(cc, ky, y0.y);
+        if constexpr (!FINAL) {
+            acc.x = fmaf(sc.b, kx, acc.x);
+            acc.y = fmaf(sc.b, ky, acc.y);
+            nx.x = fmaf(sc.cc, kx, y0.x);
+            nx.y = fmaf(sc.cc, ky, y0.y);
         } else {
             nx.x = fmaf(sdt, acc.x + kx, y0.x);
             nx.y = fmaf(sdt, acc.y + ky, y0.y);
@@ -291,13 +375,13 @@ __device__ __forceinline__ void tile_rows(const TileArgs &a, const TileCtx &c, u
             const bool mb = (unsigned)(q - p - 1) < (unsigned)a.bw;
             const float2 cj = make_float2(nx.x, -nx.y);
             if (!rmir_t) {
-                if (mb) sts(re.mir + mir_lane, cj);
+                if (mb) sts(mir + mir_lane, cj);
             } else if (mb) {
                 if (mir_local) {
-                    sts(re.mir + mir_lane, cj);
+                    sts(mir + mir_lane, cj);
                 } else {
                     const int bp = blk_of(p, a.qoff);
-                    const int mn = re.mir - a.zoff[c.rank][s][bp] + a.zoff[c.rank + 1][s][bp];
+                    const int mn = mir - a.zoff[c.rank][s][bp] + a.zoff[c.rank + 1][s][bp];
                     st_cluster(c.next_c + (uint32_t)(mn + mir_lane), cj);
                 }
             }
@@ -315,40 +399,148 @@ __device__ __forceinline__ void tile_rows(const TileArgs &a, const TileCtx &c, u
         row(i, y0a, acca);
         if (i + 1 < cnt) row(i + 1, y0b, accb);
         const uint32_t ta = c.t_state + (uint32_t)(8 * (e_base + (i >> 1)));
-        if constexpr (STAGE < 3) tm_st4(ta + 4, acca, accb);
-        else tm_st4(ta, y0a, y0b);
+        if constexpr (!FINAL) tm_st4(ta + 4, acca, accb);
+        else tm_st8z(ta, y0a, y0b);
         if (i + 2 < cnt) tm_ld8(ta + 8, w);
     }
-    if (diag_t && q >= pp0 && q < pp0 + cnt) {
-        // the lanes holding a row's diagonal publish its new value to every
-        // rank's diagonal table, and to the snapshot
-        const int di = ((CUR ^ 1) * a.S + slot) * twoN + s * N + q;
-        if constexpr (CLUSTER) {
-            const uint32_t da = c.diag_s + (uint32_t)(4 * di);
-            for (int r = 0; r < a.C; ++r) {
-                const uint32_t ra = map_rank(da, c.rank_base + (uint32_t)r);
-                asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(dnew) : "memory");
-            }
-        } else {
-            *reinterpret_cast<float *>(tile_smem + c.diag_off + 4 * di) = dnew;
-        }
-        if (STAGE == 3 && snap_now) {
-            const long long m = b_id * a.S + slot;
-            if (m < a.M) a.snap[(snap_row * a.M + m) * twoN + s * N + q] = dnew;
-        }
-    }
+    publish_diag<FINAL, CLUSTER>(a, c, diag_t && q >= pp0 && q < pp0 + cnt, cur, slot, s, q, dnew, b_id, snap_now,
+                                 snap_row);
 }
 
-template <int STAGE, bool PM1, bool CLUSTER>
-__device__ __forceinline__ void tile_stage(const TileArgs &a, const TileCtx &c, long long b_id, bool snap_now,
-                                        long long snap_row)
+// Full tiles of lattices with carried rows p -+ 1 (kR = 8 rows, no mirror
+// row in another rank): the row loop unrolled, every row offset an immediate
+// of its load, no per-row branch.  REMOTE: the far column-part slot of some
+// row is in another rank (a predicated pair of loads per row).
+template <bool FINAL, bool CLUSTER, bool REMOTE>
+__device__ __forceinline__ void tile_rows8(const TileArgs &a, const TileCtx &c, const StageC &sc, uint2 td, int e_base,
+                                           long long b_id, bool snap_now, long long snap_row)
+{
+    const int cur = FINAL ? 1 : sc.cur;
+    const int N = a.N, twoN = 2 * N, lane = c.lane;
+    const int p0 = td_p0(td.x), blk = td_blk(td.x), slot = td_slot(td.x);
+    const bool diag_t = (td.y & kDiag) != 0, band_t = (td.y & kBand) != 0;
+    const int s = p0 >= N ? 1 : 0;
+    const int pp0 = p0 - s * N;
+    const int la = lane < kW ? lane : kW - 1;
+    const int q = lane < kW ? a.qoff + kW * blk + lane : kIdleQ;
+    const int qi = q - pp0;                           // tile row holding this lane's diagonal
+    const int qc = q < 0 ? 0 : q;
+    const int cur_off = c.buf0 + cur * a.buf_bytes + slot * a.slot_bytes;
+    const int dnext = (cur ? -1 : 1) * a.buf_bytes;
+    const int own0 = cur_off + a.zoff[c.rank][s][blk] + kRowBytes * pp0 + 8 * la;
+    const int4 ko = __ldg(&a.koff[(c.rank * a.nblk + blk) * 32 + lane]);
+    const float2 *tqp = a.tq + (blk * 32 + lane) * 3;
+    const float2 tq0 = __ldg(tqp), tq1 = __ldg(tqp + 1), tq2 = __ldg(tqp + 2);
+    const int dg = c.diag_off + 4 * ((cur * a.S + slot) * twoN + (1 - s) * N);
+    auto lds = [&](int off) -> float2 { return *reinterpret_cast<const float2 *>(tile_smem + off); };
+    auto ldf = [&](int off) -> float { return *reinterpret_cast<const float *>(tile_smem + off); };
+    auto sts = [&](int off, float2 v) { *reinterpret_cast<float2 *>(tile_smem + off) = v; };
+    const float uq = a.U * ldf(dg + 4 * qc);
+    const int dg0 = dg + 4 * pp0;
+    const float sdt = a.dt * (1.0f / 6.0f);
+    const int rt0 = c.rows_off + (int)sizeof(RowPm1) * (p0 - c.rb0);
+    const int mir_lane = kRowBytes * q + cur_off + dnext;
+    const int r0 = own0 + ko.x, r1 = own0 + ko.y, r2 = own0 + ko.z;
+    uint32_t base_far = 0;   // (row 0, column q) in the rank holding the tile's remote far slots
+    float2 vprev, vlast;
+    {
+        uint32_t base_prev = 0, base_next = 0;
+        if constexpr (CLUSTER) {
+            if (c.rank > 0) base_prev = c.prev_c + (uint32_t)(cur_off + a.zoff[c.rank - 1][s][blk] + 8 * la);
+            if (c.rank + 1 < a.C) base_next = c.next_c + (uint32_t)(cur_off + a.zoff[c.rank + 1][s][blk] + 8 * la);
+        }
+        base_far = (td.y & kFarNext) ? base_next : base_prev;
+        const uint32_t pk = (td.y >> kPrevShift) & 3, nk = (td.y >> kNextShift) & 3;
+        if (CLUSTER && pk == 2) vprev = ld_cluster(base_prev + (uint32_t)(kRowBytes * (pp0 - 1)));
+        else vprev = lds(pk == 0 ? own0 - kRowBytes : own0);
+        if (CLUSTER && nk == 2) vlast = ld_cluster(base_next + (uint32_t)(kRowBytes * (pp0 + kR)));
+        else vlast = lds(nk == 0 ? own0 + kRowBytes * kR : own0);
+    }
+    float2 vcur = lds(own0);
+    float dnew = 0.f;
+    const uint32_t t0 = c.t_state + (uint32_t)(8 * e_base);
+    const uint32_t own0_s = c.smem_s + (uint32_t)own0;
+
+    // row pairs: unrolled, except in tiles with remote far slots (register
+    // budget at 768 threads)
+#pragma unroll(REMOTE ? 1 : kR / 2)
+    for (int j = 0; j < kR / 2; ++j) {
+        uint32_t w[8];
+        tm_ld8(t0 + 8 * j, w);
+        tm_wait8(w);
+        float2 y0[2] = {make_float2(__uint_as_float(w[0]), __uint_as_float(w[1])),
+                        make_float2(__uint_as_float(w[2]), __uint_as_float(w[3]))};
+        float2 acc[2] = {make_float2(__uint_as_float(w[4]), __uint_as_float(w[5])),
+                         make_float2(__uint_as_float(w[6]), __uint_as_float(w[7]))};
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int i = 2 * j + u;
+            const int own = own0 + kRowBytes * i;
+            const float4 m01 = lds128(rt0 + (int)sizeof(RowPm1) * i);
+            const float4 m2f = lds128(rt0 + (int)sizeof(RowPm1) * i + 16);
+            const int far = __float_as_int(m2f.z);
+            float2 h = make_float2(0.f, 0.f);
+            h = ffma2(tq0, lds(r0 + kRowBytes * i), h);
+            h = ffma2(tq1, lds(r1 + kRowBytes * i), h);
+            h = ffma2(tq2, lds(r2 + kRowBytes * i), h);
+            const float2 vnext = i + 1 < kR ? lds(own + kRowBytes) : vlast;
+            float2 vf;
+            if constexpr (REMOTE && CLUSTER) {
+                const uint32_t ra = base_far + (uint32_t)(far & ~3);
+                vf = ld_far(own0_s + (uint32_t)(kRowBytes * i + far), ra, (uint32_t)(far & 1));
+            } else {
+                vf = lds(own + far);
+            }
+            h = ffma2(make_float2(m01.x, m01.y), vprev, h);
+            h = ffma2(make_float2(m01.z, m01.w), vnext, h);
+            h = ffma2(make_float2(m2f.x, m2f.y), vf, h);
+            const float coef = fmaf(a.U, ldf(dg0 + 4 * i), -uq);
+            h.x = fmaf(coef, vcur.x, h.x);
+            h.y = fmaf(coef, vcur.y, h.y);
+            const float kx = -h.y;
+            const float ky = qi == i ? 0.f : h.x;
+            float2 nx;
+            if constexpr (!FINAL) {
+                acc[u].x = fmaf(sc.b, kx, acc[u].x);
+                acc[u].y = fmaf(sc.b, ky, acc[u].y);
+                nx.x = fmaf(sc.cc, kx, y0[u].x);
+                nx.y = fmaf(sc.cc, ky, y0[u].y);
+            } else {
+                nx.x = fmaf(sdt, acc[u].x + kx, y0[u].x);
+                nx.y = fmaf(sdt, acc[u].y + ky, y0[u].y);
+                y0[u] = nx;
+            }
+            if (qi >= i) sts(own + dnext, nx);
+            if (qi == i) dnew = nx.x;
+            if (band_t && (unsigned)(qi - i - 1) < (unsigned)a.bw)
+                sts(__float_as_int(m2f.w) + mir_lane, make_float2(nx.x, -nx.y));
+            vprev = vcur;
+            vcur = vnext;
+        }
+        const uint32_t ta = t0 + (uint32_t)(8 * j);
+        if constexpr (!FINAL) tm_st4(ta + 4, acc[0], acc[1]);
+        else tm_st8z(ta, y0[0], y0[1]);
+    }
+    publish_diag<FINAL, CLUSTER>(a, c, diag_t && (unsigned)qi < (unsigned)kR, cur, slot, s, q, dnew, b_id, snap_now,
+                                 snap_row);
+}
+
+template <bool FINAL, bool PM1, bool CLUSTER>
+__device__ __forceinline__ void tile_stage(const TileArgs &a, const TileCtx &c, const StageC &sc, long long b_id,
+                                           bool snap_now, long long snap_row)
 {
     int e = 0;   // row pairs of this warp done so far (tensor-memory column / 8)
     for (int it = 0; it < a.k_tiles; ++it) {
         const uint2 td = __ldg(&c.tiles[it]);
         if (td.x == 0xFFFFFFFFu) break;
-        tile_rows<STAGE, PM1, CLUSTER>(a, c, td, e, b_id, snap_now, snap_row);
-        e += (((td.x >> 9) & 15) + 1) >> 1;
+        if (PM1 && (td.y & kFull)) {
+            if (td.y & kRemote) tile_rows8<FINAL, CLUSTER, true>(a, c, sc, td, e, b_id, snap_now, snap_row);
+            else tile_rows8<FINAL, CLUSTER, false>(a, c, sc, td, e, b_id, snap_now, snap_row);
+            e += kR / 2;
+        } else {
+            tile_rows<FINAL, PM1, CLUSTER>(a, c, sc, td, e, b_id, snap_now, snap_row);
+            e += (td_cnt(td.x) + 1) >> 1;
+        }
     }
 }
 
@@ -415,15 +607,15 @@ __device__ __forceinline__ void tile_batch(const TileArgs &a, const TileCtx &c, 
             }
         }
     }
-    // y0 of the computed elements into tensor memory (acc is written at stage 0)
+    // y0 of the computed elements into tensor memory, accumulators zeroed
     {
         int e = 0;
         for (int it = 0; it < a.k_tiles; ++it) {
             const uint2 td = __ldg(&c.tiles[it]);
             if (td.x == 0xFFFFFFFFu) break;
-            const int p0 = td.x & 511, cnt = (td.x >> 9) & 15, blk = (td.x >> 13) & 7, slot = (td.x >> 16) & 255;
+            const int p0 = td_p0(td.x), cnt = td_cnt(td.x), blk = td_blk(td.x), slot = td_slot(td.x);
             const int s = p0 >= N ? 1 : 0;
-            const int q = a.qoff + 32 * blk + lane;
+            const int q = lane < kW ? a.qoff + kW * blk + lane : kIdleQ;
             const long long m = b_id * S + slot;
             for (int i = 0; i < cnt; i += 2) {
                 float2 v[2];
@@ -436,7 +628,7 @@ __device__ __forceinline__ void tile_batch(const TileArgs &a, const TileCtx &c, 
                     }
                 }
                 __syncwarp();
-                tm_st4(c.t_state + (uint32_t)(8 * (e + (i >> 1))), v[0], v[1]);
+                tm_st8z(c.t_state + (uint32_t)(8 * (e + (i >> 1))), v[0], v[1]);
             }
             e += (cnt + 1) >> 1;
         }
@@ -444,19 +636,18 @@ __device__ __forceinline__ void tile_batch(const TileArgs &a, const TileCtx &c, 
     tmem_wait_st();
     stage_sync<CLUSTER>();
 
+    const float hdt = a.dt * 0.5f;
     for (long long step = 0; step < a.n_steps; ++step) {
         const bool snap_now = a.snap && ((step + 1) % a.out_every == 0);
         const long long snap_row = (step + 1) / a.out_every;
-        tile_stage<0, PM1, CLUSTER>(a, c, b_id, snap_now, snap_row);
-        tmem_wait_st();
-        stage_sync<CLUSTER>();
-        tile_stage<1, PM1, CLUSTER>(a, c, b_id, snap_now, snap_row);
-        tmem_wait_st();
-        stage_sync<CLUSTER>();
-        tile_stage<2, PM1, CLUSTER>(a, c, b_id, snap_now, snap_row);
-        tmem_wait_st();
-        stage_sync<CLUSTER>();
-        tile_stage<3, PM1, CLUSTER>(a, c, b_id, snap_now, snap_row);
+#pragma unroll 1
+        for (int k = 0; k < 3; ++k) {
+            const StageC sc{k & 1, k == 0 ? 1.f : 2.f, k == 2 ? a.dt : hdt};
+            tile_stage<false, PM1, CLUSTER>(a, c, sc, b_id, snap_now, snap_row);
+            tmem_wait_st();
+            stage_sync<CLUSTER>();
+        }
+        tile_stage<true, PM1, CLUSTER>(a, c, StageC{1, 0.f, 0.f}, b_id, snap_now, snap_row);
         tmem_wait_st();
         stage_sync<CLUSTER>();
     }
@@ -467,9 +658,9 @@ __device__ __forceinline__ void tile_batch(const TileArgs &a, const TileCtx &c, 
         for (int it = 0; it < a.k_tiles; ++it) {
             const uint2 td = __ldg(&c.tiles[it]);
             if (td.x == 0xFFFFFFFFu) break;
-            const int p0 = td.x & 511, cnt = (td.x >> 9) & 15, blk = (td.x >> 13) & 7, slot = (td.x >> 16) & 255;
+            const int p0 = td_p0(td.x), cnt = td_cnt(td.x), blk = td_blk(td.x), slot = td_slot(td.x);
             const int s = p0 >= N ? 1 : 0;
-            const int q = a.qoff + 32 * blk + lane;
+            const int q = lane < kW ? a.qoff + kW * blk + lane : kIdleQ;
             const long long m = b_id * S + slot;
             for (int i = 0; i < cnt; i += 2) {
                 uint32_t w[8];
@@ -652,6 +843,7 @@ struct Layout {
     std::vector<int4> koff;                      // [C][nblk][32]
     std::vector<float2> tq;                      // [nblk][32][3]
     std::vector<RowEntry> rows;                  // [2N]
+    std::vector<RowPm1> rows_pm1;                // [2N], carried-row lattices: the table the kernel reads
     std::vector<int> rp_k;                       // [nblk][32][3] column read by each row-part slot
     std::vector<char> rp_real;                   // [nblk][32][3] the slot is a bond (else zero hopping)
     std::vector<int> slices;                     // per rank
@@ -691,10 +883,215 @@ static int owner(const Layout &L, int sr)
     return r;
 }
 
+// Row-part slots of every column (depends on the lattice only; computed once
+// per plan): the column read by each of a lane's three gathers and its hopping.
+struct RowSlots {
+    std::vector<int> k;         // [nblk][32][3]
+    std::vector<char> real;     // [nblk][32][3]
+    std::vector<float2> tq;     // [nblk][32][3]
+};
+static void row_part_slots(int N, int bw, const std::vector<Nbr> &nb, RowSlots &rs)
+{
+    // Each lane's neighbours may sit in any of the three slots (a slot is one
+    // warp-wide gather), and a missing neighbour reads a stored decoy column
+    // with zero hopping.  Per 16-lane half-warp the assignment and the decoys
+    // are searched so that each gather touches as few words per shared-memory
+    // bank pair as possible (the bank pair of column k in any row is
+    // lane(k) mod 16 in this layout; lanes reading the same column share a
+    // word).  The idle lane 31 repeats lane 30's reads.
+    const int nblk = (N + kW - 1) / kW, qoff = N - kW * nblk;
+    rs.k.assign((size_t)nblk * 32 * 3, 0);
+    rs.real.assign((size_t)nblk * 32 * 3, 0);
+    rs.tq.assign((size_t)nblk * 32 * 3, make_float2(0.f, 0.f));
+    auto bank = [&](int k) { return lane_of(k, qoff) % 16; };
+    struct Ent {
+        int k;
+        bool real;
+        float t;
+    };
+    static const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    for (int b = 0; b < nblk; ++b)
+        for (int h = 0; h < 2; ++h) {
+            const int l0 = 16 * h, l1 = std::min(16 * h + 16, kW), nl = l1 - l0;
+            Ent ent0[16][3];
+            int qv[16];
+            for (int j = 0; j < nl; ++j) {
+                const int q = qoff + kW * b + l0 + j;
+                qv[j] = q;
+                const int qq = q < 0 ? 0 : q;
+                for (int n = 0; n < 3; ++n) ent0[j][n] = Ent{qq, false, 0.f};
+                if (q < 0) continue;
+                for (int n = 0; n < nb[q].deg; ++n) ent0[j][n] = Ent{nb[q].k[n], true, (float)nb[q].t[n]};
+            }
+            Ent ent[16][3];
+            int perm[16][3];   // slot n holds ent[j][perm[j][n]]
+            // distinct words of slot n (lane `skip` left out), and their bank-pair counts
+            auto slot_words = [&](int n, int skip, int *cols, int &nc, int *pc) {
+                nc = 0;
+                for (int x = 0; x < 16; ++x) pc[x] = 0;
+                for (int j = 0; j < nl; ++j) {
+                    if (j == skip) continue;
+                    const int k = ent[j][perm[j][n]].k;
+                    bool seen = false;
+                    for (int x = 0; x < nc && !seen; ++x) seen = cols[x] == k;
+                    if (seen) continue;
+                    cols[nc++] = k;
+                    pc[bank(k)]++;
+                }
+            };
+            auto cost = [&]() {
+                long long c = 0;
+                int cols[16], nc, pc[16];
+                for (int n = 0; n < 3; ++n) {
+                    slot_words(n, -1, cols, nc, pc);
+                    int mx = 0, sq = 0;
+                    for (int x = 0; x < 16; ++x) {
+                        mx = std::max(mx, pc[x]);
+                        sq += pc[x] * pc[x];
+                    }
+                    c += 1000 * mx + sq;
+                }
+                return c;
+            };
+            // decoys of lane j: a column another lane of the slot already reads,
+            // else a stored column on the least used bank pair
+            auto place_decoys = [&](int j) {
+                int cols[16], nc, pc[16];
+                for (int n = 0; n < 3; ++n) {
+                    Ent &e = ent[j][perm[j][n]];
+                    if (e.real) continue;
+                    slot_words(n, j, cols, nc, pc);
+                    const int q = qv[j];
+                    int best = q, best_c = 1 << 30;
+                    for (int d = 0; d <= bw; ++d)
+                        for (int sg = 1; sg >= -1; sg -= 2) {
+                            const int k = q + sg * d;
+                            if (k < 0 || k >= N || k < q - bw) continue;
+                            bool shared = false;
+                            for (int x = 0; x < nc && !shared; ++x) shared = cols[x] == k;
+                            const int c = shared ? 0 : 1 + 4 * pc[bank(k)];
+                            if (c < best_c) {
+                                best_c = c;
+                                best = k;
+                            }
+                        }
+                    e.k = best;
+                }
+            };
+            // starting points: the neighbour order, the pattern where lanes j and
+            // j + 2 read their common neighbour column in one slot, and
+            // pseudo-random orders; a local search (one lane's order at a time)
+            // from each, the best kept
+            Ent best_ent[16][3];
+            int best_perm[16][3];
+            long long best_all = -1;
+            uint32_t rng = 0x9E3779B9u ^ (uint32_t)(b * 2 + h);
+            for (int start = 0; start < 16 && best_all != 3000 + 3 * nl; ++start) {
+                for (int j = 0; j < nl; ++j) {
+                    for (int n = 0; n < 3; ++n) ent[j][n] = ent0[j][n];
+                    int x = 0;
+                    if (start == 1 && qv[j] >= 0) {
+                        int ip = -1, im = -1;
+                        for (int n = 0; n < 3; ++n) {
+                            if (ent[j][n].real && ent[j][n].k == qv[j] + 1) ip = n;
+                            if (ent[j][n].real && ent[j][n].k == qv[j] - 1) im = n;
+                        }
+                        if (ip >= 0 && im >= 0) {
+                            const int first = (j & 3) < 2 ? ip : im, second = (j & 3) < 2 ? im : ip;
+                            for (int y = 0; y < 6; ++y)
+                                if (perms[y][0] == first && perms[y][1] == second) x = y;
+                        }
+                    } else if (start > 1 && qv[j] >= 0) {
+                        rng = rng * 1664525u + 1013904223u;
+                        x = (int)((rng >> 16) % 6);
+                    }
+                    for (int n = 0; n < 3; ++n) perm[j][n] = perms[x][n];
+                }
+                for (int j = 0; j < nl; ++j)
+                    if (qv[j] >= 0) place_decoys(j);
+                long long cur = cost();
+                for (int pass = 0; pass < 8; ++pass) {
+                    bool improved = false;
+                    for (int j = 0; j < nl; ++j) {
+                        if (qv[j] < 0) continue;
+                        Ent keep_e[3], bst_e[3];
+                        int keep_p[3], bst_p[3];
+                        for (int n = 0; n < 3; ++n) {
+                            keep_e[n] = bst_e[n] = ent[j][n];
+                            keep_p[n] = bst_p[n] = perm[j][n];
+                        }
+                        long long bst = cur;
+                        for (int y = 0; y < 6; ++y) {
+                            for (int n = 0; n < 3; ++n) {
+                                ent[j][n] = keep_e[n];
+                                perm[j][n] = perms[y][n];
+                            }
+                            place_decoys(j);
+                            const long long c = cost();
+                            if (c < bst) {
+                                bst = c;
+                                for (int n = 0; n < 3; ++n) {
+                                    bst_e[n] = ent[j][n];
+                                    bst_p[n] = perm[j][n];
+                                }
+                            }
+                        }
+                        for (int n = 0; n < 3; ++n) {
+                            ent[j][n] = bst_e[n];
+                            perm[j][n] = bst_p[n];
+                        }
+                        if (bst < cur) {
+                            cur = bst;
+                            improved = true;
+                        }
+                    }
+                    if (!improved) break;
+                }
+                if (best_all < 0 || cur < best_all) {
+                    best_all = cur;
+                    for (int j = 0; j < nl; ++j)
+                        for (int n = 0; n < 3; ++n) {
+                            best_ent[j][n] = ent[j][n];
+                            best_perm[j][n] = perm[j][n];
+                        }
+                }
+            }
+            for (int j = 0; j < nl; ++j)
+                for (int n = 0; n < 3; ++n) {
+                    const Ent &e = best_ent[j][best_perm[j][n]];
+                    const size_t ix = (size_t)(b * 32 + l0 + j) * 3 + n;
+                    rs.k[ix] = e.k;
+                    rs.real[ix] = e.real ? 1 : 0;
+                    rs.tq[ix] = e.real ? make_float2(e.t, e.t) : make_float2(0.f, 0.f);
+                }
+        }
+}
+
+// The plan's row-part slots: searched on first use, then kept in the plan.
+static void plan_row_slots(Plan *p, const std::vector<Nbr> &nb, RowSlots &rs)
+{
+    if (p->tile_rp_k.empty()) {
+        row_part_slots(p->N, p->bandwidth, nb, rs);
+        p->tile_rp_k = rs.k;
+        p->tile_rp_real = rs.real;
+        p->tile_rp_t.resize(2 * rs.tq.size());
+        for (size_t i = 0; i < rs.tq.size(); ++i) {
+            p->tile_rp_t[2 * i] = rs.tq[i].x;
+            p->tile_rp_t[2 * i + 1] = rs.tq[i].y;
+        }
+        return;
+    }
+    rs.k = p->tile_rp_k;
+    rs.real = p->tile_rp_real;
+    rs.tq.resize(p->tile_rp_t.size() / 2);
+    for (size_t i = 0; i < rs.tq.size(); ++i) rs.tq[i] = make_float2(p->tile_rp_t[2 * i], p->tile_rp_t[2 * i + 1]);
+}
+
 // Build the decomposition for C CTAs per sample and S slots (C == 1 only).
 // Returns false when it does not fit (shared memory, tensor memory, ranks
 // narrower than the bandwidth).
-static bool build_layout(const Plan *p, const std::vector<Nbr> &nb, bool pm1, int C, int S, int warps, Layout &L)
+static bool build_layout(const Plan *p, const std::vector<Nbr> &nb, const RowSlots &rs, bool pm1, int C, int S,
+                         int warps, Layout &L)
 {
     const int N = p->N, bw = p->bandwidth;
     L = Layout();
@@ -702,13 +1099,13 @@ static bool build_layout(const Plan *p, const std::vector<Nbr> &nb, bool pm1, in
     const int kWarpsT = warps;
     L.N = N;
     L.bw = bw;
-    L.nblk = (N + 31) / 32;
-    L.qoff = N - 32 * L.nblk;
+    L.nblk = (N + kW - 1) / kW;
+    L.qoff = N - kW * L.nblk;
     L.C = C;
     L.S = S;
     L.pm1 = pm1 ? 1 : 0;
     const int nblk = L.nblk, qoff = L.qoff;
-    auto lastcol = [&](int b) { return qoff + 32 * b + 31; };
+    auto lastcol = [&](int b) { return qoff + kW * b + kW - 1; };
     auto cslices = [&](int p_) { return nblk - blk_of(p_, qoff); };
     if (C > kMaxCluster || (C > 1 && (C & 1))) return false;
     // ---- ranks: C == 1 both spins; C >= 2 each spin split in C/2 ranks, balanced by computed slices
@@ -751,16 +1148,20 @@ static bool build_layout(const Plan *p, const std::vector<Nbr> &nb, bool pm1, in
             for (int b = 0; b < nblk; ++b) {
                 const int hi = std::max(P0, std::min(P1, lastcol(b) + bw + 1));
                 const int rows = hi - P0;
+                off = (off + 127) / 128 * 128;   // every region on a 128-byte boundary (bank pattern)
                 L.zoff[r][s][b] = off - P0 * kRowBytes;
                 off += rows * kRowBytes;
             }
         }
         slot_bytes = std::max(slot_bytes, off);
     }
-    L.slot_bytes = slot_bytes;
-    L.buf_bytes = S * slot_bytes;
-    L.rows_bytes = max_rows * (int)sizeof(RowEntry);
+    // slots and the stage buffers on 128-byte boundaries too: the row table is
+    // padded so that the buffers start on one
+    L.slot_bytes = (slot_bytes + 127) / 128 * 128;
+    L.buf_bytes = S * L.slot_bytes;
     const int diag_bytes = 16 * ((4 * 2 * S * 2 * N + 15) / 16);
+    L.rows_bytes = max_rows * (int)sizeof(RowEntry);
+    L.rows_bytes += (128 - (64 + diag_bytes + L.rows_bytes) % 128) % 128;
     L.smem_bytes = 64 + diag_bytes + L.rows_bytes + 2 * L.buf_bytes;
     if (L.smem_bytes > 227 * 1024) return false;
 
@@ -804,77 +1205,32 @@ static bool build_layout(const Plan *p, const std::vector<Nbr> &nb, bool pm1, in
         e.mir = L.zoff[r][s][blk_of(pp, qoff)] + 8 * lane_of(pp, qoff);
         L.rows[sr] = e;
     }
-    // ---- row-part slots per column q: the column read (k) and its hopping.
-    // PM1 lattices: slots q - 1, q + 1, far, and a missing neighbour reads a
-    // stored decoy column with zero hopping, chosen so that each slot's
-    // 16-lane half-warp gather hits 16 distinct shared-memory bank pairs
-    // (the bank pair of column k is (k - qoff) mod 16 in this layout).
-    // Other lattices: the neighbour list, empty slots read the own element.
-    L.rp_k.assign((size_t)nblk * 32 * 3, 0);
-    L.rp_real.assign((size_t)nblk * 32 * 3, 0);
-    L.tq.assign((size_t)nblk * 32 * 3, make_float2(0.f, 0.f));
-    auto bank = [&](int k) { return ((k - qoff) % 16 + 16) % 16; };
-    for (int b = 0; b < nblk; ++b)
-        for (int h = 0; h < 2; ++h) {
-            bool used[3][16] = {};
-            std::vector<int> pending[3];
-            for (int ln = 16 * h; ln < 16 * h + 16; ++ln) {
-                const int q = qoff + 32 * b + ln;
-                int *rk = &L.rp_k[(size_t)(b * 32 + ln) * 3];
-                char *re_ = &L.rp_real[(size_t)(b * 32 + ln) * 3];
-                float2 *tq = &L.tq[(size_t)(b * 32 + ln) * 3];
-                const int qq = q < 0 ? 0 : q;
-                for (int n = 0; n < 3; ++n) rk[n] = qq;
-                if (q < 0) continue;
-                if (pm1) {
-                    for (int n = 0; n < nb[q].deg; ++n) {
-                        const int k = nb[q].k[n];
-                        const int sl = k == q - 1 ? 0 : (k == q + 1 ? 1 : 2);
-                        rk[sl] = k;
-                        re_[sl] = 1;
-                        tq[sl] = make_float2((float)nb[q].t[n], (float)nb[q].t[n]);
-                    }
-                    if (!re_[0] && q >= 1) rk[0] = q - 1;
-                    if (!re_[1] && q <= N - 2) rk[1] = q + 1;
-                    for (int sl = 0; sl < 3; ++sl) {
-                        if (re_[sl] || sl < 2) used[sl][bank(rk[sl])] = true;
-                        else pending[sl].push_back(ln);
-                    }
-                } else {
-                    for (int n = 0; n < nb[q].deg; ++n) {
-                        rk[n] = nb[q].k[n];
-                        re_[n] = 1;
-                        tq[n] = make_float2((float)nb[q].t[n], (float)nb[q].t[n]);
-                    }
-                }
-            }
-            for (int ln : pending[2]) {
-                const int q = qoff + 32 * b + ln;
-                int best = q;
-                for (int d = 1; d <= bw; ++d) {
-                    for (int sg = 1; sg >= -1; sg -= 2) {
-                        const int k = q + sg * d;
-                        if (k < 0 || k >= N || k < q - bw) continue;
-                        if (!used[2][bank(k)]) {
-                            best = k;
-                            d = bw + 1;
-                            break;
-                        }
-                    }
-                }
-                L.rp_k[(size_t)(b * 32 + ln) * 3 + 2] = best;
-                used[2][bank(best)] = true;
-            }
+    if (pm1) {
+        L.rows_pm1.assign((size_t)2 * N, RowPm1{});
+        for (int sr = 0; sr < 2 * N; ++sr) {
+            const RowEntry &e = L.rows[sr];
+            RowPm1 &f = L.rows_pm1[sr];
+            f.m0[0] = f.m0[1] = e.mt[0];
+            f.m1[0] = f.m1[1] = e.mt[1];
+            f.m2[0] = f.m2[1] = e.mt[2];
+            f.far = e.dcol[2];
+            if (e.flags & 4u) f.far |= 1 | ((e.flags & 32u) ? 2 : 0);
+            f.mir = e.mir;
         }
+    }
+    L.rp_k = rs.k;
+    L.rp_real = rs.real;
+    L.tq = rs.tq;
     L.koff.assign((size_t)C * nblk * 32, int4{0, 0, 0, 0});
     for (int r = 0; r < C; ++r) {
         const int s = L.row_begin[r] >= N ? 1 : 0;
         for (int b = 0; b < nblk; ++b)
             for (int ln = 0; ln < 32; ++ln) {
                 int o[3];
+                const int lr = std::min(ln, kW - 1);   // the idle lane repeats lane 30's reads
                 for (int n = 0; n < 3; ++n) {
-                    const int k = L.rp_k[(size_t)(b * 32 + ln) * 3 + n];
-                    o[n] = L.zoff[r][s][blk_of(k, qoff)] - L.zoff[r][s][b] + 8 * (lane_of(k, qoff) - ln);
+                    const int k = L.rp_k[(size_t)(b * 32 + lr) * 3 + n];
+                    o[n] = L.zoff[r][s][blk_of(k, qoff)] - L.zoff[r][s][b] + 8 * (lane_of(k, qoff) - lr);
                 }
                 L.koff[((size_t)r * nblk + b) * 32 + ln] = int4{o[0], o[1], o[2], 0};
             }
@@ -903,9 +1259,9 @@ static bool build_layout(const Plan *p, const std::vector<Nbr> &nb, bool pm1, in
                     for (int x = P0; x < last;) {
                         const int cnt = std::min(kR, last - x);
                         uint2 td;
-                        td.x = (uint32_t)(s * N + x) | ((uint32_t)cnt << 9) | ((uint32_t)b << 13) | ((uint32_t)slot << 16);
+                        td.x = td_make(s * N + x, cnt, b, slot);
                         uint32_t f = 0;
-                        const int c0 = qoff + 32 * b;
+                        const int c0 = qoff + kW * b;
                         for (int i = 0; i < cnt; ++i) {
                             const int pp = x + i;
                             if (blk_of(pp, qoff) == b) f |= kDiag;
@@ -922,6 +1278,15 @@ static bool build_layout(const Plan *p, const std::vector<Nbr> &nb, bool pm1, in
                             if (nk == 2 && r + 1 >= C) return false;
                             f |= pk << kPrevShift;
                             f |= nk << kNextShift;
+                        }
+                        if (pm1 && cnt == kR && !(f & kRemoteMir)) {
+                            // remote far slots of the tile: all in one neighbour rank
+                            bool prev = false, next = false;
+                            for (int i = 0; i < cnt; ++i) {
+                                const uint32_t fl = L.rows[s * N + x + i].flags;
+                                if (fl & 4u) ((fl & 32u) ? next : prev) = true;
+                            }
+                            if (!(prev && next)) f |= kFull | (next ? kFarNext : 0u);
                         }
                         td.y = f;
                         tl.push_back({cnt, td});
@@ -991,18 +1356,20 @@ static long long check_layout(const Layout &L, const std::vector<Nbr> &nb, char 
             for (int it = 0; it < L.k_tiles; ++it) {
                 const uint2 td = L.tiles[((size_t)r * L.warps + w) * L.k_tiles + it];
                 if (td.x == 0xFFFFFFFFu) break;
-                const int p0 = td.x & 511, cnt = (td.x >> 9) & 15, b = (td.x >> 13) & 7, slot = (td.x >> 16) & 255;
+                const int p0 = td_p0(td.x), cnt = td_cnt(td.x), b = td_blk(td.x), slot = td_slot(td.x);
                 if (slot != 0) continue;
                 const int s = p0 >= N ? 1 : 0, pp0 = p0 - s * N;
                 // diagonal-table writes (once per row of a tile holding the row's diagonal)
                 for (int i = 0; i < cnt; ++i) {
-                    const int c0 = qoff + 32 * b, p = pp0 + i;
-                    if ((td.y & kDiag) && (unsigned)(p - c0) < 32u) dwrites[(size_t)s * N + p]++;
+                    const int c0 = qoff + kW * b, p = pp0 + i;
+                    if ((td.y & kDiag) && (unsigned)(p - c0) < (unsigned)kW) dwrites[(size_t)s * N + p]++;
                 }
                 for (int ln = 0; ln < 32; ++ln) {
-                    const int q = qoff + 32 * b + ln;
+                    // the idle lane 31 reads lane 30's addresses and writes nothing
+                    const int lr = std::min(ln, kW - 1);
+                    const int q = ln < kW ? qoff + kW * b + ln : kIdleQ;
                     const int4 ko = L.koff[((size_t)r * nblk + b) * 32 + ln];
-                    const int own0 = L.zoff[r][s][b] + kRowBytes * pp0 + 8 * ln;
+                    const int own0 = L.zoff[r][s][b] + kRowBytes * pp0 + 8 * lr;
                     for (int i = 0; i < cnt; ++i) {
                         const int p = pp0 + i, sr = s * N + p;
                         const bool act = q >= p && q < N && q >= 0;
@@ -1021,6 +1388,33 @@ static long long check_layout(const Layout &L, const std::vector<Nbr> &nb, char 
                         }
                         const RowEntry &e = L.rows[sr];
                         for (int n = 0; n < 3; ++n) {
+                            if (L.pm1) {
+                                const RowPm1 &f = L.rows_pm1[sr];
+                                const float *m = n == 0 ? f.m0 : (n == 1 ? f.m1 : f.m2);
+                                if (m[0] != e.mt[n] || m[1] != e.mt[n]) note("row table hopping pair", r, sr, q);
+                            }
+                            if (L.pm1 && n == 2) {
+                                // the far slot as the kernel decodes it
+                                const int far = L.rows_pm1[sr].far;
+                                if (L.rows_pm1[sr].mir != e.mir) note("row table mirror offset", r, sr, q);
+                                if ((td.y & kFull) && (far & 1) && (((far & 2) != 0) != ((td.y & kFarNext) != 0)))
+                                    note("remote far slot outside the fast tile's far rank", r, sr, q);
+                                if (far & 1) {
+                                    const int o = (far & 2) ? r + 1 : r - 1;
+                                    const int k = (far & ~3) / kRowBytes;
+                                    if (o < 0 || o >= C) {
+                                        note("far slot in a rank outside the cluster", r, sr, q);
+                                        continue;
+                                    }
+                                    read_ok(o, L.zoff[o][s][b] + (far & ~3) + 8 * lr, (s * N + k) * N + q, act, sr, q,
+                                            "far column-part read (remote)");
+                                } else {
+                                    if (far & 3) note("far slot offset not row aligned", r, sr, q);
+                                    const int k = p + far / kRowBytes;
+                                    read_ok(r, own + far, (s * N + k) * N + q, act, sr, q, "far column-part read");
+                                }
+                                continue;
+                            }
                             if (L.pm1 && n < 2) {
                                 // carried rows p -+ 1: from the tile, or the boundary rows
                                 const int k = n == 0 ? p - 1 : p + 1;
@@ -1029,7 +1423,7 @@ static long long check_layout(const Layout &L, const std::vector<Nbr> &nb, char 
                                 const uint32_t kind = (td.y >> (n == 0 ? kPrevShift : kNextShift)) & 3;
                                 if (kind == 2) {
                                     const int o = n == 0 ? r - 1 : r + 1;
-                                    read_ok(o, elem_off(L.zoff[o], s, k, q, qoff), (s * N + k) * N + q, act, sr, q,
+                                    read_ok(o, L.zoff[o][s][b] + kRowBytes * k + 8 * lr, (s * N + k) * N + q, act, sr, q,
                                             "boundary-row read (remote)");
                                 } else if (kind == 0) {
                                     read_ok(r, own + (n == 0 ? -kRowBytes : kRowBytes), (s * N + k) * N + q, act, sr,
@@ -1042,7 +1436,7 @@ static long long check_layout(const Layout &L, const std::vector<Nbr> &nb, char 
                             if (e.flags & (1u << n)) {
                                 const int o = (e.flags >> (3 + n)) & 1u ? r + 1 : r - 1;
                                 const int k = e.dcol[n] / kRowBytes;
-                                read_ok(o, L.zoff[o][s][b] + e.dcol[n] + 8 * ln, (s * N + k) * N + q, act, sr, q,
+                                read_ok(o, L.zoff[o][s][b] + e.dcol[n] + 8 * lr, (s * N + k) * N + q, act, sr, q,
                                         "column-part read (remote)");
                             } else {
                                 const int k = p + e.dcol[n] / kRowBytes;
@@ -1059,6 +1453,8 @@ static long long check_layout(const Layout &L, const std::vector<Nbr> &nb, char 
                                 const int off = (o == r ? e.mir : mir_next) + kRowBytes * q;
                                 if (o >= C) {
                                     note("mirror row beyond the last rank", r, sr, q);
+                                } else if (o != r && !(td.y & kRemoteMir)) {
+                                    note("mirror row in the next rank in a tile without kRemoteMir", r, sr, q);
                                 } else {
                                     read_ok(o, off, (s * N + q) * N + p, true, sr, q, "mirror store");
                                     mwrites[(size_t)(s * N + q) * N + p]++;
@@ -1085,7 +1481,8 @@ static long long check_layout(const Layout &L, const std::vector<Nbr> &nb, char 
 // slots as useful for C == 1.
 // C_force / warps_force (0: the plan's overrides or defaults); multi_slot:
 // several samples per cluster also for C > 1 (batched launches).
-static bool choose_layout(const Plan *p, int64_t M, const std::vector<Nbr> &nb, bool pm1, Layout &out,
+static bool choose_layout(const Plan *p, int64_t M, const std::vector<Nbr> &nb, const RowSlots &rs, bool pm1,
+                          Layout &out,
                           int C_force = 0, int warps_force = 0, bool multi_slot = false)
 {
     const int sm = p->sm_count > 0 ? p->sm_count : 1;
@@ -1100,7 +1497,7 @@ static bool choose_layout(const Plan *p, int64_t M, const std::vector<Nbr> &nb, 
         bool ok = false;
         for (int S = 1; S <= want; ++S) {
             Layout L;
-            if (!build_layout(p, nb, pm1, C, S, warps, L)) break;
+            if (!build_layout(p, nb, rs, pm1, C, S, warps, L)) break;
             best = L;
             ok = true;
         }
@@ -1120,7 +1517,7 @@ struct TablePack {
 };
 static void pack_tables(const Layout &L, TablePack &t)
 {
-    const size_t b_rows = L.rows.size() * sizeof(RowEntry);
+    const size_t b_rows = L.rows.size() * sizeof(RowEntry);   // RowPm1 entries have the same size
     const size_t b_tiles = ((L.tiles.size() * sizeof(uint2) + 15) / 16) * 16;
     const size_t b_koff = L.koff.size() * sizeof(int4);
     const size_t b_tq = ((L.tq.size() * sizeof(float2) + 15) / 16) * 16;
@@ -1128,7 +1525,8 @@ static void pack_tables(const Layout &L, TablePack &t)
     t.o_tiles = b_rows;
     t.o_koff = b_rows + b_tiles;
     t.o_tq = b_rows + b_tiles + b_koff;
-    std::memcpy(t.bytes.data(), L.rows.data(), b_rows);
+    if (L.pm1) std::memcpy(t.bytes.data(), L.rows_pm1.data(), b_rows);
+    else std::memcpy(t.bytes.data(), L.rows.data(), b_rows);
     std::memcpy(t.bytes.data() + t.o_tiles, L.tiles.data(), L.tiles.size() * sizeof(uint2));
     std::memcpy(t.bytes.data() + t.o_koff, L.koff.data(), b_koff);
     std::memcpy(t.bytes.data() + t.o_tq, L.tq.data(), L.tq.size() * sizeof(float2));
@@ -1182,7 +1580,9 @@ int launch_tile(Plan *p, void *rho, int64_t M, int64_t n_steps, void *snap, cuda
     neighbours(p, nb);
     const bool pm1 = is_pm1(nb);
     Layout L;
-    if (!choose_layout(p, M, nb, pm1, L)) return FTWA_ERR_UNSUPPORTED;
+    RowSlots rs;
+    plan_row_slots(p, nb, rs);
+    if (!choose_layout(p, M, nb, rs, pm1, L)) return FTWA_ERR_UNSUPPORTED;
     const int sm = p->sm_count > 0 ? p->sm_count : 1;
     const long long batches = (M + L.S - 1) / L.S;
     int grid = (int)std::min<long long>(std::max<long long>(batches, 1), std::max(1, sm / L.C)) * L.C;
@@ -1286,12 +1686,14 @@ extern "C" int ftwa_debug_tile_check(int32_t n_sites, int32_t n_bonds, const int
     }
     std::vector<Nbr> nb;
     neighbours(&p, nb);
+    RowSlots rs;
+    row_part_slots(p.N, p.bandwidth, nb, rs);
     // both CTA sizes the stepper launches with
     *violations = 0;
     bool any = false;
     for (int warps : {16, 24}) {
         Layout L;
-        if (!build_layout(&p, nb, is_pm1(nb), cluster, slots, warps, L)) continue;
+        if (!build_layout(&p, nb, rs, is_pm1(nb), cluster, slots, warps, L)) continue;
         any = true;
         *violations += check_layout(L, nb, msg, msg_len);
     }
@@ -1314,7 +1716,8 @@ struct BatchConfig {
 };
 
 static bool batch_config(Plan *const *plans, int n, const int64_t *M, const std::vector<std::vector<Nbr>> &nb,
-                         const std::vector<char> &pm1, int C, int warps, BatchConfig &bc)
+                         const std::vector<RowSlots> &rs, const std::vector<char> &pm1, int C, int warps,
+                         BatchConfig &bc)
 {
     bc = BatchConfig();
     bc.C = C;
@@ -1327,7 +1730,8 @@ static bool batch_config(Plan *const *plans, int n, const int64_t *M, const std:
         // cluster's C / Ci groups then integrate batches of it side by side
         bool ok = false;
         for (int Ci = 1; Ci <= C && !ok; Ci *= 2)
-            ok = choose_layout(plans[i], std::max<int64_t>(M[i], 1), nb[i], pm1[i] != 0, bc.L[i], Ci, warps, true);
+            ok = choose_layout(plans[i], std::max<int64_t>(M[i], 1), nb[i], rs[i], pm1[i] != 0, bc.L[i], Ci, warps,
+                               true);
         if (!ok) return false;
         bc.smem = std::max(bc.smem, bc.L[i].smem_bytes);
         pack_tables(bc.L[i], bc.tp[i]);
@@ -1435,15 +1839,17 @@ extern "C" int ftwa_batch_create_persistent(ftwa_plan_t *const *plans, int32_t n
     std::vector<Plan *> P(plans, plans + n);
     std::vector<std::vector<Nbr>> nb(n);
     std::vector<char> pm1(n);
+    std::vector<RowSlots> rs(n);
     for (int i = 0; i < n; ++i) {
         neighbours(P[i], nb[i]);
         pm1[i] = is_pm1(nb[i]) ? 1 : 0;
+        plan_row_slots(P[i], nb[i], rs[i]);
     }
     // the smallest cluster size every problem fits
     int C_min = 0;
     for (int C = 1; C <= kMaxCluster && !C_min; C *= 2) {
         BatchConfig bc;
-        if (batch_config(P.data(), n, M, nb, pm1, C, 24, bc)) C_min = C;
+        if (batch_config(P.data(), n, M, nb, rs, pm1, C, 24, bc)) C_min = C;
     }
     if (!C_min) return FTWA_ERR_UNSUPPORTED;
     std::vector<std::pair<int, int>> cands = {{C_min, 24}};
@@ -1469,7 +1875,7 @@ extern "C" int ftwa_batch_create_persistent(ftwa_plan_t *const *plans, int32_t n
         cudaEventCreate(&e1);
         for (size_t c = 0; c < cands.size() && rc == FTWA_OK; ++c) {
             BatchConfig bc;
-            if (!batch_config(P.data(), n, M, nb, pm1, cands[c].first, cands[c].second, bc)) continue;
+            if (!batch_config(P.data(), n, M, nb, rs, pm1, cands[c].first, cands[c].second, bc)) continue;
             for (int i = 0; i < n && rc == FTWA_OK; ++i) {
                 Mp[i] = std::min<int64_t>(M[i], 64LL * bc.L[i].S);
                 cudaFree(rp[i]);
@@ -1480,7 +1886,7 @@ extern "C" int ftwa_batch_create_persistent(ftwa_plan_t *const *plans, int32_t n
             }
             if (rc != FTWA_OK) break;
             BatchConfig bp;
-            if (!batch_config(P.data(), n, Mp.data(), nb, pm1, cands[c].first, cands[c].second, bp)) continue;
+            if (!batch_config(P.data(), n, Mp.data(), nb, rs, pm1, cands[c].first, cands[c].second, bp)) continue;
             BatchArgs B;
             void *mem = nullptr;
             rc = batch_upload(P.data(), n, bp, rp.data(), Mp.data(), std::min<int64_t>(n_steps, 10), nullptr, B, &mem, s);
@@ -1513,7 +1919,7 @@ extern "C" int ftwa_batch_create_persistent(ftwa_plan_t *const *plans, int32_t n
     BatchConfig bc;
     BatchArgs B;
     void *mem = nullptr;
-    if (rc == FTWA_OK && !batch_config(P.data(), n, M, nb, pm1, cands[best].first, cands[best].second, bc))
+    if (rc == FTWA_OK && !batch_config(P.data(), n, M, nb, rs, pm1, cands[best].first, cands[best].second, bc))
         rc = FTWA_ERR_UNSUPPORTED;
     if (rc == FTWA_OK) rc = batch_upload(P.data(), n, bc, rho_dev, M, n_steps, snap_dev, B, &mem, s);
     cudaLaunchConfig_t cfg;

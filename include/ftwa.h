@@ -94,8 +94,9 @@ typedef struct {
     double dt;                /* RK4 step in units of hbar/t (> 0)            */
     int32_t out_every;        /* snapshot cadence in steps (>= 1)             */
     int32_t cluster_override; /* CTAs per sample (1..8), 0 = automatic         */
-    int32_t threads_override; /* threads per CTA: 0 (automatic) or 768; the
-                                 tiled stepper (variant 3) also takes 512     */
+    int32_t threads_override; /* threads per CTA: 0 (automatic: 512 for the
+                                 tiled stepper, else 768) or 768; the tiled
+                                 stepper (variant 3) also takes 512           */
     int32_t autotune;         /* 1 = time candidate shapes on first evolve     */
     uint64_t timeout_us;      /* limit of every bounded in-kernel wait in
                                  microseconds, 0 = default (5 s)             */

@@ -1289,7 +1289,9 @@ static bool build_layout(const Plan *p, const std::vector<Nbr> &nb, const RowSlo
                             if (!(prev && next)) f |= kFull | (next ? kFarNext : 0u);
                         }
                         td.y = f;
-                        tl.push_back({cnt, td});
+                        // cost weight (per row, x100): unrolled tiles, with remote far slots, general path
+                        const int wgt = (f & kFull) ? ((f & kRemote) ? 110 : 100) : 150;
+                        tl.push_back({cnt * wgt, td});
                         L.slices[r] += cnt;
                         x += cnt;
                     }
@@ -1299,11 +1301,12 @@ static bool build_layout(const Plan *p, const std::vector<Nbr> &nb, const RowSlo
         std::vector<int> load(kWarpsT, 0), pairs(kWarpsT, 0);
         for (const auto &t : tl) {
             int w = -1;
+            const int tc = td_cnt(t.second.x);
             for (int x = 0; x < kWarpsT; ++x)
-                if (pairs[x] + (t.first + 1) / 2 <= pairs_cap && (w < 0 || load[x] < load[w])) w = x;
+                if (pairs[x] + (tc + 1) / 2 <= pairs_cap && (w < 0 || load[x] < load[w])) w = x;
             if (w < 0) return false;
             load[w] += t.first;
-            pairs[w] += (t.first + 1) / 2;
+            pairs[w] += (tc + 1) / 2;
             per_rank_warp[(size_t)r * kWarpsT + w].push_back(t.second);
         }
         for (int x = 0; x < kWarpsT; ++x) kt = std::max<int>(kt, (int)per_rank_warp[(size_t)r * kWarpsT + x].size());
@@ -1486,7 +1489,7 @@ static bool choose_layout(const Plan *p, int64_t M, const std::vector<Nbr> &nb, 
                           int C_force = 0, int warps_force = 0, bool multi_slot = false)
 {
     const int sm = p->sm_count > 0 ? p->sm_count : 1;
-    const int warps = warps_force ? warps_force : (p->threads_override == 512 ? 16 : 24);
+    const int warps = warps_force ? warps_force : (p->threads_override == 768 ? 24 : 16);
     for (int C = 1; C <= kMaxCluster; C *= 2) {
         if (C_force && C != C_force) continue;
         if (!C_force && p->cluster_override && C != p->cluster_override) continue;

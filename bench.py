@@ -49,7 +49,8 @@ def workload(M=16384, steps=1000, every=10, U=1.6):
 def config_dict(wl, extra=None):
     c = {"workload": "fTWA 198-site honeycomb flake (brick wall 11x18), charge-imbalanced Fock start",
          "n_sites": 198, "U_over_t": wl["U"], "samples_per_gpu": wl["M"], "rk4_steps": wl["steps"],
-         "dt": 0.01, "T": 10.0, "out_every": wl["every"], "state": "fp32 complex", "moments": "fp64",
+         "dt": 0.01, "T": 10.0, "out_every": wl["every"], "state": "fp32 complex",
+         "moments": "FP64 sample means, BF16x3 tcgen05 connected Gram (FP32 accumulate), FP64 estimators",
          "l2": "inputs larger than L2 (state 10.3 GB per GPU)"}
     if extra:
         c.update(extra)
@@ -143,6 +144,30 @@ def traffic_record(kernel_src, record="tile_stepper_fp32_198_traffic.txt"):
     try:
         return float(kv["dram_bytes_per_launch_full_workload"])
     except (KeyError, ValueError):
+        return None
+
+
+def count_kernels(fn):
+    """Kernels (not copies or memsets) that fn() launches, counted by CUPTI
+    through torch.profiler; NCCL's kernels are left out.  None if the
+    profiler is unavailable."""
+    import torch
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            fn()
+            torch.cuda.synchronize()
+        n = 0
+        for e in prof.events():
+            if e.device_type != torch.autograd.DeviceType.CUDA:
+                continue
+            name = e.name
+            if name.startswith(("Memcpy", "Memset", "memcpy", "memset")) or "nccl" in name.lower():
+                continue
+            n += 1
+        return n
+    except Exception as exc:   # profiler missing on this build: no count
+        print(f"note: kernel count unavailable ({exc})", file=sys.stderr)
         return None
 
 
@@ -609,8 +634,10 @@ def run_gpu(args):
             # exchange step: the estimators over the union of all ranks' samples
             shard.combine_moments(M, occ, conn, ws)
 
-    for _ in range(args.warmup):
+    for _ in range(args.warmup - 1):
         one_step(0, False)
+    # the last warm-up step also counts the kernels one step launches
+    launches_per_step = count_kernels(lambda: one_step(0, False))
     torch.cuda.synchronize()
     if P.status() != 0:
         raise RuntimeError("device status after warm-up")
@@ -767,7 +794,7 @@ def run_gpu(args):
             "config": config_dict(wl, {"parallelism": f"samples split over {ws} GPU(s); estimators all-reduced "
                                                         f"at the end of each step when more than one",
                                        "launch": info}),
-            "e2e": e2e, "roofline": roof, "clocks": clk, "gpu_launches": 4 * args.steps,
+            "e2e": e2e, "roofline": roof, "clocks": clk, "gpu_launches": (launches_per_step * args.steps if launches_per_step is not None else None),
             "evolve_ms": evolve_ms, "fp64": fp64, "u_1p0": u_alt, **extra}
     if rank == 0 and ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()

@@ -147,25 +147,29 @@ def traffic_record(kernel_src, record="tile_stepper_fp32_198_traffic.txt"):
         return None
 
 
-def count_kernels(fn):
-    """Kernels (not copies or memsets) that fn() launches, counted by CUPTI
-    through torch.profiler; NCCL's kernels are left out.  None if the
-    profiler is unavailable."""
+def count_kernels(fn, sessions=2):
+    """Kernels (not copies or memsets) that fn() launches, counted from the
+    CUPTI activity records that torch.profiler collects (the raw records:
+    kernels launched outside torch have no CPU-side op) in the last of
+    `sessions` profiled calls (the first session of a process may miss device
+    records); NCCL's kernels are left out.  None if the profiler is
+    unavailable or saw no kernel."""
     import torch
     try:
         from torch.profiler import ProfilerActivity, profile
-        with profile(activities=[ProfilerActivity.CUDA]) as prof:
-            fn()
-            torch.cuda.synchronize()
+        for _ in range(sessions):
+            with profile(activities=[ProfilerActivity.CUDA]) as prof:
+                fn()
+                torch.cuda.synchronize()
         n = 0
-        for e in prof.events():
-            if e.device_type != torch.autograd.DeviceType.CUDA:
+        for e in prof.profiler.kineto_results.events():
+            if not str(e.device_type()).endswith("CUDA"):
                 continue
-            name = e.name
+            name = e.name()
             if name.startswith(("Memcpy", "Memset", "memcpy", "memset")) or "nccl" in name.lower():
                 continue
             n += 1
-        return n
+        return n if n > 0 else None
     except Exception as exc:   # profiler missing on this build: no count
         print(f"note: kernel count unavailable ({exc})", file=sys.stderr)
         return None
@@ -634,10 +638,12 @@ def run_gpu(args):
             # exchange step: the estimators over the union of all ranks' samples
             shard.combine_moments(M, occ, conn, ws)
 
-    for _ in range(args.warmup - 1):
+    # the last two warm-up steps run under the profiler (the first session of a
+    # process may miss device records); the last one counts the kernels of a step
+    n_prof = 2 if args.warmup >= 2 else max(args.warmup, 1)
+    for _ in range(args.warmup - n_prof):
         one_step(0, False)
-    # the last warm-up step also counts the kernels one step launches
-    launches_per_step = count_kernels(lambda: one_step(0, False))
+    launches_per_step = count_kernels(lambda: one_step(0, False), sessions=n_prof)
     torch.cuda.synchronize()
     if P.status() != 0:
         raise RuntimeError("device status after warm-up")

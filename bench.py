@@ -579,8 +579,12 @@ def bench_gram(F, args):
     stat = d[:, :, None] * d[:, None, :] / (M ** 0.5)        # statistical error scale of C_kl
     err = ((c16 - c64).abs() / stat.clamp_min(1e-30)).max().item()
     n_kt = (K + 127) // 128
+    # MMA work issued: M = 128 rows per tile, N = 128 columns, or the real
+    # columns of the last site block rounded up to 16
+    ncol = [min(128, K - 128 * lt) for lt in range(n_kt)]
+    n_of = [(c + 15) // 16 * 16 for c in ncol]
     tiles = n_kt * (n_kt + 1) // 2
-    mma_flops = 3 * 2.0 * M * 128 * 128 * tiles * T
+    mma_flops = 3 * 2.0 * M * 128 * sum(n_of[lt] for kt in range(n_kt) for lt in range(kt, n_kt)) * T
     useful = 2.0 * M * K * (K + 1) / 2 * T
     pk = peaks()
     ms16 = res["bf16x3"][0]

@@ -127,17 +127,20 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr)
 }
 
 // instruction descriptor: kind::f16, A = B = bf16, D = f32, K-major A and B,
-// M = 128, N = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTile >> 3) << 17) |
-                            ((uint32_t)(kTile >> 4) << 24);
+// M = 128, N = n (a multiple of 16: 128, or the real columns of the last site
+// block rounded up)
+__host__ __device__ constexpr uint32_t mma_idesc(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate)
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.u32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d_tmem), "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+        ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -271,15 +274,15 @@ __device__ __forceinline__ void write_tile(const float (&acc)[64], int t, int kt
 
 // MMA issue of one 64-sample chunk: 4 K-steps x {hi hi, hi lo, lo hi}
 __device__ __forceinline__ void mma_chunk(uint32_t acc, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi, uint32_t b_lo,
-                                          bool first)
+                                          uint32_t idesc, bool first)
 {
 #pragma unroll
     for (int ks = 0; ks < kChunk / 16; ++ks) {
         const uint32_t ko = ks * 32;   // 16 bf16 = 32 bytes along K inside the swizzle atom
         const uint32_t acc0 = (!first || ks > 0) ? 1u : 0u;
-        mma_bf16(acc, make_desc(a_hi + ko), make_desc(b_hi + ko), acc0);
-        mma_bf16(acc, make_desc(a_hi + ko), make_desc(b_lo + ko), 1u);
-        mma_bf16(acc, make_desc(a_lo + ko), make_desc(b_hi + ko), 1u);
+        mma_bf16(acc, make_desc(a_hi + ko), make_desc(b_hi + ko), idesc, acc0);
+        mma_bf16(acc, make_desc(a_hi + ko), make_desc(b_lo + ko), idesc, 1u);
+        mma_bf16(acc, make_desc(a_lo + ko), make_desc(b_hi + ko), idesc, 1u);
     }
 }
 
@@ -363,6 +366,10 @@ __global__ void __launch_bounds__(kThreadsG, 1) gram_tc_kernel(const __grid_cons
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
+            // columns of this tile: the real sites of the column block, rounded
+            // up to 16 (the last block at K = 396 has 12)
+            const int ncol = min(kTile, g.K - lt * kTile);
+            const uint32_t idesc = mma_idesc((ncol + 15) / 16 * 16);
             bool ok = true;
             long long c = 0;
             for (long long seg = 0; seg < n_seg && ok; ++seg) {
@@ -386,7 +393,7 @@ __global__ void __launch_bounds__(kThreadsG, 1) gram_tc_kernel(const __grid_cons
                     const uint32_t base = smem_addr(img + st * 4 * kImage);
                     const uint32_t a_hi = base, a_lo = base + kImage;
                     const uint32_t b_hi = same ? a_hi : base + 2 * kImage, b_lo = same ? a_lo : base + 3 * kImage;
-                    mma_chunk(acc, a_hi, a_lo, b_hi, b_lo, c == first);
+                    mma_chunk(acc, a_hi, a_lo, b_hi, b_lo, idesc, c == first);
                     mma_commit(smem_addr(&sh->empty[st]));
                 }
                 if (ok) mma_commit(smem_addr(&sh->accfull[buf]));
@@ -446,8 +453,9 @@ struct GramGeom {
     size_t mu_bytes, ops_bytes;
 };
 
-// Times per batch: one wave of (time, tile) CTAs over the SMs, and at most
-// about 2 GB of split operands.
+// Times per batch: three waves of (time, tile) CTAs over the SMs (the tiles
+// of the last, partly filled site block are cheaper; the hardware fills the
+// SMs they free with the next CTAs), and at most about 6 GB of split operands.
 GramGeom gram_geom(Plan *p, int64_t M, int32_t T)
 {
     using namespace gram;
@@ -459,8 +467,8 @@ GramGeom gram_geom(Plan *p, int64_t M, int32_t T)
     gg.Mp = (M + kChunk - 1) / kChunk * kChunk;
     const size_t per_t = 2 * (size_t)gg.Kd * (size_t)gg.Mp * sizeof(__nv_bfloat16);
     const int sm = std::max(1, p->sm_count);
-    int tb = std::max(1, sm / gg.n_tiles);
-    tb = (int)std::min<size_t>((size_t)tb, std::max<size_t>(1, (size_t)(2ull << 30) / per_t));
+    int tb = std::max(1, 3 * sm / gg.n_tiles);
+    tb = (int)std::min<size_t>((size_t)tb, std::max<size_t>(1, (size_t)(6ull << 30) / per_t));
     gg.TB = std::max(1, std::min(tb, (int)T));
     gg.mu_bytes = ((sizeof(double) * (size_t)T * gg.K + 255) / 256) * 256;
     gg.ops_bytes = per_t * gg.TB;

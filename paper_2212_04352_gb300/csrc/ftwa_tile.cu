@@ -47,7 +47,6 @@ namespace ftwa {
 namespace tile {
 
 constexpr int kR = 8;                     // rows per tile
-constexpr int kMaxWarpsT = 24;            // warps per CTA: 16 (512 threads) or 24 (768)
 // tensor-memory columns per warp: warps w, w + 4, ... share lane quadrant w % 4
 // and split the 512 columns (multiples of 8 for the 8-column row-pair blocks)
 __host__ __device__ constexpr int cols_per_warp(int warps) { return (512 / (warps / 4)) / 8 * 8; }
@@ -1015,10 +1014,10 @@ static void row_part_slots(int N, int bw, const std::vector<Nbr> &nb, RowSlots &
                     for (int j = 0; j < nl; ++j) {
                         if (qv[j] < 0) continue;
                         Ent keep_e[3], bst_e[3];
-                        int keep_p[3], bst_p[3];
+                        int bst_p[3];
                         for (int n = 0; n < 3; ++n) {
                             keep_e[n] = bst_e[n] = ent[j][n];
-                            keep_p[n] = bst_p[n] = perm[j][n];
+                            bst_p[n] = perm[j][n];
                         }
                         long long bst = cur;
                         for (int y = 0; y < 6; ++y) {

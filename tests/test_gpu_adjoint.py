@@ -122,6 +122,44 @@ def test_adjoint_96_sites_fp64_spot_check(ftwa):
         assert abs(got - want) <= 1e-6 * scale, (got, want)
 
 
+def test_adjoint_fd_gate_at_adjoint_workload_size(ftwa):
+    """The adjoint workload's lattice, horizon and checkpointing (96-site
+    flake, U/t = 1.6, T = 5: 500 RK4 steps, checkpoints every 50, outputs
+    every 10) in FP64 on 8 samples: dL/dU, two bond gradients and two
+    initial-occupation gradients against central differences (h = 1e-5,
+    same seed) of the oracle, relative error <= 1e-6."""
+    lat = W.hexagonal_flake(4)
+    n0u, n0d = W.neel_state(lat)
+    nu, nd = W.softened(n0u), W.softened(n0d)
+    U, seed, M, steps, every, ckpt = 1.6, 11, 8, 500, 10, 50
+    rng = np.random.default_rng(4)
+    target = 0.5 + 0.05 * rng.standard_normal((steps // every + 1, 2 * lat.n_sites))
+    tb = np.array(lat.t_bond, dtype=np.float64)
+    _, occ = _loss(lat, U, nu, nd, seed, M, steps, every, target, tb)
+    g = torch.from_numpy(2.0 * (occ - target)).cuda()
+    with ftwa.Plan(lat, U, n_up=nu, n_dn=nd, precision=0, out_every=every) as P:
+        gU, gt, gn = P.adjoint(seed, M, steps, ckpt, g)
+        assert P.status() == 0
+    gU, gt, gn = gU.item(), gt.cpu().numpy(), gn.cpu().numpy()
+    h = 1e-5
+
+    def fd(fn):
+        return (fn(h) - fn(-h)) / (2 * h)
+    checks = [(gU, fd(lambda d: _loss(lat, U + d, nu, nd, seed, M, steps, every, target, tb)[0]))]
+    for b in (0, lat.n_bonds // 2):
+        checks.append((gt[b], fd(lambda d, b=b: _loss(lat, U, nu, nd, seed, M, steps, every, target,
+                                                      tb + d * (np.arange(lat.n_bonds) == b))[0])))
+    for s_, i in ((0, 5), (1, 70)):
+        def Ln(d, s_=s_, i=i):
+            a, b = nu.copy(), nd.copy()
+            (a if s_ == 0 else b)[i] += d
+            return _loss(lat, U, a, b, seed, M, steps, every, target, tb)[0]
+        checks.append((gn[s_, i], fd(Ln)))
+    scale = max(abs(w) for _, w in checks)
+    for got, want in checks:
+        assert abs(got - want) <= 1e-6 * max(abs(want), 1e-3 * scale), (got, want)
+
+
 @pytest.mark.parametrize("lat_name", ["flake96", "flake150", "brick198"])
 def test_adjoint_fp32_follows_fp64_large(ftwa, lat_name):
     """The FP32 adjoint (row-pass VJP, one 1024-thread CTA per SM) against the
